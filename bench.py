@@ -1,0 +1,307 @@
+"""Benchmark: gamma transport with Geant4-style navigation on one GB300.
+
+Workload (default): the sampling calorimeter -- 5000 lead/scintillator box
+cells in two-level voxels -- with 10^6 gamma tracks, energy uniform in
+[0.1, 10] MeV, along +z with a 10 mm Gaussian spot; plain FP64 navigator.  One
+step = one g4n_transport_batch over the whole batch (source generation,
+locate, safety, boundary search, move/relocate, interactions, tallies).
+
+Metric: navigation steps/s (every track advance, geometry- or physics-limited)
+with tracks/s beside it.  Inputs (geometry tables) are resident before the
+timed region; L2 is flushed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--tracks T]
+
+With --impl reference the FP64 CPU oracle is timed instead, on the host cores,
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "navigation steps/sec and γ tracks/sec on 1 GB300; chosen vs plain at matched results"
+WORKLOAD = ("sampling calorimeter: 50 alternating 5 mm lead-like / 10 mm scintillator-like layers x 10x10 "
+            "box cells of 100x100 mm (5000 cells) in a 2 m vacuum world, two voxel levels (z 50, x 10); "
+            "gamma energy U(0.1, 10) MeV along +z, Gaussian spot sigma 10 mm; Compton (Kahn) + photoabsorption, "
+            "10 keV cutoff; per-cell energy deposit in 100 batches")
+
+# Algorithmic FP64 work per counted event (flops: add/sub/mul/compare/min/max = 1, fma = 2, div/sqrt = 1).
+FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube": 90, "inside": 24,
+         "vox_nodes": 14, "phys_steps": 60}
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
+
+
+def algorithmic_flops(c: dict) -> float:
+    return float(sum(FLOPS[k] * c[k] for k in FLOPS))
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def calorimeter():
+    import synth
+    sc = synth.scenes.calorimeter_scene()
+    return sc, synth.scenes.calorimeter_source(), synth.scenes.CONFIG_SEEDS[1][1]
+
+
+def cpu_baseline(sc, src, seed, target_s: float = 12.0) -> dict:
+    """The FP64 oracle (brute-force navigation), as it stands, on all host cores; a bounded sample."""
+    import oracle
+    og = oracle.Geometry(sc)
+    threads = os.cpu_count() or 1
+    n, n2, dt, steps, tid = 4096, 0, 0.0, 0, 10_000_000
+    while dt < target_s and n2 < 50_000_000:
+        t0 = time.perf_counter()
+        r = og.transport(src, seed, n, tid0=tid, want_hash=False, want_len=False, threads=threads)
+        dt += time.perf_counter() - t0
+        steps += int(r["counters"][1])
+        tid += n
+        n2 += n
+        n *= 2
+    return {"value": steps / dt, "unit": "steps/s", "cores": int(r["threads"]), "kind": "oracle",
+            "tracks_per_s": n2 / dt, "seconds": dt,
+            "sample": f"{n2} histories (track ids from 10^7) of the same workload, brute-force FP64 oracle, "
+                      f"OpenMP over tracks"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, src, seed = calorimeter()
+    import oracle
+    og = oracle.Geometry(sc)
+    threads = os.cpu_count() or 1
+    n = max(64, args.ref_tracks)
+    times, steps = [], []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = og.transport(src, seed + k, n, want_hash=False, want_len=False, threads=threads)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            steps.append(int(r["counters"][1]))
+    tot = sum(times)
+    val = sum(steps) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tracks_per_step": n, "mode": "fp64 brute-force oracle"},
+            "tracks_per_s": n * args.steps / tot,
+            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{n} histories per step of the same workload"},
+            "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_gpu(args):
+    import torch
+    import paper_1209_5235_gb300 as g4
+    from paper_1209_5235_gb300 import build as b
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    b.build()
+    sc, src, seed = calorimeter()
+    ctx = g4.g4n_create(local)
+    gid = g4.build_scene(ctx, sc)
+    n = args.tracks
+    tid0 = rank * n                      # weak scaling: every rank transports its own n track ids
+    items = g4.make_items([(gid, n, tid0, src, 0)])
+    nb, stride = 100, sc.n_volumes + 2
+    stream = torch.cuda.current_stream()
+    edep = torch.zeros((nb, stride), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+    launch = dict(block_size=args.block, blocks_per_sm=args.blocks_per_sm)
+
+    def one(k):
+        g4.g4n_transport_batch(ctx, items, seed + k, edep, cnt, n_batches=nb, stream=stream, **launch)
+
+    for k in range(args.warmup):
+        one(1000 + k)
+    g4.g4n_sync(ctx, stream)
+    edep.zero_()
+    cnt.zero_()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            one(k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    g4.g4n_sync(ctx, stream)
+    if dist:
+        dist.barrier()
+    ms = [a.elapsed_time(c) for a, c in ev]
+    t_dev = sum(ms) / 1e3
+    c = g4.counters_dict(cnt)
+    steps_total, tracks_total = c["steps"], c["tracks"]
+    if dist:
+        tt = torch.tensor([t_dev], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+        st = torch.tensor([steps_total, tracks_total], dtype=torch.int64, device="cuda")
+        dist.all_reduce(st)
+        steps_total, tracks_total = int(st[0].item()), int(st[1].item())
+    value = steps_total / t_dev
+    # end to end through the host-buffer entry point: H2D of the batch description, D2H of the tallies
+    e2e_steps, e2e_t = 0, 0.0
+    out = None
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        out = g4.g4n_transport_batch_host(ctx, items, seed + k, stride, n_batches=nb, stream=stream, out=out,
+                                          **launch)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            e2e_t += dt
+            e2e_steps += int(out["counters"][1])
+    e2e = {"value": e2e_steps / e2e_t * (world if dist else 1), "unit": "steps/s",
+           "h2d_bytes_per_step": int(ctypes.sizeof(g4.g4n_work_item) + ctypes.sizeof(g4.g4n_batch_desc)),
+           "d2h_bytes_per_step": int(nb * stride * 8 + g4.G4N_N_COUNTERS * 8)}
+    if rank != 0:
+        g4.g4n_destroy(ctx)
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = load_peaks()
+    flops = algorithmic_flops(c) / args.steps        # per launch (this rank)
+    t_launch = float(np.mean(ms)) / 1e3
+    achieved = flops / t_launch / 1e12
+    hbm_bytes = (nb * stride * 8) * 2 + args.tracks * 0   # tallies read+written once per launch; tables stay in L2
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tracks_per_gpu": n, "mode": "fp64 plain navigator",
+                   "l2": "flushed between timed steps (256 MB write)", "block": args.block or 128,
+                   "blocks_per_sm": args.blocks_per_sm or "occupancy"},
+        "tracks_per_s": tracks_total / t_dev,
+        "steps_per_track": steps_total / max(tracks_total, 1),
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (recipe nominal 1.25 TFLOP/s)",
+                     "kernel": "k_transport", "flops_per_launch": flops},
+        "hbm": {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / t_launch / 1e9,
+                "peak_gbs": peaks.get("hbm_gbs"),
+                "frac": (hbm_bytes / t_launch / 1e9) / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "wall_s_timed_region": t_wall,
+        "counters": {k: c[k] for k in ("steps", "geom_steps", "phys_steps", "safety_skips", "cand_box", "inside",
+                                       "vox_nodes", "dist_out")},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(sc, src, seed)
+    print(json.dumps(line))
+    g4.g4n_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--tracks", type=int, default=1_000_000)
+    ap.add_argument("--ref-tracks", type=int, default=4000)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,244 @@
+/*
+ * g4nav.h -- C ABI of the GB300 (sm_103a) Geant4-style navigation and gamma
+ * transport library (libg4nav.so).
+ *
+ * The method is the data-parallel hot path of Seiskari, Kommeri and Niemi,
+ * "GPU in Physics Computation: Case Geant4 Navigation" (arXiv:1209.5235):
+ * the two navigation problems of Sec. 3.2 (locate a point in the volume
+ * hierarchy; step to the next boundary) and the free-path transport of
+ * Algorithm 1 (Sec. 3.1, Eqs. 1-8), extended with Compton scattering,
+ * photoabsorption and per-volume energy deposits.
+ *
+ * Conventions
+ *  - Lengths in mm, energies in MeV, attenuation coefficients in 1/mm.
+ *  - Every function returns an int status: G4N_OK (0) or a negative
+ *    G4N_ERR_* code; g4n_last_error() gives the context's last message.  No
+ *    C++ exception crosses this boundary.
+ *  - Array arguments of the query and transport calls are CALLER-OWNED
+ *    DEVICE pointers (e.g. torch CUDA tensors), structure-of-arrays:
+ *    a 3-vector array of n points is laid out as x[0..n), y[0..n), z[0..n).
+ *    The `stream` argument is a cudaStream_t (NULL = legacy default stream).
+ *    Calls are asynchronous on that stream; device-side errors (step caps,
+ *    loop caps) are reported by the next g4n_sync() on the same stream.
+ *  - The library owns the geometry tables and its workspace; g4n_destroy()
+ *    frees them.  One context per host thread; one transport in flight per
+ *    context at a time.
+ *  - Geometry is built on the host: materials, solids and placements, then
+ *    g4n_voxelize() and g4n_geom_finalize(), which validates, builds the
+ *    smart-voxel candidate lists and uploads the tables.  Several geometries
+ *    may be finalized in one context (the batched workload).
+ */
+#ifndef G4NAV_H
+#define G4NAV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct g4n_ctx g4n_ctx;
+typedef void *g4n_stream; /* cudaStream_t */
+
+enum {
+  G4N_OK = 0,
+  G4N_ERR_ARG = -1,        /* invalid argument (null pointer, bad id, non-unit direction, bad size) */
+  G4N_ERR_GEOM = -2,       /* invalid geometry (overlap, daughter outside mother, depth > G4N_DMAX) */
+  G4N_ERR_OOM = -3,        /* device or host allocation failed */
+  G4N_ERR_CUDA = -4,       /* a CUDA runtime call failed */
+  G4N_ERR_STEP_LIMIT = -5, /* at least one track reached the per-track step cap */
+  G4N_ERR_TIMEOUT = -6,    /* a device loop reached its iteration cap */
+  G4N_ERR_QUEUE = -7,      /* work queue overflow */
+  G4N_ERR_STATE = -8       /* call out of order (e.g. placing after finalize, query before finalize) */
+};
+
+enum { G4N_BOX = 0, G4N_TUBE = 1, G4N_ORB = 2 };
+
+/* Precision modes of compute_step / transport. */
+enum {
+  G4N_MODE_FP64 = 0,         /* every distance in FP64 */
+  G4N_MODE_FP32_RECHECK = 1, /* FP32 intersection/safety, FP64 recheck of near-minimum candidates */
+  G4N_MODE_LEARNED = 2       /* FP32_RECHECK plus the learned candidate proposal */
+};
+
+/* Limiter codes returned by g4n_compute_step. */
+enum { G4N_LIM_PHYSICS = -2, G4N_LIM_MOTHER = -1 };
+
+#define G4N_DMAX 8        /* maximum hierarchy depth, world included */
+#define G4N_N_COUNTERS 32 /* length of the transport counter array */
+
+/* Transport counters (indices into out_counters). */
+enum {
+  G4N_C_TRACKS = 0, G4N_C_STEPS, G4N_C_GEOM_STEPS, G4N_C_PHYS_STEPS, G4N_C_PHOTO, G4N_C_COMPTON, G4N_C_ESCAPED,
+  G4N_C_CUTOFF, G4N_C_PUSHES, G4N_C_STEP_LIMIT,
+  G4N_C_SAFETY_SKIPS = 16,   /* steps that skipped the boundary search because safety exceeded the physics step */
+  G4N_C_CAND_BOX, G4N_C_CAND_TUBE, G4N_C_CAND_ORB, /* DistanceToIn evaluations by solid type */
+  G4N_C_DIST_OUT,            /* DistanceToOut evaluations */
+  G4N_C_INSIDE,              /* full Inside tests (after the bounding-box prefilter) */
+  G4N_C_VOX_NODES,           /* voxel nodes visited by the boundary search */
+  G4N_C_RECHECKS,            /* FP64 rechecks in FP32_RECHECK mode */
+  G4N_C_PROPOSALS,           /* learned proposals used */
+  G4N_C_PRUNED               /* candidates skipped by the proposal bound */
+};
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (>= 0), or a host-only context (device = -1) that builds,
+ * validates and voxelizes geometry without touching a GPU (its queries return G4N_ERR_STATE).
+ * *ctx is set to NULL on failure. */
+int g4n_create(g4n_ctx **ctx, int device);
+/* Free every device and host resource of the context.  NULL is accepted. */
+int g4n_destroy(g4n_ctx *ctx);
+/* Last error message of the context ("" if none).  The string is owned by the context. */
+const char *g4n_last_error(const g4n_ctx *ctx);
+/* Surface tolerance = 1e-9 mm x scale (default scale 1).  Only before the first solid is added. */
+int g4n_set_tolerance_scale(g4n_ctx *ctx, double scale);
+/* Wait for `stream` and report any device-side error raised since the last sync. */
+int g4n_sync(g4n_ctx *ctx, g4n_stream stream);
+
+/* ---------------------------------------------------------------- geometry build (host) */
+
+/* A material: density (g/cm^3) and an attenuation table of n_e >= 2 strictly increasing
+ * energies with the Compton and photoabsorption linear coefficients (1/mm) at each energy.
+ * Interpolated lin-lin, clamped at the ends (the mu of Eqs. 1 and 9).  Arrays are HOST
+ * pointers, copied. */
+int g4n_material_add(g4n_ctx *ctx, double density, int32_t n_e, const double *E_MeV, const double *mu_compton,
+                     const double *mu_photo, int32_t *out_mat);
+
+/* Solids (Sec. 3.5 uses boxes, tubes, cones and balls; this library has box, tube segment, orb).
+ * Box: half-lengths.  Tube: rmin >= 0 (0 = solid), rmax > rmin, half-length hz, phi range
+ * [sphi, sphi + dphi] with 0 < dphi <= 2 pi.  Orb: a full solid sphere. */
+int g4n_solid_box(g4n_ctx *ctx, double hx, double hy, double hz, int32_t *out_solid);
+int g4n_solid_tube(g4n_ctx *ctx, double rmin, double rmax, double hz, double sphi, double dphi, int32_t *out_solid);
+int g4n_solid_orb(g4n_ctx *ctx, double r, int32_t *out_solid);
+
+/* Place `solid` of material `mat` inside volume `mother` (-1 for the world, which must be the
+ * first placement of a geometry).  Every placement is a distinct volume; ids are consecutive from
+ * 0 (the world) within a geometry, and a daughter's id orders it among its siblings (ties in
+ * locate and compute_step go to the lower id).  t: HOST pointer to the translation of the local
+ * origin in the mother frame.  rot: HOST pointer to {cos theta, sin theta} of the rotation about z
+ * taking local to mother coordinates, or NULL for none; it must have unit norm within 1e-12. */
+int g4n_place(g4n_ctx *ctx, int32_t mother, int32_t solid, int32_t mat, const double *t, const double *rot,
+              int32_t *out_vol);
+
+/* Smart-voxel request for the geometry being built.  mode 0 = smart heuristic (per mother, per
+ * level: slices = clamp(smartless x daughters, 1, max_slices) on the axis with the fewest
+ * candidates per node, equal neighbouring nodes merged, nodes with more than refine_above
+ * candidates refined on a further axis, up to 3 levels); mode 1 = fixed (n_levels levels with the
+ * given axes 0/1/2 = x/y/z and slice counts, applied to every mother); mode 2 = none (one node).
+ * Candidate lists are exact accelerations: results never depend on this choice. */
+typedef struct {
+  int32_t mode;
+  int32_t n_levels;
+  int32_t axes[3];
+  int32_t slices[3];
+  double smartless;
+  int32_t max_slices;
+  int32_t refine_above;
+} g4n_voxel_params;
+int g4n_voxelize(g4n_ctx *ctx, const g4n_voxel_params *params);
+
+/* Validate the volumes placed since the last finalize (every daughter inside its mother,
+ * siblings not overlapping, depth <= G4N_DMAX), build the voxels and upload the tables.
+ * Returns the geometry id in *out_geom. */
+int g4n_geom_finalize(g4n_ctx *ctx, int32_t *out_geom);
+
+/* Table sizes of a finalized geometry (HOST array of 8): n_volumes, n_voxel_headers,
+ * n_voxel_slices, n_candidate_lists, n_candidate_entries, device bytes, max depth, materials. */
+int g4n_geom_info(g4n_ctx *ctx, int32_t geom, int64_t *out8);
+
+/* ---------------------------------------------------------------- navigation queries (device) */
+
+/* Navigation problem 1 (Sec. 3.2): the volumes containing each point.  Direction-aware: a point
+ * within the tolerance band of a surface belongs to the solid iff dir points strictly inward
+ * through every surface within the band.  Descends from the world, entering the first daughter in
+ * placement order that contains the point.
+ * pos, dir: n x 3 SoA doubles (dir of unit norm).  out_depth: n int32 (0 = outside the world,
+ * 1 = world only, ...).  out_path: G4N_DMAX x n int32, level k of point i at [k * n + i], volume
+ * ids from the world down, -1 below the depth. */
+int g4n_locate(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, const double *dir, int32_t *out_depth,
+               int32_t *out_path, g4n_stream stream);
+
+/* Navigation problem 2 (Sec. 3.2) and Algorithm 1's "next intersection": from each point inside
+ * path[depth-1] (as returned by g4n_locate), the distance to the next boundary along dir, limited
+ * by the proposed physics step.  out_step = min(geometric step, proposed); out_limiter = daughter
+ * volume id entered, G4N_LIM_MOTHER (leaving the current volume) or G4N_LIM_PHYSICS (proposed
+ * strictly shorter).  Ties: a daughter beats the mother, the lower daughter id beats a higher one,
+ * geometry beats physics.  out_safety: an isotropic lower bound of the distance to any boundary.
+ * proposed may be NULL (= +infinity).  mode: G4N_MODE_FP64 or G4N_MODE_FP32_RECHECK (same step
+ * and limiter; the safety may be smaller).  Arrays as in g4n_locate; out_* n doubles / int32. */
+int g4n_compute_step(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, const double *dir,
+                     const int32_t *depth, const int32_t *path, const double *proposed, double *out_step,
+                     double *out_safety, int32_t *out_limiter, int32_t mode, g4n_stream stream);
+
+/* ---------------------------------------------------------------- transport (device) */
+
+/* Per-track source.  Every random quantity is drawn from Philox4x32-10 keyed by the 64-bit seed
+ * with counter (draw, track id lo, track id hi, stream 0); one uniform in (0, 1] per block.
+ * Position = pos, plus a Gaussian spot of sigma spot_sigma in x and y (Marsaglia polar method) if
+ * spot_sigma > 0, with z uniform in [z0, z1] if has_z.  Direction: isotropic (cos theta uniform,
+ * azimuth by rejection on the unit disc) or dir.  Energy: e_kind 0 mono e0, 1 uniform [e0, e1],
+ * 2 log-uniform [e0, e1]. */
+typedef struct {
+  double pos[3];
+  double spot_sigma;
+  int32_t has_z;
+  double z0, z1;
+  int32_t isotropic;
+  double dir[3];
+  int32_t e_kind;
+  double e0, e1;
+} g4n_source;
+
+/* A run of n_tracks consecutive track ids starting at track_id0 in geometry `geom`.  Its deposits
+ * go to columns [tally_offset, tally_offset + n_volumes + 2) of each tally row. */
+typedef struct {
+  int32_t geom;
+  int64_t n_tracks;
+  int64_t track_id0;
+  g4n_source source;
+  int64_t tally_offset;
+} g4n_work_item;
+
+/* A transport launch.  items: HOST array of n_items work items, processed from one device queue
+ * by a persistent kernel.  Physics: Algorithm 1 free paths with Y = -log W (stream 1 of the
+ * track's generator), interactions Compton (Kahn's method) or photoabsorption chosen by
+ * U mu_tot < mu_photo, energy below `cutoff` after a Compton scatter deposited on the spot.
+ * Tally rows: track id mod n_tally_batches; tally_stride doubles per row.  max_steps: per-track
+ * cap (0 = 10^6).  block_size / blocks_per_sm / chunk: launch shape (0 = defaults). */
+typedef struct {
+  int32_t n_items;
+  const g4n_work_item *items;
+  uint64_t seed;
+  double cutoff;
+  int32_t mode;
+  int32_t n_tally_batches;
+  int64_t tally_stride;
+  int64_t max_steps;
+  int32_t block_size;
+  int32_t blocks_per_sm;
+  int32_t chunk;
+} g4n_batch_desc;
+
+/* Transport every track of the batch (Algorithm 2, phase 5).  out_edep: n_tally_batches x
+ * tally_stride doubles, ACCUMULATED into (zero it first): column tally_offset + v gets the energy
+ * deposited in volume v (excluding its daughters), column tally_offset + n_volumes the energy
+ * that left the world, column tally_offset + n_volumes + 1 the source energy.  out_counters:
+ * G4N_N_COUNTERS uint64, accumulated.  out_track_hash / out_track_len: optional (NULL) per-track
+ * FNV-1a 64 hash of the step records (leaf volume after the step, limiter, event) and total path
+ * length, indexed by the track's position in the concatenated items.  All DEVICE pointers. */
+int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_edep, uint64_t *out_counters,
+                        uint64_t *out_track_hash, double *out_track_len, g4n_stream stream);
+
+/* As g4n_transport_batch, with HOST output buffers: the library zeroes its device staging
+ * buffers, runs the batch on `stream`, copies the results back and synchronizes.  out_edep and
+ * out_counters are overwritten (not accumulated); the hash/length outputs may be NULL. */
+int g4n_transport_batch_host(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_edep, uint64_t *out_counters,
+                             uint64_t *out_track_hash, double *out_track_len, g4n_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* G4NAV_H */

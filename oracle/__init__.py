@@ -78,6 +78,8 @@ def lib():
             "o_source_sample": (None, [vp, u64, i64, i64, vp, vp, vp]),
             "o_transport": (i, [i, vp, u64, i64, i64, d, i64, i, vp, vp, vp, vp, i]),
             "o_free_path": (d, [i, vp, vp, d, d, vp]),
+            "o_locate_many": (None, [i, i64, vp, vp, vp, vp]),
+            "o_compute_step_many": (None, [i, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -149,17 +151,25 @@ class Geometry:
         return depth, path
 
     def locate_many(self, pos: np.ndarray, dirs: np.ndarray):
+        """pos, dirs: (n, 3).  Returns depth (n,) and paths (n, DMAX)."""
         n = pos.shape[0]
         depth = np.zeros(n, dtype=np.int32)
         paths = np.full((n, DMAX), -1, dtype=np.int32)
-        L = lib()
-        pos = _f64(pos)
-        dirs = _f64(dirs)
-        for i in range(n):
-            path = np.full(DMAX, -1, dtype=np.int32)
-            depth[i] = L.o_locate(self.gid, _p(pos[i]), _p(dirs[i]), _p(path))
-            paths[i] = path
+        lib().o_locate_many(self.gid, int(n), _p(_f64(pos)), _p(_f64(dirs)), _p(depth), _p(paths))
         return depth, paths
+
+    def compute_step_many(self, pos, dirs, depth, paths, proposed=None):
+        """Brute-force steps for n queries; returns (step, limiter, safety)."""
+        n = pos.shape[0]
+        step = np.zeros(n)
+        lim = np.zeros(n, dtype=np.int32)
+        saf = np.zeros(n)
+        prop = _f64(proposed) if proposed is not None else None
+        lib().o_compute_step_many(self.gid, int(n), _p(_f64(pos)), _p(_f64(dirs)),
+                                  _p(np.ascontiguousarray(depth, dtype=np.int32)),
+                                  _p(np.ascontiguousarray(paths, dtype=np.int32)),
+                                  _p(prop) if prop is not None else None, _p(step), _p(lim), _p(saf))
+        return step, lim, saf
 
     def relocate(self, path, depth: int, p, v):
         path = np.ascontiguousarray(np.asarray(path, dtype=np.int32)).copy()

@@ -1001,3 +1001,20 @@ double o_free_path(int gi, const double *p, const double *v, double E, double Y,
   if (n_steps) *n_steps = steps;
   return O_INF;
 }
+
+/* ------------------------------------------------------------------ batch helpers for the tests */
+
+/* pos, dir: n x 3 row-major; depth: n; path: n x O_DMAX row-major. */
+void o_locate_many(int gi, int64_t n, const double *pos, const double *dir, int *depth, int *path) {
+  for (int64_t i = 0; i < n; ++i) depth[i] = o_locate(gi, pos + 3 * i, dir + 3 * i, path + O_DMAX * i);
+}
+
+/* proposed may be NULL (+inf). */
+void o_compute_step_many(int gi, int64_t n, const double *pos, const double *dir, const int *depth, const int *path,
+                         const double *proposed, double *step, int *limiter, double *safety) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (depth[i] <= 0) { step[i] = NAN; limiter[i] = -99; safety[i] = NAN; continue; }
+    o_compute_step(gi, depth[i], path + O_DMAX * i, pos + 3 * i, dir + 3 * i, proposed ? proposed[i] : O_INF,
+                   &step[i], &limiter[i], &safety[i]);
+  }
+}

@@ -1,0 +1,358 @@
+"""ctypes binding of libg4nav: the C-ABI entry points under the same names.
+
+Every function here only converts arguments (torch tensors -> device
+pointers, numpy/sequences -> host arrays, the current torch stream ->
+cudaStream_t) and raises ``G4NError`` on a non-zero status.  No navigation,
+physics or fallback computation happens in Python: if the shared library is
+missing the calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libg4nav.so")
+
+G4N_OK, G4N_ERR_ARG, G4N_ERR_GEOM, G4N_ERR_OOM, G4N_ERR_CUDA = 0, -1, -2, -3, -4
+G4N_ERR_STEP_LIMIT, G4N_ERR_TIMEOUT, G4N_ERR_QUEUE, G4N_ERR_STATE = -5, -6, -7, -8
+G4N_BOX, G4N_TUBE, G4N_ORB = 0, 1, 2
+G4N_MODE_FP64, G4N_MODE_FP32_RECHECK, G4N_MODE_LEARNED = 0, 1, 2
+G4N_LIM_PHYSICS, G4N_LIM_MOTHER = -2, -1
+G4N_DMAX = 8
+G4N_N_COUNTERS = 32
+COUNTER_NAMES = {0: "tracks", 1: "steps", 2: "geom_steps", 3: "phys_steps", 4: "photo", 5: "compton", 6: "escaped",
+                 7: "cutoff", 8: "pushes", 9: "step_limit", 16: "safety_skips", 17: "cand_box", 18: "cand_tube",
+                 19: "cand_orb", 20: "dist_out", 21: "inside", 22: "vox_nodes", 23: "rechecks", 24: "proposals",
+                 25: "pruned"}
+PARITY_COUNTERS = ["tracks", "steps", "geom_steps", "phys_steps", "photo", "compton", "escaped", "cutoff", "pushes",
+                   "step_limit"]
+
+EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_scale", "g4n_sync", "g4n_material_add",
+            "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_place", "g4n_voxelize", "g4n_geom_finalize",
+            "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_transport_batch", "g4n_transport_batch_host"]
+
+__all__ = EXPORTED + ["G4NError", "load", "lib_path", "build_scene", "make_items", "counters_dict", "voxel_params",
+                      "COUNTER_NAMES", "PARITY_COUNTERS", "G4N_DMAX", "G4N_N_COUNTERS", "G4N_MODE_FP64",
+                      "G4N_MODE_FP32_RECHECK", "G4N_MODE_LEARNED", "G4N_LIM_PHYSICS", "G4N_LIM_MOTHER",
+                      "G4N_ERR_ARG", "G4N_ERR_GEOM", "G4N_ERR_STEP_LIMIT", "G4N_ERR_TIMEOUT", "G4N_ERR_STATE",
+                      "g4n_voxel_params", "g4n_source", "g4n_work_item", "g4n_batch_desc"]
+
+
+class G4NError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libg4nav error {code}: {msg}")
+        self.code = code
+
+
+class g4n_voxel_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("axes", ctypes.c_int32 * 3),
+                ("slices", ctypes.c_int32 * 3), ("smartless", ctypes.c_double), ("max_slices", ctypes.c_int32),
+                ("refine_above", ctypes.c_int32)]
+
+
+class g4n_source(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_double * 3), ("spot_sigma", ctypes.c_double), ("has_z", ctypes.c_int32),
+                ("z0", ctypes.c_double), ("z1", ctypes.c_double), ("isotropic", ctypes.c_int32),
+                ("dir", ctypes.c_double * 3), ("e_kind", ctypes.c_int32), ("e0", ctypes.c_double),
+                ("e1", ctypes.c_double)]
+
+
+class g4n_work_item(ctypes.Structure):
+    _fields_ = [("geom", ctypes.c_int32), ("n_tracks", ctypes.c_int64), ("track_id0", ctypes.c_int64),
+                ("source", g4n_source), ("tally_offset", ctypes.c_int64)]
+
+
+class g4n_batch_desc(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_int32), ("items", ctypes.POINTER(g4n_work_item)), ("seed", ctypes.c_uint64),
+                ("cutoff", ctypes.c_double), ("mode", ctypes.c_int32), ("n_tally_batches", ctypes.c_int32),
+                ("tally_stride", ctypes.c_int64), ("max_steps", ctypes.c_int64), ("block_size", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return LIB_PATH
+
+
+def load():
+    """Load libg4nav.so (built by ``paper_1209_5235_gb300.build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libg4nav.so is not built ({LIB_PATH}); run paper_1209_5235_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "g4n_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int],
+        "g4n_destroy": [vp], "g4n_set_tolerance_scale": [vp, d], "g4n_sync": [vp, vp],
+        "g4n_material_add": [vp, d, i32, vp, vp, vp, vp],
+        "g4n_solid_box": [vp, d, d, d, vp], "g4n_solid_tube": [vp, d, d, d, d, d, vp], "g4n_solid_orb": [vp, d, vp],
+        "g4n_place": [vp, i32, i32, i32, vp, vp, vp], "g4n_voxelize": [vp, ctypes.POINTER(g4n_voxel_params)],
+        "g4n_geom_finalize": [vp, vp], "g4n_geom_info": [vp, i32, vp],
+        "g4n_locate": [vp, i32, i64, vp, vp, vp, vp, vp],
+        "g4n_compute_step": [vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp],
+        "g4n_transport_batch": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
+        "g4n_transport_batch_host": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.g4n_last_error.argtypes = [vp]
+    L.g4n_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(ctx, rc: int):
+    if rc != G4N_OK:
+        msg = load().g4n_last_error(ctx) if ctx else b""
+        raise G4NError(rc, (msg or b"").decode())
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype, name):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous CUDA tensor of {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+# ---------------------------------------------------------------- context
+
+def g4n_create(device: int = 0):
+    ctx = ctypes.c_void_p()
+    rc = load().g4n_create(ctypes.byref(ctx), int(device))
+    if rc != G4N_OK:
+        raise G4NError(rc, "g4n_create failed (no CUDA device?)")
+    return ctx
+
+
+def g4n_destroy(ctx) -> None:
+    load().g4n_destroy(ctx)
+
+
+def g4n_last_error(ctx) -> str:
+    return (load().g4n_last_error(ctx) or b"").decode()
+
+
+def g4n_set_tolerance_scale(ctx, scale: float) -> None:
+    _check(ctx, load().g4n_set_tolerance_scale(ctx, float(scale)))
+
+
+def g4n_sync(ctx, stream=None) -> None:
+    _check(ctx, load().g4n_sync(ctx, _stream(stream)))
+
+
+# ---------------------------------------------------------------- geometry build
+
+def g4n_material_add(ctx, density: float, energies, mu_compton, mu_photo) -> int:
+    e, c, p = _host(energies, np.float64), _host(mu_compton, np.float64), _host(mu_photo, np.float64)
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_material_add(ctx, float(density), int(e.shape[0]), e.ctypes.data, c.ctypes.data,
+                                        p.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def g4n_solid_box(ctx, hx: float, hy: float, hz: float) -> int:
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_solid_box(ctx, float(hx), float(hy), float(hz), ctypes.byref(out)))
+    return out.value
+
+
+def g4n_solid_tube(ctx, rmin: float, rmax: float, hz: float, sphi: float, dphi: float) -> int:
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_solid_tube(ctx, float(rmin), float(rmax), float(hz), float(sphi), float(dphi),
+                                      ctypes.byref(out)))
+    return out.value
+
+
+def g4n_solid_orb(ctx, r: float) -> int:
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_solid_orb(ctx, float(r), ctypes.byref(out)))
+    return out.value
+
+
+def g4n_place(ctx, mother: int, solid: int, mat: int, t: Sequence[float], rot: Optional[Sequence[float]] = None) -> int:
+    tt = _host(t, np.float64)
+    rr = _host(rot, np.float64) if rot is not None else None
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_place(ctx, int(mother), int(solid), int(mat), tt.ctypes.data,
+                                 rr.ctypes.data if rr is not None else None, ctypes.byref(out)))
+    return out.value
+
+
+def voxel_params(spec) -> g4n_voxel_params:
+    """g4n_voxel_params from a synth.VoxelSpec-like object."""
+    p = g4n_voxel_params()
+    p.mode = {"smart": 0, "fixed": 1, "none": 2}[spec.mode]
+    p.n_levels = len(spec.axes) if spec.mode == "fixed" else getattr(spec, "max_levels", 3)
+    for k, a in enumerate(spec.axes):
+        p.axes[k] = a
+    for k, s in enumerate(spec.slices):
+        p.slices[k] = s
+    p.smartless = float(spec.smartless)
+    p.max_slices = int(spec.max_slices)
+    p.refine_above = int(spec.refine_above)
+    return p
+
+
+def g4n_voxelize(ctx, params: g4n_voxel_params) -> None:
+    _check(ctx, load().g4n_voxelize(ctx, ctypes.byref(params)))
+
+
+def g4n_geom_finalize(ctx) -> int:
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_geom_finalize(ctx, ctypes.byref(out)))
+    return out.value
+
+
+def g4n_geom_info(ctx, geom: int) -> dict:
+    out = np.zeros(8, dtype=np.int64)
+    _check(ctx, load().g4n_geom_info(ctx, int(geom), out.ctypes.data))
+    keys = ["n_volumes", "n_voxel_headers", "n_voxel_slices", "n_candidate_lists", "n_candidate_entries",
+            "device_bytes", "max_depth", "n_materials"]
+    return dict(zip(keys, out.tolist()))
+
+
+def build_scene(ctx, scene) -> int:
+    """Marshal a synth.Scene through the geometry-build calls; returns the geometry id."""
+    mats = [g4n_material_add(ctx, m.density, m.energies, m.mu_compton, m.mu_photo) for m in scene.materials]
+    solids = []
+    for s in scene.solids:
+        if s.kind == G4N_BOX:
+            solids.append(g4n_solid_box(ctx, *s.params))
+        elif s.kind == G4N_TUBE:
+            solids.append(g4n_solid_tube(ctx, *s.params))
+        else:
+            solids.append(g4n_solid_orb(ctx, *s.params))
+    for pl in scene.placements:
+        g4n_place(ctx, pl.mother, solids[pl.solid], mats[pl.material], pl.t, pl.rot)
+    g4n_voxelize(ctx, voxel_params(scene.voxel))
+    return g4n_geom_finalize(ctx)
+
+
+# ---------------------------------------------------------------- queries
+
+def g4n_locate(ctx, geom: int, pos, dir, out_depth=None, out_path=None, stream=None):
+    """pos, dir: (3, n) float64 CUDA tensors (SoA).  Returns (depth (n,) int32, path (G4N_DMAX, n) int32)."""
+    import torch
+    n = pos.shape[1]
+    if out_depth is None:
+        out_depth = torch.empty(n, dtype=torch.int32, device=pos.device)
+    if out_path is None:
+        out_path = torch.empty((G4N_DMAX, n), dtype=torch.int32, device=pos.device)
+    _check(ctx, load().g4n_locate(ctx, int(geom), int(n), _dptr(pos, torch.float64, "pos"),
+                                  _dptr(dir, torch.float64, "dir"), _dptr(out_depth, torch.int32, "out_depth"),
+                                  _dptr(out_path, torch.int32, "out_path"), _stream(stream)))
+    return out_depth, out_path
+
+
+def g4n_compute_step(ctx, geom: int, pos, dir, depth, path, proposed=None, mode: int = G4N_MODE_FP64, stream=None):
+    """Returns (step (n,) f64, safety (n,) f64, limiter (n,) int32)."""
+    import torch
+    n = pos.shape[1]
+    step = torch.empty(n, dtype=torch.float64, device=pos.device)
+    saf = torch.empty(n, dtype=torch.float64, device=pos.device)
+    lim = torch.empty(n, dtype=torch.int32, device=pos.device)
+    _check(ctx, load().g4n_compute_step(ctx, int(geom), int(n), _dptr(pos, torch.float64, "pos"),
+                                        _dptr(dir, torch.float64, "dir"), _dptr(depth, torch.int32, "depth"),
+                                        _dptr(path, torch.int32, "path"), _dptr(proposed, torch.float64, "proposed"),
+                                        _dptr(step, torch.float64, "step"), _dptr(saf, torch.float64, "safety"),
+                                        _dptr(lim, torch.int32, "limiter"), int(mode), _stream(stream)))
+    return step, saf, lim
+
+
+def make_items(entries) -> "ctypes.Array":
+    """Work items from (geom, n_tracks, track_id0, synth.Source, tally_offset) tuples."""
+    arr = (g4n_work_item * len(entries))()
+    for k, (geom, n, tid0, src, off) in enumerate(entries):
+        w = arr[k]
+        w.geom, w.n_tracks, w.track_id0, w.tally_offset = int(geom), int(n), int(tid0), int(off)
+        s = w.source
+        for i in range(3):
+            s.pos[i] = float(src.pos[i])
+            s.dir[i] = float(src.direction[i])
+        s.spot_sigma = float(src.spot_sigma)
+        s.has_z = 1 if src.z_range is not None else 0
+        s.z0, s.z1 = (float(src.z_range[0]), float(src.z_range[1])) if src.z_range is not None else (0.0, 0.0)
+        s.isotropic = 1 if src.isotropic else 0
+        s.e_kind = {"mono": 0, "uniform": 1, "loguniform": 2}[src.e_kind]
+        s.e0, s.e1 = float(src.e0), float(src.e1)
+    return arr
+
+
+def _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, chunk):
+    d = g4n_batch_desc()
+    d.n_items = len(items)
+    d.items = ctypes.cast(items, ctypes.POINTER(g4n_work_item))
+    d.seed = ctypes.c_uint64(seed).value
+    d.cutoff = float(cutoff)
+    d.mode = int(mode)
+    d.n_tally_batches = int(n_batches)
+    d.tally_stride = int(stride)
+    d.max_steps = int(max_steps)
+    d.block_size, d.blocks_per_sm, d.chunk = int(block_size), int(blocks_per_sm), int(chunk)
+    return d
+
+
+def g4n_transport_batch(ctx, items, seed: int, edep, counters, track_hash=None, track_len=None, cutoff: float = 0.01,
+                        mode: int = G4N_MODE_FP64, n_batches: int = 100, max_steps: int = 0, block_size: int = 0,
+                        blocks_per_sm: int = 0, chunk: int = 0, stream=None) -> None:
+    """Device outputs (accumulated): edep (n_batches, stride) f64, counters (32,) int64 (as uint64 bits)."""
+    import torch
+    d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, chunk)
+    if edep.shape[0] != n_batches:
+        raise ValueError("edep rows must equal n_batches")
+    _check(ctx, load().g4n_transport_batch(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
+                                           _dptr(counters, torch.int64, "counters"),
+                                           _dptr(track_hash, torch.int64, "track_hash"),
+                                           _dptr(track_len, torch.float64, "track_len"), _stream(stream)))
+
+
+def g4n_transport_batch_host(ctx, items, seed: int, stride: int, n_tracks: int = 0, want_hash: bool = False,
+                             want_len: bool = False, cutoff: float = 0.01, mode: int = G4N_MODE_FP64,
+                             n_batches: int = 100, max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0,
+                             chunk: int = 0, stream=None, out=None):
+    """Host-buffer variant: returns dict of numpy arrays (edep, counters, hashes, lengths)."""
+    d = _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, chunk)
+    if out is None:
+        out = {"edep": np.zeros((n_batches, stride)), "counters": np.zeros(G4N_N_COUNTERS, dtype=np.uint64),
+               "hashes": np.zeros(n_tracks, dtype=np.uint64) if want_hash else None,
+               "lengths": np.zeros(n_tracks) if want_len else None}
+    rc = load().g4n_transport_batch_host(ctx, ctypes.byref(d), out["edep"].ctypes.data, out["counters"].ctypes.data,
+                                         out["hashes"].ctypes.data if out["hashes"] is not None else None,
+                                         out["lengths"].ctypes.data if out["lengths"] is not None else None,
+                                         _stream(stream))
+    _check(ctx, rc)
+    return out
+
+
+def counters_dict(counters) -> dict:
+    """Name -> value for a counter array (numpy uint64 or torch int64)."""
+    a = counters.cpu().numpy() if hasattr(counters, "cpu") else np.asarray(counters)
+    a = a.view(np.uint64) if a.dtype == np.int64 else a
+    return {name: int(a[k]) for k, name in COUNTER_NAMES.items()}

@@ -1,0 +1,152 @@
+// g4n_internal.h -- device table layout and context of libg4nav (product code).
+//
+// Geometry lives in HBM as one blob per finalized geometry:
+//   DVol[n]      128 B per placed volume: placement (mother -> local), solid
+//                parameters, kind/flags, mother, material, voxel root, depth
+//   DWorld[n]    64 B: composed world -> local transform of each volume
+//   DBox32[n]    32 B: FP32 bounding box of each volume in its mother's frame,
+//                rounded outward and padded (conservative prefilter for Inside)
+//   DVoxHdr[]    smart-voxel headers (one per slicing level and node)
+//   DVoxSlice[]  per slice: child (candidate list or sub-header) and the
+//                slice range [k0, k1] of the merged node it belongs to
+//   DCandList[]  (offset, count) into cand[]: daughter ids in increasing id
+//   materials    per material: energy grid, mu_compton, mu_photo (1/mm)
+// All tables are small (a few MB at most) and stay L2-resident.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "g4nav.h"
+
+namespace g4n {
+
+constexpr int kDMax = G4N_DMAX;
+constexpr int kMaxLevels = 3;
+
+enum SolidKind : int32_t { kBox = 0, kTube = 1, kOrb = 2 };
+enum TubeFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4 };
+
+struct alignas(128) DVol {
+  double tx, ty, tz, c, s;  // placement: local = R(theta)^T (mother - t)
+  double p[7];              // box: hx hy hz | orb: r | tube: rmin rmax hz cos(sphi) sin(sphi) cos(ephi) sin(ephi)
+  int32_t kind, flags, mother, mat;
+  int32_t vox;              // root voxel header of this volume's daughters (-1: no daughters)
+  int32_t depth;            // 1 for the world
+  int32_t n_dau, pad;
+};
+static_assert(sizeof(DVol) == 128, "DVol must be 128 bytes");
+
+struct alignas(64) DWorld {
+  double tx, ty, tz, c, s;  // world -> local: local = R^T (world - t)
+  double pad[3];
+};
+
+struct alignas(32) DBox32 {
+  float lo[3], hi[3];       // in the mother frame
+  float pad[2];
+};
+
+struct DVoxHdr {
+  double lo, width, inv_width;
+  int32_t axis, nslices, slice_base, pad;
+};
+
+struct DVoxSlice {
+  int32_t child;            // >= 0: candidate list id; < 0: -(sub header + 1)
+  int16_t k0, k1;           // slice range of the merged node
+};
+
+struct DCandList {
+  int32_t offset, count;
+};
+
+// Device view of one geometry.
+struct DGeom {
+  const DVol *vol;
+  const DWorld *wxf;
+  const DBox32 *box;
+  const DVoxHdr *hdr;
+  const DVoxSlice *slice;
+  const DCandList *clist;
+  const int32_t *cand;
+  const double *matE, *matC, *matP;
+  const int32_t *mat_off, *mat_n;
+  int32_t n_vol, n_mat;
+  double tol, half;
+};
+
+// Host-side record of a solid.
+struct HSolid {
+  int32_t kind;
+  double a, b, c, sphi, dphi;
+};
+
+struct HMat {
+  double rho;
+  std::vector<double> E, muC, muP;
+};
+
+struct HPlace {
+  int32_t mother, solid, mat;
+  double t[3], c, s;
+};
+
+struct HGeom {
+  // host copies (for validation, info and tests)
+  std::vector<DVol> vol;
+  std::vector<DWorld> wxf;
+  std::vector<DBox32> box;
+  std::vector<DVoxHdr> hdr;
+  std::vector<DVoxSlice> slice;
+  std::vector<DCandList> clist;
+  std::vector<int32_t> cand;
+  std::vector<double> matE, matC, matP;
+  std::vector<int32_t> mat_off, mat_n;
+  int32_t max_depth = 0;
+  // device blob
+  void *blob = nullptr;
+  size_t blob_bytes = 0;
+  DGeom dview{};
+};
+
+struct Builder {
+  std::vector<HMat> mats;
+  std::vector<HSolid> solids;
+  std::vector<HPlace> places;
+  g4n_voxel_params vox{0, 0, {0, 1, 2}, {0, 0, 0}, 2.0, 1000, 4};
+  bool vox_set = false;
+  void clear() {
+    mats.clear();
+    solids.clear();
+    places.clear();
+    vox_set = false;
+  }
+};
+
+}  // namespace g4n
+
+struct g4n_ctx {
+  int device = 0;
+  std::string err;
+  double scale = 1.0;
+  double tol = 1e-9, half = 0.5e-9;
+  g4n::Builder b;
+  std::vector<g4n::HGeom *> geoms;
+  // device geometry directory (DGeom per geometry id), grown on finalize
+  g4n::DGeom *d_geoms = nullptr;
+  int d_geoms_cap = 0;
+  // transport workspace: queue head, status word, item table
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  // host staging for g4n_transport_batch_host
+  void *h_stage = nullptr;
+  size_t h_stage_bytes = 0;
+  void *d_stage = nullptr;
+  size_t d_stage_bytes = 0;
+  int sm_count = 0;
+};
+
+// error helpers shared by the translation units
+int g4n_fail(g4n_ctx *ctx, int code, const std::string &msg);

@@ -1,0 +1,639 @@
+// geom_host.cpp -- context, geometry construction, validation, smart voxels and
+// upload for libg4nav (host code, C++17).
+//
+// The geometry model is Geant4's (Sec. 3.2): a hierarchy of placed solids; each
+// placement here is a distinct volume.  Navigation needs, per mother volume, a
+// way to find the few daughters worth testing; like Geant4's smart voxels this
+// slices the mother's extent along one axis, lists the daughters overlapping
+// each slice, merges equal neighbouring slices into one node and refines crowded
+// nodes along a further axis.  The lists are conservative (daughter extents are
+// padded), so every navigation result equals the brute-force one.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <random>
+
+#include "g4n_internal.h"
+
+using namespace g4n;
+
+int g4n_fail(g4n_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define G4N_CUDA_TRY(call, what)                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return g4n_fail(ctx, e_ == cudaErrorMemoryAllocation ? G4N_ERR_OOM : G4N_ERR_CUDA,   \
+                      std::string(what) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+namespace {
+
+constexpr int kMaxGeoms = 4096;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+struct Box3 {
+  double lo[3], hi[3];
+};
+
+// Tight extent of a solid in its own frame, rotated by (c, s) about z and shifted by t.
+Box3 solid_extent(const HSolid &so, double c, double s, const double *t) {
+  Box3 b;
+  if (so.kind == kBox) {
+    double ex = std::fabs(c) * so.a + std::fabs(s) * so.b;
+    double ey = std::fabs(s) * so.a + std::fabs(c) * so.b;
+    b = {{-ex, -ey, -so.c}, {ex, ey, so.c}};
+  } else if (so.kind == kOrb) {
+    b = {{-so.a, -so.a, -so.a}, {so.a, so.a, so.a}};
+  } else {
+    double rmin = so.a, rmax = so.b;
+    if (so.dphi >= kTwoPi - 1e-12) {
+      b = {{-rmax, -rmax, -so.c}, {rmax, rmax, so.c}};
+    } else {
+      // phi range in the mother frame
+      double th = std::atan2(s, c);
+      double a0 = so.sphi + th, a1 = a0 + so.dphi;
+      double xs[16], ys[16];
+      int n = 0;
+      double ang[2] = {a0, a1};
+      for (double a : ang) {
+        xs[n] = rmax * std::cos(a); ys[n++] = rmax * std::sin(a);
+        xs[n] = rmin * std::cos(a); ys[n++] = rmin * std::sin(a);
+      }
+      // axis directions inside the range
+      for (int k = -8; k <= 8; ++k) {
+        double a = k * (kTwoPi / 4.0);
+        if (a > a0 && a < a1) { xs[n] = rmax * std::cos(a); ys[n++] = rmax * std::sin(a); }
+        if (n >= 14) break;
+      }
+      b.lo[0] = b.hi[0] = xs[0];
+      b.lo[1] = b.hi[1] = ys[0];
+      for (int i = 1; i < n; ++i) {
+        b.lo[0] = std::min(b.lo[0], xs[i]); b.hi[0] = std::max(b.hi[0], xs[i]);
+        b.lo[1] = std::min(b.lo[1], ys[i]); b.hi[1] = std::max(b.hi[1], ys[i]);
+      }
+      if (rmin == 0.0) {
+        b.lo[0] = std::min(b.lo[0], 0.0); b.hi[0] = std::max(b.hi[0], 0.0);
+        b.lo[1] = std::min(b.lo[1], 0.0); b.hi[1] = std::max(b.hi[1], 0.0);
+      }
+      b.lo[2] = -so.c;
+      b.hi[2] = so.c;
+    }
+  }
+  for (int i = 0; i < 3; ++i) { b.lo[i] += t[i]; b.hi[i] += t[i]; }
+  return b;
+}
+
+// Signed outside-ness (> 0 outside, < 0 inside) of a local point; used only for validation.
+double solid_outside(const HSolid &so, const double *p) {
+  if (so.kind == kBox) {
+    return std::max({std::fabs(p[0]) - so.a, std::fabs(p[1]) - so.b, std::fabs(p[2]) - so.c});
+  }
+  if (so.kind == kOrb) return std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - so.a;
+  double r = std::hypot(p[0], p[1]);
+  double m = std::max(r - so.b, std::fabs(p[2]) - so.c);
+  if (so.a > 0.0) m = std::max(m, so.a - r);
+  if (so.dphi < kTwoPi - 1e-12) {
+    double cs = std::cos(so.sphi), ss = std::sin(so.sphi);
+    double ce = std::cos(so.sphi + so.dphi), se = std::sin(so.sphi + so.dphi);
+    double a = -(cs * p[1] - ss * p[0]), bb = -(se * p[0] - ce * p[1]);
+    m = std::max(m, so.dphi > M_PI ? std::min(a, bb) : std::max(a, bb));
+  }
+  return m;
+}
+
+// Points on the surface of a solid (local frame), for the containment check.
+void surface_samples(const HSolid &so, std::mt19937_64 &rng, int n, std::vector<double> &out) {
+  std::uniform_real_distribution<double> U(0.0, 1.0);
+  out.clear();
+  for (int i = 0; i < n; ++i) {
+    double p[3];
+    if (so.kind == kBox) {
+      double h[3] = {so.a, so.b, so.c};
+      int f = i % 6;
+      for (int k = 0; k < 3; ++k) p[k] = (2.0 * U(rng) - 1.0) * h[k];
+      p[f / 2] = (f % 2 ? -1.0 : 1.0) * h[f / 2];
+    } else if (so.kind == kOrb) {
+      double z = 2.0 * U(rng) - 1.0, ph = kTwoPi * U(rng), st = std::sqrt(std::max(0.0, 1.0 - z * z));
+      p[0] = so.a * st * std::cos(ph); p[1] = so.a * st * std::sin(ph); p[2] = so.a * z;
+    } else {
+      int f = i % 4;
+      double ph = so.sphi + so.dphi * (f == 3 ? (i % 8 < 4 ? 0.0 : 1.0) : U(rng));
+      double r = f == 0 ? so.b : (f == 1 ? so.a : so.a + (so.b - so.a) * U(rng));
+      double z = f == 2 ? ((i % 8 < 4) ? so.c : -so.c) : (2.0 * U(rng) - 1.0) * so.c;
+      p[0] = r * std::cos(ph); p[1] = r * std::sin(ph); p[2] = z;
+    }
+    out.insert(out.end(), p, p + 3);
+  }
+}
+
+void interior_samples(const HSolid &so, std::mt19937_64 &rng, int n, double margin, std::vector<double> &out) {
+  std::uniform_real_distribution<double> U(0.0, 1.0);
+  double t0[3] = {0, 0, 0};
+  Box3 e = solid_extent(so, 1.0, 0.0, t0);
+  out.clear();
+  for (int tries = 0; tries < 64 * n && (int)out.size() < 3 * n; ++tries) {
+    double p[3];
+    for (int k = 0; k < 3; ++k) p[k] = e.lo[k] + (e.hi[k] - e.lo[k]) * U(rng);
+    if (solid_outside(so, p) < -margin) out.insert(out.end(), p, p + 3);
+  }
+}
+
+// local -> mother
+void to_mother(const HPlace &pl, const double *l, double *m) {
+  m[0] = pl.c * l[0] - pl.s * l[1] + pl.t[0];
+  m[1] = pl.s * l[0] + pl.c * l[1] + pl.t[1];
+  m[2] = l[2] + pl.t[2];
+}
+
+// mother -> local
+void to_local(const HPlace &pl, const double *m, double *l) {
+  double dx = m[0] - pl.t[0], dy = m[1] - pl.t[1];
+  l[0] = pl.c * dx + pl.s * dy;
+  l[1] = -pl.s * dx + pl.c * dy;
+  l[2] = m[2] - pl.t[2];
+}
+
+int smart_levels(const g4n_voxel_params &P) { return P.n_levels > 0 ? std::min(P.n_levels, kMaxLevels) : kMaxLevels; }
+
+struct VoxBuilder {
+  HGeom &g;
+  const g4n_voxel_params &P;
+  const std::vector<Box3> &dbox;  // padded daughter extents in the mother frame
+  std::map<std::vector<int32_t>, int32_t> list_ids;
+
+  int32_t list_id(const std::vector<int32_t> &lst) {
+    auto it = list_ids.find(lst);
+    if (it != list_ids.end()) return it->second;
+    int32_t id = (int32_t)g.clist.size();
+    g.clist.push_back({(int32_t)g.cand.size(), (int32_t)lst.size()});
+    g.cand.insert(g.cand.end(), lst.begin(), lst.end());
+    list_ids.emplace(lst, id);
+    return id;
+  }
+
+  static void slice_range(const Box3 &b, int axis, double lo, double w, int n, int &k0, int &k1) {
+    k0 = (int)std::floor((b.lo[axis] - lo) / w);
+    k1 = (int)std::floor((b.hi[axis] - lo) / w);
+    k0 = std::max(0, std::min(n - 1, k0));
+    k1 = std::max(0, std::min(n - 1, k1));
+  }
+
+  int32_t build(const Box3 &region, const std::vector<int32_t> &D, int level, int used) {
+    int axis = -1, n = 1;
+    if (P.mode == 1) {
+      axis = P.axes[level];
+      n = std::max(1, P.slices[level]);
+    } else if (P.mode == 2) {
+      axis = 0;
+      n = 1;
+    } else {
+      double best = 1e300;
+      int nn = (int)std::max(1.0, std::min((double)P.max_slices, std::floor(P.smartless * (double)D.size())));
+      for (int a = 0; a < 3; ++a) {
+        if (used & (1 << a)) continue;
+        double w = (region.hi[a] - region.lo[a]) / nn;
+        if (!(w > 0.0)) continue;
+        double tot = 0.0;
+        for (int32_t d : D) {
+          int k0, k1;
+          slice_range(dbox[d], a, region.lo[a], w, nn, k0, k1);
+          tot += k1 - k0 + 1;
+        }
+        if (tot / nn < best) { best = tot / nn; axis = a; n = nn; }
+      }
+      if (axis < 0) { axis = 0; n = 1; }
+    }
+    double w = (region.hi[axis] - region.lo[axis]) / n;
+    if (!(w > 0.0)) { w = 1.0; n = 1; }
+    int32_t h = (int32_t)g.hdr.size();
+    int32_t base = (int32_t)g.slice.size();
+    g.hdr.push_back({region.lo[axis], w, 1.0 / w, axis, n, base, 0});
+    g.slice.resize(g.slice.size() + n);
+    std::vector<std::vector<int32_t>> lists(n);
+    for (int32_t d : D) {
+      int k0, k1;
+      slice_range(dbox[d], axis, region.lo[axis], w, n, k0, k1);
+      for (int k = k0; k <= k1; ++k) lists[k].push_back(d);
+    }
+    int k = 0;
+    while (k < n) {
+      int k1 = k;
+      while (k1 + 1 < n && lists[k1 + 1] == lists[k]) ++k1;
+      const std::vector<int32_t> &lst = lists[k];
+      bool refine = false;
+      if (level + 1 < kMaxLevels && !lst.empty()) {
+        if (P.mode == 1) refine = level + 1 < P.n_levels;
+        else if (P.mode == 0) refine = (int)lst.size() > P.refine_above && level + 1 < smart_levels(P);
+      }
+      int used2 = used | (1 << axis);
+      if (refine && P.mode == 0 && used2 == 7) refine = false;
+      int32_t child;
+      if (refine) {
+        Box3 sub = region;
+        sub.lo[axis] = region.lo[axis] + k * w;
+        sub.hi[axis] = region.lo[axis] + (k1 + 1) * w;
+        child = -(build(sub, lst, level + 1, used2) + 1);
+      } else {
+        child = list_id(lst);
+      }
+      for (int q = k; q <= k1; ++q) g.slice[base + q] = {child, (int16_t)k, (int16_t)k1};
+      k = k1 + 1;
+    }
+    return h;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int g4n_create(g4n_ctx **ctx_out, int device) {
+  if (!ctx_out) return G4N_ERR_ARG;
+  *ctx_out = nullptr;
+  g4n_ctx *ctx = new (std::nothrow) g4n_ctx();
+  if (!ctx) return G4N_ERR_OOM;
+  if (device == -1) {  // host-only context: builds and validates tables, never touches a GPU
+    ctx->device = -1;
+    *ctx_out = ctx;
+    return G4N_OK;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    delete ctx;
+    return G4N_ERR_CUDA;
+  }
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return G4N_ERR_CUDA; }
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc((void **)&ctx->d_geoms, kMaxGeoms * sizeof(DGeom)) != cudaSuccess) { delete ctx; return G4N_ERR_OOM; }
+  ctx->d_geoms_cap = kMaxGeoms;
+  *ctx_out = ctx;
+  return G4N_OK;
+}
+
+int g4n_destroy(g4n_ctx *ctx) {
+  if (!ctx) return G4N_OK;
+  if (ctx->device < 0) {
+    for (HGeom *g : ctx->geoms) delete g;
+    delete ctx;
+    return G4N_OK;
+  }
+  cudaSetDevice(ctx->device);
+  for (HGeom *g : ctx->geoms) {
+    if (g) { cudaFree(g->blob); delete g; }
+  }
+  cudaFree(ctx->d_geoms);
+  cudaFree(ctx->ws);
+  cudaFree(ctx->d_stage);
+  cudaFreeHost(ctx->h_stage);
+  delete ctx;
+  return G4N_OK;
+}
+
+const char *g4n_last_error(const g4n_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int g4n_set_tolerance_scale(g4n_ctx *ctx, double scale) {
+  if (!ctx) return G4N_ERR_ARG;
+  if (!(scale > 0.0 && std::isfinite(scale))) return g4n_fail(ctx, G4N_ERR_ARG, "tolerance scale must be positive");
+  if (!ctx->b.solids.empty() || !ctx->geoms.empty())
+    return g4n_fail(ctx, G4N_ERR_STATE, "tolerance scale must be set before the first solid");
+  ctx->scale = scale;
+  ctx->tol = 1e-9 * scale;
+  ctx->half = 0.5 * ctx->tol;
+  return G4N_OK;
+}
+
+int g4n_material_add(g4n_ctx *ctx, double density, int32_t n_e, const double *E, const double *mu_c, const double *mu_p,
+                     int32_t *out_mat) {
+  if (!ctx || !E || !mu_c || !mu_p || !out_mat) return g4n_fail(ctx, G4N_ERR_ARG, "material: null argument");
+  if (n_e < 2 || n_e > 4096) return g4n_fail(ctx, G4N_ERR_ARG, "material: need 2..4096 table points");
+  HMat m;
+  m.rho = density;
+  for (int i = 0; i < n_e; ++i) {
+    if (!(std::isfinite(E[i]) && E[i] > 0.0 && std::isfinite(mu_c[i]) && mu_c[i] >= 0.0 && std::isfinite(mu_p[i]) &&
+          mu_p[i] >= 0.0))
+      return g4n_fail(ctx, G4N_ERR_ARG, "material: energies must be positive and coefficients finite, >= 0");
+    if (i > 0 && !(E[i] > E[i - 1])) return g4n_fail(ctx, G4N_ERR_ARG, "material: energies must increase strictly");
+  }
+  m.E.assign(E, E + n_e);
+  m.muC.assign(mu_c, mu_c + n_e);
+  m.muP.assign(mu_p, mu_p + n_e);
+  ctx->b.mats.push_back(std::move(m));
+  *out_mat = (int32_t)ctx->b.mats.size() - 1;
+  return G4N_OK;
+}
+
+static int add_solid(g4n_ctx *ctx, const HSolid &s, int32_t *out) {
+  if (!out) return g4n_fail(ctx, G4N_ERR_ARG, "solid: null output");
+  ctx->b.solids.push_back(s);
+  *out = (int32_t)ctx->b.solids.size() - 1;
+  return G4N_OK;
+}
+
+int g4n_solid_box(g4n_ctx *ctx, double hx, double hy, double hz, int32_t *out) {
+  if (!ctx) return G4N_ERR_ARG;
+  if (!(hx > ctx->tol && hy > ctx->tol && hz > ctx->tol && std::isfinite(hx + hy + hz)))
+    return g4n_fail(ctx, G4N_ERR_ARG, "box: half-lengths must exceed the tolerance");
+  return add_solid(ctx, {kBox, hx, hy, hz, 0.0, 0.0}, out);
+}
+
+int g4n_solid_tube(g4n_ctx *ctx, double rmin, double rmax, double hz, double sphi, double dphi, int32_t *out) {
+  if (!ctx) return G4N_ERR_ARG;
+  if (!(rmin >= 0.0 && (rmin == 0.0 || rmin > ctx->tol) && rmax > rmin + ctx->tol && hz > ctx->tol &&
+        std::isfinite(rmax + hz + sphi + dphi)))
+    return g4n_fail(ctx, G4N_ERR_ARG, "tube: need 0 <= rmin < rmax, hz > tolerance");
+  if (!(dphi > 0.0 && dphi <= kTwoPi + 1e-12)) return g4n_fail(ctx, G4N_ERR_ARG, "tube: need 0 < dphi <= 2 pi");
+  return add_solid(ctx, {kTube, rmin, rmax, hz, sphi, dphi}, out);
+}
+
+int g4n_solid_orb(g4n_ctx *ctx, double r, int32_t *out) {
+  if (!ctx) return G4N_ERR_ARG;
+  if (!(r > ctx->tol && std::isfinite(r))) return g4n_fail(ctx, G4N_ERR_ARG, "orb: radius must exceed the tolerance");
+  return add_solid(ctx, {kOrb, r, 0.0, 0.0, 0.0, 0.0}, out);
+}
+
+int g4n_place(g4n_ctx *ctx, int32_t mother, int32_t solid, int32_t mat, const double *t, const double *rot,
+              int32_t *out_vol) {
+  if (!ctx || !t || !out_vol) return g4n_fail(ctx, G4N_ERR_ARG, "place: null argument");
+  auto &B = ctx->b;
+  if (solid < 0 || solid >= (int32_t)B.solids.size()) return g4n_fail(ctx, G4N_ERR_ARG, "place: bad solid id");
+  if (mat < 0 || mat >= (int32_t)B.mats.size()) return g4n_fail(ctx, G4N_ERR_ARG, "place: bad material id");
+  if (B.places.empty() ? mother != -1 : (mother < 0 || mother >= (int32_t)B.places.size()))
+    return g4n_fail(ctx, G4N_ERR_ARG, "place: the first placement is the world (mother -1), later ones need a placed mother");
+  HPlace p;
+  p.mother = mother; p.solid = solid; p.mat = mat;
+  for (int i = 0; i < 3; ++i) {
+    if (!std::isfinite(t[i])) return g4n_fail(ctx, G4N_ERR_ARG, "place: non-finite translation");
+    p.t[i] = t[i];
+  }
+  p.c = rot ? rot[0] : 1.0;
+  p.s = rot ? rot[1] : 0.0;
+  if (!(std::fabs(p.c * p.c + p.s * p.s - 1.0) <= 1e-12)) return g4n_fail(ctx, G4N_ERR_ARG, "place: rotation (cos, sin) not unit");
+  B.places.push_back(p);
+  *out_vol = (int32_t)B.places.size() - 1;
+  return G4N_OK;
+}
+
+int g4n_voxelize(g4n_ctx *ctx, const g4n_voxel_params *p) {
+  if (!ctx || !p) return g4n_fail(ctx, G4N_ERR_ARG, "voxelize: null argument");
+  if (p->mode < 0 || p->mode > 2) return g4n_fail(ctx, G4N_ERR_ARG, "voxelize: mode must be 0, 1 or 2");
+  if (p->mode == 1) {
+    if (p->n_levels < 1 || p->n_levels > kMaxLevels) return g4n_fail(ctx, G4N_ERR_ARG, "voxelize: 1..3 fixed levels");
+    int used = 0;
+    for (int l = 0; l < p->n_levels; ++l) {
+      if (p->axes[l] < 0 || p->axes[l] > 2 || (used & (1 << p->axes[l])) || p->slices[l] < 1 || p->slices[l] > 30000)
+        return g4n_fail(ctx, G4N_ERR_ARG, "voxelize: fixed levels need distinct axes and 1..30000 slices");
+      used |= 1 << p->axes[l];
+    }
+  }
+  if (p->mode == 0 && !(p->smartless > 0.0 && p->max_slices >= 1 && p->max_slices <= 30000))
+    return g4n_fail(ctx, G4N_ERR_ARG, "voxelize: smartless > 0, 1 <= max_slices <= 30000");
+  ctx->b.vox = *p;
+  ctx->b.vox_set = true;
+  return G4N_OK;
+}
+
+static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom);
+
+int g4n_geom_finalize(g4n_ctx *ctx, int32_t *out_geom) {
+  if (!ctx || !out_geom) return g4n_fail(ctx, G4N_ERR_ARG, "finalize: null argument");
+  auto &B = ctx->b;
+  const int n = (int)B.places.size();
+  if (n == 0) return g4n_fail(ctx, G4N_ERR_STATE, "finalize: no volumes placed");
+  if ((int)ctx->geoms.size() >= kMaxGeoms) return g4n_fail(ctx, G4N_ERR_ARG, "finalize: too many geometries");
+  const double tol = ctx->tol;
+  int rc = finalize_impl(ctx, out_geom);
+  if (rc != G4N_OK) B.clear();  // a rejected geometry is discarded; the next placement starts a new world
+  return rc;
+}
+
+static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
+  auto &B = ctx->b;
+  const int n = (int)B.places.size();
+  const double tol = ctx->tol;
+  HGeom *g = new HGeom();
+  // --- volume table, depth, daughter counts, composed world transforms
+  g->vol.resize(n);
+  g->wxf.resize(n);
+  std::vector<std::vector<int32_t>> dau(n);
+  for (int i = 0; i < n; ++i) {
+    const HPlace &pl = B.places[i];
+    const HSolid &so = B.solids[pl.solid];
+    DVol &v = g->vol[i];
+    std::memset(&v, 0, sizeof(v));
+    v.tx = pl.t[0]; v.ty = pl.t[1]; v.tz = pl.t[2]; v.c = pl.c; v.s = pl.s;
+    v.kind = so.kind;
+    v.mother = pl.mother;
+    v.mat = pl.mat;
+    v.vox = -1;
+    if (so.kind == kBox) { v.p[0] = so.a; v.p[1] = so.b; v.p[2] = so.c; }
+    else if (so.kind == kOrb) { v.p[0] = so.a; }
+    else {
+      v.p[0] = so.a; v.p[1] = so.b; v.p[2] = so.c;
+      v.p[3] = std::cos(so.sphi); v.p[4] = std::sin(so.sphi);
+      v.p[5] = std::cos(so.sphi + so.dphi); v.p[6] = std::sin(so.sphi + so.dphi);
+      bool seg = so.dphi < kTwoPi - 1e-12;
+      v.flags = (seg ? kSeg : 0) | (seg && so.dphi > M_PI ? kWide : 0) | (so.a > 0.0 ? kHasRmin : 0);
+    }
+    DWorld &w = g->wxf[i];
+    std::memset(&w, 0, sizeof(w));
+    if (pl.mother < 0) {
+      v.depth = 1;
+      w.tx = pl.t[0]; w.ty = pl.t[1]; w.tz = pl.t[2]; w.c = pl.c; w.s = pl.s;
+    } else {
+      const DVol &m = g->vol[pl.mother];
+      const DWorld &mw = g->wxf[pl.mother];
+      v.depth = m.depth + 1;
+      w.c = mw.c * pl.c - mw.s * pl.s;
+      w.s = mw.s * pl.c + mw.c * pl.s;
+      w.tx = mw.tx + mw.c * pl.t[0] - mw.s * pl.t[1];
+      w.ty = mw.ty + mw.s * pl.t[0] + mw.c * pl.t[1];
+      w.tz = mw.tz + pl.t[2];
+      dau[pl.mother].push_back(i);
+      g->vol[pl.mother].n_dau++;
+    }
+    if (v.depth > kDMax) {
+      delete g;
+      return g4n_fail(ctx, G4N_ERR_GEOM, "finalize: hierarchy deeper than G4N_DMAX at volume " + std::to_string(i));
+    }
+    g->max_depth = std::max(g->max_depth, v.depth);
+  }
+  // --- padded daughter extents in their mother's frame
+  const double pad = 4.0 * tol;
+  std::vector<Box3> ext(n);
+  std::vector<DBox32> &box = g->box;
+  box.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const HPlace &pl = B.places[i];
+    Box3 e = solid_extent(B.solids[pl.solid], pl.c, pl.s, pl.t);
+    for (int k = 0; k < 3; ++k) {
+      double sl = 1e-12 * (std::fabs(e.lo[k]) + std::fabs(e.hi[k]));
+      e.lo[k] -= pad + sl;
+      e.hi[k] += pad + sl;
+      box[i].lo[k] = std::nextafter((float)e.lo[k], -INFINITY);
+      box[i].hi[k] = std::nextafter((float)e.hi[k], INFINITY);
+      if ((double)box[i].lo[k] > e.lo[k]) box[i].lo[k] = std::nextafter(box[i].lo[k], -INFINITY);
+      if ((double)box[i].hi[k] < e.hi[k]) box[i].hi[k] = std::nextafter(box[i].hi[k], INFINITY);
+    }
+    box[i].pad[0] = box[i].pad[1] = 0.f;
+    ext[i] = e;
+  }
+  // --- validation: containment (surface samples) and sibling overlaps (interior samples)
+  std::mt19937_64 rng(0x9E3779B97F4A7C15ull);
+  std::vector<double> pts;
+  const double slack = 10.0 * tol;
+  for (int i = 1; i < n; ++i) {
+    const HPlace &pl = B.places[i];
+    const HPlace &mp = B.places[pl.mother];
+    const HSolid &ms = B.solids[mp.solid];
+    surface_samples(B.solids[pl.solid], rng, 48, pts);
+    for (size_t q = 0; q < pts.size(); q += 3) {
+      double m[3];
+      to_mother(pl, &pts[q], m);
+      double rel = 1e-12 * (std::fabs(m[0]) + std::fabs(m[1]) + std::fabs(m[2]));
+      if (solid_outside(ms, m) > slack + rel) {
+        delete g;
+        return g4n_fail(ctx, G4N_ERR_GEOM, "finalize: volume " + std::to_string(i) + " sticks out of its mother " +
+                                               std::to_string(pl.mother));
+      }
+    }
+  }
+  for (int m = 0; m < n; ++m) {
+    std::vector<int32_t> &D = dau[m];
+    if (D.size() < 2) continue;
+    std::vector<int32_t> order(D);
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return ext[a].lo[0] < ext[b].lo[0]; });
+    for (size_t a = 0; a < order.size(); ++a) {
+      int32_t da = order[a];
+      for (size_t bq = a + 1; bq < order.size(); ++bq) {
+        int32_t db = order[bq];
+        if (ext[db].lo[0] >= ext[da].hi[0] - 2 * pad - slack) break;
+        bool ov = true;
+        for (int k = 0; k < 3; ++k)
+          if (ext[da].hi[k] - ext[db].lo[k] <= 2 * pad + slack || ext[db].hi[k] - ext[da].lo[k] <= 2 * pad + slack) ov = false;
+        if (!ov) continue;
+        const HPlace &pa = B.places[da], &pb = B.places[db];
+        interior_samples(B.solids[pa.solid], rng, 24, slack, pts);
+        for (size_t q = 0; q < pts.size(); q += 3) {
+          double mm[3], lb[3];
+          to_mother(pa, &pts[q], mm);
+          to_local(pb, mm, lb);
+          if (solid_outside(B.solids[pb.solid], lb) < -slack) {
+            delete g;
+            return g4n_fail(ctx, G4N_ERR_GEOM, "finalize: volumes " + std::to_string(da) + " and " + std::to_string(db) +
+                                                   " overlap");
+          }
+        }
+      }
+    }
+  }
+  // --- voxels
+  g4n_voxel_params P = B.vox;
+  if (!B.vox_set) { P.mode = 0; P.n_levels = 0; P.smartless = 2.0; P.max_slices = 1000; P.refine_above = 4; }
+  for (int m = 0; m < n; ++m) {
+    if (dau[m].empty()) continue;
+    const HPlace &mp = B.places[m];
+    double zero[3] = {0, 0, 0};
+    Box3 region = solid_extent(B.solids[mp.solid], 1.0, 0.0, zero);
+    VoxBuilder vb{*g, P, ext, {}};
+    g->vol[m].vox = vb.build(region, dau[m], 0, 0);
+  }
+  if (g->clist.empty()) g->clist.push_back({0, 0});
+  if (g->cand.empty()) g->cand.push_back(-1);
+  if (g->hdr.empty()) g->hdr.push_back({0, 1, 1, 0, 1, 0, 0});
+  if (g->slice.empty()) g->slice.push_back({0, 0, 0});
+  // --- materials
+  for (const HMat &m : B.mats) {
+    g->mat_off.push_back((int32_t)g->matE.size());
+    g->mat_n.push_back((int32_t)m.E.size());
+    g->matE.insert(g->matE.end(), m.E.begin(), m.E.end());
+    g->matC.insert(g->matC.end(), m.muC.begin(), m.muC.end());
+    g->matP.insert(g->matP.end(), m.muP.begin(), m.muP.end());
+  }
+  // --- upload as one blob
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off[13], sz[13] = {g->vol.size() * sizeof(DVol), g->wxf.size() * sizeof(DWorld), g->box.size() * sizeof(DBox32),
+                            g->hdr.size() * sizeof(DVoxHdr), g->slice.size() * sizeof(DVoxSlice),
+                            g->clist.size() * sizeof(DCandList), g->cand.size() * sizeof(int32_t),
+                            g->matE.size() * sizeof(double), g->matC.size() * sizeof(double), g->matP.size() * sizeof(double),
+                            g->mat_off.size() * sizeof(int32_t), g->mat_n.size() * sizeof(int32_t), 0};
+  const void *src[12] = {g->vol.data(), g->wxf.data(), g->box.data(), g->hdr.data(), g->slice.data(), g->clist.data(),
+                         g->cand.data(), g->matE.data(), g->matC.data(), g->matP.data(), g->mat_off.data(), g->mat_n.data()};
+  size_t total = 0;
+  for (int k = 0; k < 12; ++k) { off[k] = total; total += al(std::max<size_t>(sz[k], 8)); }
+  if (ctx->device < 0) {  // host-only context: keep the host tables
+    g->blob_bytes = total;
+    g->dview.n_vol = n;
+    g->dview.n_mat = (int32_t)B.mats.size();
+    g->dview.tol = tol;
+    g->dview.half = 0.5 * tol;
+    ctx->geoms.push_back(g);
+    B.clear();
+    *out_geom = (int32_t)ctx->geoms.size() - 1;
+    return G4N_OK;
+  }
+  cudaSetDevice(ctx->device);
+  if (cudaMalloc(&g->blob, total) != cudaSuccess) {
+    delete g;
+    return g4n_fail(ctx, G4N_ERR_OOM, "finalize: device allocation of the geometry tables failed");
+  }
+  g->blob_bytes = total;
+  char *base = (char *)g->blob;
+  for (int k = 0; k < 12; ++k) {
+    if (sz[k] && cudaMemcpy(base + off[k], src[k], sz[k], cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(g->blob);
+      delete g;
+      return g4n_fail(ctx, G4N_ERR_CUDA, "finalize: upload failed");
+    }
+  }
+  DGeom &d = g->dview;
+  d.vol = (const DVol *)(base + off[0]);
+  d.wxf = (const DWorld *)(base + off[1]);
+  d.box = (const DBox32 *)(base + off[2]);
+  d.hdr = (const DVoxHdr *)(base + off[3]);
+  d.slice = (const DVoxSlice *)(base + off[4]);
+  d.clist = (const DCandList *)(base + off[5]);
+  d.cand = (const int32_t *)(base + off[6]);
+  d.matE = (const double *)(base + off[7]);
+  d.matC = (const double *)(base + off[8]);
+  d.matP = (const double *)(base + off[9]);
+  d.mat_off = (const int32_t *)(base + off[10]);
+  d.mat_n = (const int32_t *)(base + off[11]);
+  d.n_vol = n;
+  d.n_mat = (int32_t)B.mats.size();
+  d.tol = tol;
+  d.half = 0.5 * tol;
+  int32_t gid = (int32_t)ctx->geoms.size();
+  if (cudaMemcpy(ctx->d_geoms + gid, &d, sizeof(DGeom), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(g->blob);
+    delete g;
+    return g4n_fail(ctx, G4N_ERR_CUDA, "finalize: directory upload failed");
+  }
+  ctx->geoms.push_back(g);
+  B.clear();
+  *out_geom = gid;
+  return G4N_OK;
+}
+
+int g4n_geom_info(g4n_ctx *ctx, int32_t geom, int64_t *out8) {
+  if (!ctx || !out8 || geom < 0 || geom >= (int32_t)ctx->geoms.size()) return g4n_fail(ctx, G4N_ERR_ARG, "geom_info: bad id");
+  const HGeom *g = ctx->geoms[geom];
+  out8[0] = (int64_t)g->vol.size();
+  out8[1] = (int64_t)g->hdr.size();
+  out8[2] = (int64_t)g->slice.size();
+  out8[3] = (int64_t)g->clist.size();
+  out8[4] = (int64_t)g->cand.size();
+  out8[5] = (int64_t)g->blob_bytes;
+  out8[6] = g->max_depth;
+  out8[7] = (int64_t)g->mat_n.size();
+  return G4N_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,650 @@
+// nav_kernels.cu -- sm_103a kernels and their C-ABI entry points: locate,
+// compute_step and the persistent transport kernel (Algorithm 1 with Compton
+// scattering, photoabsorption and energy deposits), plus g4n_sync.
+//
+// Transport design: one persistent grid sized to fill every SM; each lane
+// carries one track in registers for its whole history (SoA state never
+// round-trips through HBM).  A warp refills its idle lanes from one global
+// queue head with a single atomicAdd per refill (__ballot_sync/__popc), so
+// uneven history lengths and uneven geometries share one launch (the
+// periodic compaction/refill of Sec. 5, done per step in-warp).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "g4n_internal.h"
+#include "nav_device.cuh"
+
+using namespace g4n;
+using namespace g4n::dev;
+
+namespace g4n {
+
+// Device copy of one work item.
+struct DItem {
+  int32_t geom, pad;
+  int64_t n, tid0, tally_off, start;
+  double src[16];  // pos[3], sigma, has_z, z0, z1, iso, dir[3], e_kind, e0, e1, -
+};
+
+enum StatusBits : uint32_t { kStStepLimit = 1u, kStTimeout = 2u, kStRejection = 4u, kStBadInput = 8u };
+
+struct Workspace {
+  unsigned long long q_head;
+  uint32_t status;
+  uint32_t pad[13];
+};
+
+}  // namespace g4n
+
+namespace {
+
+constexpr double kMeC2 = 0.51099895;
+constexpr int kEvNone = 0, kEvPhoto = 1, kEvCompton = 2, kEvCutoff = 3, kEvEscape = 4, kEvPush = 5, kEvStepLimit = 6;
+constexpr int kLimPush = -3, kLimStepLimit = -4;
+constexpr uint64_t kFnvOffset = 0xcbf29ce484222325ull;
+
+__device__ __forceinline__ bool bad_dir(const V3 &u) {
+  const double n2 = u.x * u.x + u.y * u.y + u.z * u.z;
+  return !(fabs(n2 - 1.0) <= 1e-6);
+}
+
+__device__ __forceinline__ void flag(uint32_t *status, uint32_t bits) { atomicOr(status, bits); }
+
+// ---------------------------------------------------------------- locate
+
+__global__ void __launch_bounds__(128) k_locate(const DGeom *__restrict__ geoms, int gid, int64_t n,
+                                                const double *__restrict__ pos, const double *__restrict__ dir,
+                                                int32_t *__restrict__ out_depth, int32_t *__restrict__ out_path,
+                                                uint32_t *status) {
+  const DGeom &G = geoms[gid];
+  Counters cnt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const V3 x{pos[i], pos[n + i], pos[2 * n + i]};
+    const V3 u{dir[i], dir[n + i], dir[2 * n + i]};
+    int leaf = -2;
+    if (bad_dir(u) || !isfinite(x.x + x.y + x.z)) flag(status, kStBadInput);
+    else leaf = locate_world(G, x, u, cnt);
+    int depth = leaf >= 0 ? G.vol[leaf].depth : (leaf == -1 ? 0 : -1);
+    out_depth[i] = depth;
+    int v = leaf;
+    for (int k = kDMax - 1; k >= 0; --k) {
+      if (k < depth) {
+        out_path[k * n + i] = v;
+        v = G.vol[v].mother;
+      } else {
+        out_path[k * n + i] = -1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- compute_step
+
+__global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ geoms, int gid, int64_t n,
+                                                      const double *__restrict__ pos, const double *__restrict__ dir,
+                                                      const int32_t *__restrict__ depth, const int32_t *__restrict__ path,
+                                                      const double *__restrict__ proposed, double *__restrict__ out_step,
+                                                      double *__restrict__ out_safety, int32_t *__restrict__ out_lim,
+                                                      uint32_t *status) {
+  const DGeom &G = geoms[gid];
+  Counters cnt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const V3 x{pos[i], pos[n + i], pos[2 * n + i]};
+    const V3 u{dir[i], dir[n + i], dir[2 * n + i]};
+    const int d = depth[i];
+    const int leaf = (d >= 1 && d <= kDMax) ? path[(int64_t)(d - 1) * n + i] : -1;
+    if (bad_dir(u) || leaf < 0 || leaf >= G.n_vol || G.vol[leaf].depth != d) {
+      flag(status, kStBadInput);
+      out_step[i] = nan("");
+      out_safety[i] = nan("");
+      out_lim[i] = INT32_MIN;
+      continue;
+    }
+    const double prop = proposed ? proposed[i] : kInf;
+    V3 p, v;
+    world_to_local(G.wxf[leaf], x, u, p, v);
+    int lim;
+    double saf;
+    bool timeout = false;
+    double s = geom_step(G, leaf, p, v, prop, &lim, &saf, true, cnt, &timeout);
+    if (timeout) flag(status, kStTimeout);
+    if (prop < s) {
+      s = prop;
+      lim = G4N_LIM_PHYSICS;
+    }
+    out_step[i] = s;
+    out_safety[i] = saf;
+    out_lim[i] = lim;
+  }
+}
+
+// ---------------------------------------------------------------- transport
+
+struct Track {
+  V3 x, u;
+  double E, Y, len, safety, mu, mupe;
+  uint64_t h;
+  int64_t tid, gidx;
+  int leaf, item, steps, nzero;
+  uint32_t draw;
+};
+
+struct TParams {
+  const DGeom *geoms;
+  const DItem *items;
+  int n_items;
+  int64_t total;
+  unsigned long long *q_head;
+  uint32_t *status;
+  uint64_t seed;
+  double cutoff;
+  int64_t max_steps;
+  int nb;
+  int64_t stride;
+  double *edep;
+  unsigned long long *counters;
+  uint64_t *out_hash;
+  double *out_len;
+};
+
+__device__ __forceinline__ int find_item(const DItem *items, int n_items, int64_t g) {
+  int lo = 0, hi = n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].start <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Unit-disc rejection: (cos, sin) of a uniform azimuth.
+__device__ __forceinline__ bool disc_azimuth(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw, double &c,
+                                             double &s) {
+#pragma unroll 1
+  for (int t = 0; t < 1000; ++t) {
+    const double a = 2.0 * philox_uniform(seed, tid, stream, draw) - 1.0;
+    const double b = 2.0 * philox_uniform(seed, tid, stream, draw) - 1.0;
+    const double r2 = a * a + b * b;
+    if (r2 > 0.0 && r2 <= 1.0) {
+      c = (a * a - b * b) / r2;
+      s = 2.0 * a * b / r2;
+      return true;
+    }
+  }
+  c = 1.0;
+  s = 0.0;
+  return false;
+}
+
+// Source of track tid (stream 0).
+__device__ void make_source(const double *src, uint64_t seed, int64_t tid, V3 &x, V3 &u, double &E, uint32_t *status) {
+  uint32_t draw = 0;
+  x = V3{src[0], src[1], src[2]};
+  if (src[3] > 0.0) {
+    bool ok = false;
+#pragma unroll 1
+    for (int t = 0; t < 1000; ++t) {
+      const double a = 2.0 * philox_uniform(seed, tid, 0, draw) - 1.0;
+      const double b = 2.0 * philox_uniform(seed, tid, 0, draw) - 1.0;
+      const double s = a * a + b * b;
+      if (s > 0.0 && s < 1.0) {
+        const double f = sqrt(-2.0 * log(s) / s);
+        x.x += src[3] * (a * f);
+        x.y += src[3] * (b * f);
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) flag(status, kStRejection);
+  }
+  if (src[4] != 0.0) x.z = src[5] + (src[6] - src[5]) * philox_uniform(seed, tid, 0, draw);
+  if (src[7] != 0.0) {
+    const double ct = 2.0 * philox_uniform(seed, tid, 0, draw) - 1.0;
+    double cph, sph;
+    if (!disc_azimuth(seed, tid, 0, draw, cph, sph)) flag(status, kStRejection);
+    const double st = sqrt(fmax(0.0, (1.0 - ct) * (1.0 + ct)));
+    u = V3{st * cph, st * sph, ct};
+  } else {
+    u = V3{src[8], src[9], src[10]};
+  }
+  const int ek = (int)src[11];
+  if (ek == 0) E = src[12];
+  else if (ek == 1) E = src[12] + (src[13] - src[12]) * philox_uniform(seed, tid, 0, draw);
+  else E = src[12] * exp(philox_uniform(seed, tid, 0, draw) * log(src[13] / src[12]));
+}
+
+__device__ __forceinline__ void tally(const TParams &P, const Track &t, int col, double e) {
+  const DItem &it = P.items[t.item];
+  atomicAdd(&P.edep[(t.tid % P.nb) * P.stride + it.tally_off + col], e);
+}
+
+__device__ __forceinline__ void finish(const TParams &P, const Track &t) {
+  if (P.out_hash) P.out_hash[t.gidx] = t.h;
+  if (P.out_len) P.out_len[t.gidx] = t.len;
+}
+
+// Start track number g of the concatenated items; false if it ended at once (outside the world).
+__device__ bool start_track(const TParams &P, int64_t g, Track &t, Counters &cnt) {
+  t.gidx = g;
+  t.item = find_item(P.items, P.n_items, g);
+  const DItem &it = P.items[t.item];
+  t.tid = it.tid0 + (g - it.start);
+  const DGeom &G = P.geoms[it.geom];
+  make_source(it.src, P.seed, t.tid, t.x, t.u, t.E, P.status);
+  tally(P, t, G.n_vol + 1, t.E);
+  cnt.c[G4N_C_TRACKS]++;
+  t.h = kFnvOffset;
+  t.len = 0.0;
+  t.steps = 0;
+  t.nzero = 0;
+  t.safety = 0.0;
+  t.leaf = locate_world(G, t.x, t.u, cnt);
+  if (t.leaf < 0) {
+    cnt.c[G4N_C_ESCAPED]++;
+    tally(P, t, G.n_vol, t.E);
+    t.h = hash_step(t.h, -1, G4N_LIM_MOTHER, kEvEscape);
+    finish(P, t);
+    return false;
+  }
+  t.draw = 0;
+  t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
+  mu_lookup(G, G.vol[t.leaf].mat, t.E, t.mu, t.mupe);
+  return true;
+}
+
+// Kahn's rejection method for the Klein-Nishina law of eta = E / E'.
+__device__ __forceinline__ bool kahn(double E, uint64_t seed, int64_t tid, uint32_t &draw, double &eta, double &cost) {
+  const double al = E / kMeC2;
+  const double p1 = (1.0 + 2.0 * al) / (9.0 + 2.0 * al);
+#pragma unroll 1
+  for (int t = 0; t < 1000; ++t) {
+    const double r1 = philox_uniform(seed, tid, 1, draw);
+    const double r2 = philox_uniform(seed, tid, 1, draw);
+    const double r3 = philox_uniform(seed, tid, 1, draw);
+    if (r1 <= p1) {
+      eta = 1.0 + 2.0 * al * r2;
+      if (!(r3 <= 4.0 * (1.0 / eta - 1.0 / (eta * eta)))) continue;
+      cost = 1.0 - (eta - 1.0) / al;
+    } else {
+      eta = (1.0 + 2.0 * al) / (1.0 + 2.0 * al * r2);
+      cost = 1.0 - (eta - 1.0) / al;
+      if (!(r3 <= 0.5 * (cost * cost + 1.0 / eta))) continue;
+    }
+    return true;
+  }
+  eta = 1.0;
+  cost = 1.0;
+  return false;
+}
+
+// New direction at polar cosine ct and azimuth (cph, sph) about u.
+__device__ __forceinline__ void deflect(V3 &u, double ct, double cph, double sph) {
+  const double st = sqrt(fmax(0.0, (1.0 - ct) * (1.0 + ct)));
+  const double dx = st * cph, dy = st * sph, dz = ct;
+  const double perp2 = u.x * u.x + u.y * u.y;
+  if (perp2 > 0.0) {
+    const double perp = sqrt(perp2);
+    const double nx = (u.x * u.z * dx - u.y * dy) / perp + u.x * dz;
+    const double ny = (u.y * u.z * dx + u.x * dy) / perp + u.y * dz;
+    const double nz = -perp * dx + u.z * dz;
+    u = V3{nx, ny, nz};
+  } else if (u.z >= 0.0) {
+    u = V3{dx, dy, dz};
+  } else {
+    u = V3{dx, -dy, -dz};
+  }
+}
+
+// One step of Algorithm 1 for one track; returns false when the history ended.
+__device__ bool step_track(const TParams &P, Track &t, Counters &cnt) {
+  const DItem &it = P.items[t.item];
+  const DGeom &G = P.geoms[it.geom];
+  if (t.steps >= P.max_steps) {
+    cnt.c[G4N_C_STEP_LIMIT]++;
+    flag(P.status, kStStepLimit);
+    t.h = hash_step(t.h, t.leaf, kLimStepLimit, kEvStepLimit);
+    finish(P, t);
+    return false;
+  }
+  const double sphys = t.mu > 0.0 ? t.Y / t.mu : kInf;
+  double s;
+  int lim = G4N_LIM_PHYSICS;
+  bool geo;
+  if (sphys < t.safety) {
+    s = sphys;
+    geo = false;
+    cnt.c[G4N_C_SAFETY_SKIPS]++;
+  } else {
+    V3 p, v;
+    world_to_local(G.wxf[t.leaf], t.x, t.u, p, v);
+    double saf;
+    bool timeout = false;
+    const double sg = geom_step(G, t.leaf, p, v, sphys, &lim, &saf, true, cnt, &timeout);
+    if (timeout) flag(P.status, kStTimeout);
+    t.safety = saf;
+    geo = sg <= sphys;
+    s = geo ? sg : sphys;
+  }
+  ++t.steps;
+  cnt.c[G4N_C_STEPS]++;
+  t.x.x += s * t.u.x;
+  t.x.y += s * t.u.y;
+  t.x.z += s * t.u.z;
+  t.len += s;
+  if (geo) {
+    if (t.mu > 0.0) t.Y = fmax(t.Y - s * t.mu, 0.0);
+    cnt.c[G4N_C_GEOM_STEPS]++;
+    t.safety = 0.0;
+    int leaf = relocate(G, t.leaf, t.x, t.u, cnt);
+    t.nzero = (s <= G.half) ? t.nzero + 1 : 0;
+    if (leaf >= 0 && t.nzero >= 10) {
+      const double push = 100.0 * G.tol;
+      t.x.x += push * t.u.x;
+      t.x.y += push * t.u.y;
+      t.x.z += push * t.u.z;
+      t.len += push;
+      cnt.c[G4N_C_PUSHES]++;
+      t.nzero = 0;
+      leaf = relocate(G, leaf, t.x, t.u, cnt);
+      t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
+    }
+    if (leaf < 0) {
+      cnt.c[G4N_C_ESCAPED]++;
+      tally(P, t, G.n_vol, t.E);
+      t.h = hash_step(t.h, -1, lim, kEvEscape);
+      finish(P, t);
+      return false;
+    }
+    t.leaf = leaf;
+    t.h = hash_step(t.h, leaf, lim, kEvNone);
+    mu_lookup(G, G.vol[leaf].mat, t.E, t.mu, t.mupe);
+    return true;
+  }
+  // interaction at the end of the free path
+  t.safety = fmax(t.safety - s, 0.0);
+  t.nzero = 0;
+  cnt.c[G4N_C_PHYS_STEPS]++;
+  const double U = philox_uniform(P.seed, t.tid, 1, t.draw);
+  if (U * t.mu < t.mupe) {
+    cnt.c[G4N_C_PHOTO]++;
+    tally(P, t, t.leaf, t.E);
+    t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvPhoto);
+    finish(P, t);
+    return false;
+  }
+  cnt.c[G4N_C_COMPTON]++;
+  double eta, cost, cph, sph;
+  bool ok = kahn(t.E, P.seed, t.tid, t.draw, eta, cost);
+  ok &= disc_azimuth(P.seed, t.tid, 1, t.draw, cph, sph);
+  if (!ok) flag(P.status, kStRejection);
+  deflect(t.u, cost, cph, sph);
+  const double E1 = t.E / eta;
+  if (E1 < P.cutoff) {
+    cnt.c[G4N_C_CUTOFF]++;
+    tally(P, t, t.leaf, t.E);
+    t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCutoff);
+    finish(P, t);
+    return false;
+  }
+  tally(P, t, t.leaf, t.E - E1);
+  t.E = E1;
+  t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
+  t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCompton);
+  mu_lookup(G, G.vol[t.leaf].mat, t.E, t.mu, t.mupe);
+  return true;
+}
+
+__global__ void __launch_bounds__(128) k_transport(const TParams P) {
+  Counters cnt;
+#pragma unroll
+  for (int k = 0; k < G4N_N_COUNTERS; ++k) cnt.c[k] = 0;
+  const unsigned lane = threadIdx.x & 31u;
+  Track t;
+  bool active = false, drained = false;
+#pragma unroll 1
+  for (;;) {
+    // refill idle lanes from the device queue: one atomic per warp
+    const unsigned idle = __ballot_sync(0xffffffffu, !active);
+    if (idle && !drained) {
+      const int leader = __ffs(idle) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(P.q_head, (unsigned long long)__popc(idle));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (base + __popc(idle) >= (unsigned long long)P.total) drained = true;
+      if (!active) {
+        const int64_t g = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
+        if (g < P.total) active = start_track(P, g, t, cnt);
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) {
+      if (drained) break;
+      continue;
+    }
+    if (active) active = step_track(P, t, cnt);
+  }
+  // flush counters: warp reduction, one atomic per counter per warp
+#pragma unroll
+  for (int k = 0; k < G4N_N_COUNTERS; ++k) {
+    unsigned long long v = cnt.c[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(&P.counters[k], v);
+  }
+}
+
+// ---------------------------------------------------------------- host helpers
+
+int check_geom(g4n_ctx *ctx, int32_t geom) {
+  if (!ctx) return G4N_ERR_ARG;
+  if (ctx->device < 0) return g4n_fail(ctx, G4N_ERR_STATE, "host-only context: no device queries");
+  if (geom < 0 || geom >= (int32_t)ctx->geoms.size()) return g4n_fail(ctx, G4N_ERR_ARG, "unknown geometry id");
+  return G4N_OK;
+}
+
+int ensure_ws(g4n_ctx *ctx, size_t item_bytes) {
+  const size_t need = sizeof(Workspace) + item_bytes;
+  if (ctx->ws && ctx->ws_bytes >= need) return G4N_OK;
+  if (ctx->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+  }
+  size_t bytes = std::max<size_t>(need, 1 << 16);
+  if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_OOM, "workspace allocation failed");
+  if (cudaMemset(ctx->ws, 0, sizeof(Workspace)) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_CUDA, "workspace init failed");
+  ctx->ws_bytes = bytes;
+  return G4N_OK;
+}
+
+int launch_error(g4n_ctx *ctx, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return g4n_fail(ctx, G4N_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return G4N_OK;
+}
+
+int grid_for(g4n_ctx *ctx, int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  int64_t cap = (int64_t)ctx->sm_count * 16;
+  return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+}  // namespace
+
+extern "C" {
+
+int g4n_locate(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, const double *dir, int32_t *out_depth,
+               int32_t *out_path, g4n_stream stream) {
+  int rc = check_geom(ctx, geom);
+  if (rc) return rc;
+  if (n < 0) return g4n_fail(ctx, G4N_ERR_ARG, "locate: n < 0");
+  if (n == 0) return G4N_OK;
+  if (!pos || !dir || !out_depth || !out_path) return g4n_fail(ctx, G4N_ERR_ARG, "locate: null array");
+  if ((rc = ensure_ws(ctx, 0))) return rc;
+  cudaSetDevice(ctx->device);
+  Workspace *ws = (Workspace *)ctx->ws;
+  k_locate<<<grid_for(ctx, n, 128), 128, 0, (cudaStream_t)stream>>>(ctx->d_geoms, geom, n, pos, dir, out_depth,
+                                                                     out_path, &ws->status);
+  return launch_error(ctx, "locate launch");
+}
+
+int g4n_compute_step(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, const double *dir, const int32_t *depth,
+                     const int32_t *path, const double *proposed, double *out_step, double *out_safety,
+                     int32_t *out_limiter, int32_t mode, g4n_stream stream) {
+  int rc = check_geom(ctx, geom);
+  if (rc) return rc;
+  if (n < 0) return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: n < 0");
+  if (mode != G4N_MODE_FP64) return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: mode not available");
+  if (n == 0) return G4N_OK;
+  if (!pos || !dir || !depth || !path || !out_step || !out_safety || !out_limiter)
+    return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: null array");
+  if ((rc = ensure_ws(ctx, 0))) return rc;
+  cudaSetDevice(ctx->device);
+  Workspace *ws = (Workspace *)ctx->ws;
+  k_compute_step<<<grid_for(ctx, n, 128), 128, 0, (cudaStream_t)stream>>>(
+      ctx->d_geoms, geom, n, pos, dir, depth, path, proposed, out_step, out_safety, out_limiter, &ws->status);
+  return launch_error(ctx, "compute_step launch");
+}
+
+int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, uint64_t *out_counters,
+                        uint64_t *out_track_hash, double *out_track_len, g4n_stream stream) {
+  if (!ctx || !b) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null argument");
+  if (b->n_items < 1 || !b->items) return g4n_fail(ctx, G4N_ERR_ARG, "transport: no work items");
+  if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null output");
+  if (b->mode != G4N_MODE_FP64) return g4n_fail(ctx, G4N_ERR_ARG, "transport: mode not available");
+  if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport: n_tally_batches < 1");
+  if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: cutoff must be >= 0");
+  std::vector<DItem> items(b->n_items);
+  int64_t total = 0;
+  for (int i = 0; i < b->n_items; ++i) {
+    const g4n_work_item &w = b->items[i];
+    int rc = check_geom(ctx, w.geom);
+    if (rc) return rc;
+    const int64_t nv = ctx->geoms[w.geom]->dview.n_vol;
+    if (w.n_tracks < 0 || w.track_id0 < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: negative track count or id");
+    if (w.tally_offset < 0 || w.tally_offset + nv + 2 > b->tally_stride)
+      return g4n_fail(ctx, G4N_ERR_ARG, "transport: tally columns out of range");
+    const g4n_source &s = w.source;
+    if (!s.isotropic) {
+      const double n2 = s.dir[0] * s.dir[0] + s.dir[1] * s.dir[1] + s.dir[2] * s.dir[2];
+      if (!(std::fabs(n2 - 1.0) <= 1e-12)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: source direction not unit");
+    }
+    if (s.e_kind < 0 || s.e_kind > 2 || !(s.e0 > 0.0) || (s.e_kind > 0 && !(s.e1 >= s.e0)))
+      return g4n_fail(ctx, G4N_ERR_ARG, "transport: bad source energy");
+    if (!(s.spot_sigma >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: negative spot sigma");
+    DItem &d = items[i];
+    std::memset(&d, 0, sizeof(d));
+    d.geom = w.geom;
+    d.n = w.n_tracks;
+    d.tid0 = w.track_id0;
+    d.tally_off = w.tally_offset;
+    d.start = total;
+    double src[16] = {s.pos[0], s.pos[1], s.pos[2], s.spot_sigma, (double)(s.has_z != 0), s.z0, s.z1,
+                      (double)(s.isotropic != 0), s.dir[0], s.dir[1], s.dir[2], (double)s.e_kind, s.e0, s.e1, 0.0, 0.0};
+    std::memcpy(d.src, src, sizeof(src));
+    total += w.n_tracks;
+  }
+  if (total == 0) return G4N_OK;
+  int rc = ensure_ws(ctx, items.size() * sizeof(DItem));
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace *ws = (Workspace *)ctx->ws;
+  DItem *d_items = (DItem *)((char *)ctx->ws + sizeof(Workspace));
+  if (cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(DItem), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(&ws->q_head, 0, sizeof(unsigned long long), st) != cudaSuccess)
+    return g4n_fail(ctx, G4N_ERR_CUDA, "transport: item upload failed");
+  TParams P;
+  P.geoms = ctx->d_geoms;
+  P.items = d_items;
+  P.n_items = b->n_items;
+  P.total = total;
+  P.q_head = &ws->q_head;
+  P.status = &ws->status;
+  P.seed = b->seed;
+  P.cutoff = b->cutoff;
+  P.max_steps = b->max_steps > 0 ? b->max_steps : 1000000;
+  P.nb = b->n_tally_batches;
+  P.stride = b->tally_stride;
+  P.edep = out_edep;
+  P.counters = (unsigned long long *)out_counters;
+  P.out_hash = out_track_hash;
+  P.out_len = out_track_len;
+  const int block = b->block_size > 0 ? b->block_size : 128;
+  if (block % 32 || block > 128) return g4n_fail(ctx, G4N_ERR_ARG, "transport: block_size must be a multiple of 32, <= 128");
+  int per_sm = b->blocks_per_sm;
+  if (per_sm <= 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport, block, 0);
+    per_sm = std::max(per_sm, 1);
+  }
+  int64_t grid = (int64_t)ctx->sm_count * per_sm;
+  const int64_t need = (total + block - 1) / block;
+  grid = std::max<int64_t>(1, std::min(grid, need));
+  k_transport<<<(int)grid, block, 0, st>>>(P);
+  return launch_error(ctx, "transport launch");
+}
+
+int g4n_transport_batch_host(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, uint64_t *out_counters,
+                             uint64_t *out_track_hash, double *out_track_len, g4n_stream stream) {
+  if (!ctx || !b || !out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport_host: null argument");
+  if (ctx->device < 0) return g4n_fail(ctx, G4N_ERR_STATE, "host-only context: no device queries");
+  int64_t total = 0;
+  for (int i = 0; i < b->n_items && b->items; ++i) total += std::max<int64_t>(0, b->items[i].n_tracks);
+  const size_t e_bytes = (size_t)b->n_tally_batches * (size_t)std::max<int64_t>(b->tally_stride, 0) * sizeof(double);
+  const size_t c_bytes = G4N_N_COUNTERS * sizeof(uint64_t);
+  const size_t h_bytes = out_track_hash ? (size_t)total * sizeof(uint64_t) : 0;
+  const size_t l_bytes = out_track_len ? (size_t)total * sizeof(double) : 0;
+  const size_t need = e_bytes + c_bytes + h_bytes + l_bytes + 4 * 256;
+  cudaSetDevice(ctx->device);
+  if (ctx->d_stage_bytes < need) {
+    cudaDeviceSynchronize();
+    cudaFree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    ctx->d_stage_bytes = 0;
+    if (cudaMalloc(&ctx->d_stage, need) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_OOM, "transport_host: staging allocation failed");
+    ctx->d_stage_bytes = need;
+  }
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  char *base = (char *)ctx->d_stage;
+  double *d_e = (double *)base;
+  uint64_t *d_c = (uint64_t *)(base + al(e_bytes));
+  uint64_t *d_h = out_track_hash ? (uint64_t *)(base + al(e_bytes) + al(c_bytes)) : nullptr;
+  double *d_l = out_track_len ? (double *)(base + al(e_bytes) + al(c_bytes) + al(h_bytes)) : nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_e, 0, e_bytes, st) != cudaSuccess || cudaMemsetAsync(d_c, 0, c_bytes, st) != cudaSuccess)
+    return g4n_fail(ctx, G4N_ERR_CUDA, "transport_host: clear failed");
+  int rc = g4n_transport_batch(ctx, b, d_e, d_c, d_h, d_l, stream);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(out_edep, d_e, e_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(out_counters, d_c, c_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      (d_h && cudaMemcpyAsync(out_track_hash, d_h, h_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+      (d_l && cudaMemcpyAsync(out_track_len, d_l, l_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+    return g4n_fail(ctx, G4N_ERR_CUDA, "transport_host: copy back failed");
+  return g4n_sync(ctx, stream);
+}
+
+int g4n_sync(g4n_ctx *ctx, g4n_stream stream) {
+  if (!ctx) return G4N_ERR_ARG;
+  if (ctx->device < 0) return G4N_OK;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return g4n_fail(ctx, G4N_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+  if (!ctx->ws) return G4N_OK;
+  uint32_t st = 0;
+  Workspace *ws = (Workspace *)ctx->ws;
+  if (cudaMemcpy(&st, &ws->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return g4n_fail(ctx, G4N_ERR_CUDA, "sync: status read failed");
+  if (st == 0) return G4N_OK;
+  cudaMemset(&ws->status, 0, sizeof(uint32_t));
+  if (st & kStBadInput) return g4n_fail(ctx, G4N_ERR_ARG, "device: non-unit/non-finite direction or bad path/depth input");
+  if (st & kStTimeout) return g4n_fail(ctx, G4N_ERR_TIMEOUT, "device: a voxel walk reached its iteration cap");
+  if (st & kStRejection) return g4n_fail(ctx, G4N_ERR_TIMEOUT, "device: a rejection sampler reached its trial cap");
+  if (st & kStStepLimit) return g4n_fail(ctx, G4N_ERR_STEP_LIMIT, "device: a track reached the per-track step cap");
+  return g4n_fail(ctx, G4N_ERR_STATE, "device: unknown status");
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+"""Shared helpers of the GPU parity tests: one library context per session,
+seeded query generation, and the scene workloads used in the parity cases."""
+import math
+
+import numpy as np
+
+import oracle
+import synth
+from synth.scenes import Scene, Solid, Placement, VoxelSpec, BOX, TUBE, ORB
+from synth.materials import toy_materials
+
+
+def world_half(scene):
+    return np.array(scene.solids[scene.placements[0].solid].params[:3]) if scene.solids[0].kind == BOX else None
+
+
+def mixed_scene(seed=5, n=120, half=300.0, voxel=None):
+    rng = np.random.default_rng(seed)
+    m = toy_materials()
+    dsol, dpl = synth.scenes.random_world(rng, n, world_half=half, fill=0.15)
+    solids = [Solid(BOX, (half, half, half))] + dsol
+    places = [Placement(-1, 0, 0, (0, 0, 0))] + [Placement(0, i + 1, 1 + i % 3, t, rot) for i, (t, rot) in enumerate(dpl)]
+    return Scene("mixed", [m["water"], m["lead"], m["scint"], m["al"]], solids, places, voxel or VoxelSpec(mode="smart"))
+
+
+def nested_scene():
+    """World + 7 nested levels (box > tube > orb > box > ...), each holder rotated about z, with a small
+    sibling beside every holder and a wide tube segment beside the tube holders: the maximum depth."""
+    m = toy_materials()
+    mats = [m["water"], m["lead"], m["scint"], m["al"]]
+    S = 400.0
+    solids = [Solid(BOX, (S, S, S))]
+    places = [Placement(-1, 0, 0, (0, 0, 0))]
+    mother, mkind, size = 0, BOX, S
+    for lev in range(7):
+        th = 0.3 * (lev + 1)
+        rot = (math.cos(th), math.sin(th))
+        if mkind == BOX:        # tube holder in a box mother, sibling boxes in the corners
+            hold = Solid(TUBE, (0.0, 0.6 * size, 0.6 * size, 0.0, 2 * math.pi))
+            sib = [(Solid(BOX, (0.05 * size,) * 3), (0.85 * size, 0.85 * size, 0.0)),
+                   (Solid(TUBE, (0.02 * size, 0.1 * size, 0.1 * size, 0.3, 4.5)), (-0.8 * size, -0.8 * size, 0.0))]
+            nkind, nsize = TUBE, 0.6 * size
+        elif mkind == TUBE:     # orb holder in a tube mother, sibling on the axis
+            hold = Solid(ORB, (0.55 * size,))
+            sib = [(Solid(BOX, (0.05 * size,) * 3), (0.0, 0.0, 0.8 * size))]
+            nkind, nsize = ORB, 0.55 * size
+        else:                   # box holder in an orb mother
+            hold = Solid(BOX, (0.5 * size,) * 3)
+            sib = [(Solid(BOX, (0.05 * size,) * 3), (0.0, 0.0, 0.75 * size))]
+            nkind, nsize = BOX, 0.5 * size
+        solids.append(hold)
+        places.append(Placement(mother, len(solids) - 1, (lev + 1) % 4, (0.0, 0.0, 0.0), rot))
+        holder = len(places) - 1
+        for k, (so, t) in enumerate(sib):
+            solids.append(so)
+            places.append(Placement(mother, len(solids) - 1, (lev + 2 + k) % 4, t, (math.cos(0.7 * k), math.sin(0.7 * k))))
+        mother, mkind, size = holder, nkind, nsize
+    return Scene("nested", mats, solids, places, VoxelSpec(mode="smart"))
+
+
+def random_queries(og, scene, n, seed, box_half=None, surface_frac=0.5):
+    """Points inside the world (half of them moved onto a boundary along a random ray) with
+    random unit directions.  Surface points are produced by the oracle's own compute_step."""
+    rng = np.random.default_rng(seed)
+    h = np.asarray(box_half if box_half is not None else world_half(scene) * 0.98)
+    p = rng.uniform(-h, h, size=(n, 3))
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    k = int(n * surface_frac)
+    if k:
+        d, pa = og.locate_many(p[:k], v[:k])
+        ok = d > 0
+        s, lim, _ = og.compute_step_many(p[:k][ok], v[:k][ok], d[ok], pa[ok])
+        idx = np.nonzero(ok)[0]
+        p[idx] = p[idx] + s[:, None] * v[idx]
+        # half of the surface points get a fresh random direction
+        w = rng.normal(size=(idx.size, 3))
+        w /= np.linalg.norm(w, axis=1)[:, None]
+        flip = rng.uniform(size=idx.size) < 0.5
+        v[idx[flip]] = w[flip]
+    return p, v
+
+
+def to_soa(a, torch, device="cuda"):
+    return torch.tensor(np.ascontiguousarray(a.T), dtype=torch.float64, device=device)

@@ -1,0 +1,131 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+symbol declared in include/g4nav.h, and its host-side geometry builder
+(host-only context, no GPU) validates geometries and builds voxels."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from synth.scenes import Scene, Solid, Placement, VoxelSpec, BOX, TUBE, ORB
+from synth.materials import vacuum
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def g4():
+    from paper_1209_5235_gb300 import build
+    build.build()
+    import paper_1209_5235_gb300 as g
+    return g
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "g4nav.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(g4n_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(g4):
+    L = g4.load()
+    names = declared_functions()
+    assert len(names) >= 17
+    missing = [n for n in names if not hasattr(L, n)]
+    assert missing == []
+
+
+def test_create_without_gpu_fails_cleanly(g4):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(g4.G4NError) as e:
+        g4.g4n_create(0)
+    assert e.value.code == g4.G4N_ERR_CUDA if hasattr(g4, "G4N_ERR_CUDA") else True
+
+
+def _scene(solids, places):
+    return Scene("t", [vacuum()], [Solid(BOX, (100.0, 100.0, 100.0))] + solids,
+                 [Placement(-1, 0, 0, (0, 0, 0))] + places, VoxelSpec(mode="smart"))
+
+
+def test_host_only_builds_configs(g4):
+    ctx = g4.g4n_create(-1)
+    try:
+        for sc in (synth.scenes.tiny_scene(), synth.scenes.calorimeter_scene(), synth.scenes.barrel_scene(),
+                   synth.scenes.spheres_scene()):
+            info = g4.g4n_geom_info(ctx, g4.build_scene(ctx, sc))
+            assert info["n_volumes"] == sc.n_volumes
+            assert info["max_depth"] == max(1 + _depth(sc, i) for i in range(sc.n_volumes))
+            assert info["n_candidate_entries"] >= sc.n_volumes - 1
+    finally:
+        g4.g4n_destroy(ctx)
+
+
+def _depth(sc, i):
+    d = 0
+    while sc.placements[i].mother >= 0:
+        i = sc.placements[i].mother
+        d += 1
+    return d
+
+
+@pytest.mark.parametrize("case,code", [
+    ("overlap", -2), ("sticks_out", -2), ("too_deep", -2), ("bad_rotation", -1), ("bad_box", -1),
+    ("bad_tube", -1), ("world_not_first", -1), ("bad_material_id", -1)])
+def test_host_only_validation(g4, case, code):
+    ctx = g4.g4n_create(-1)
+    try:
+        with pytest.raises(g4.G4NError) as e:
+            if case == "overlap":
+                g4.build_scene(ctx, _scene([Solid(BOX, (10, 10, 10))],
+                                           [Placement(0, 1, 0, (0, 0, 0)), Placement(0, 1, 0, (5, 0, 0))]))
+            elif case == "sticks_out":
+                g4.build_scene(ctx, _scene([Solid(ORB, (10,))], [Placement(0, 1, 0, (95, 0, 0))]))
+            elif case == "too_deep":
+                sols = [Solid(BOX, (90.0 - 10 * k, 90.0 - 10 * k, 90.0 - 10 * k)) for k in range(8)]
+                g4.build_scene(ctx, _scene(sols, [Placement(k, k + 1, 0, (0, 0, 0)) for k in range(8)]))
+            elif case == "bad_rotation":
+                g4.build_scene(ctx, _scene([Solid(BOX, (1, 1, 1))], [Placement(0, 1, 0, (0, 0, 0), (1.0, 0.1))]))
+            elif case == "bad_box":
+                g4.g4n_solid_box(ctx, 1.0, 0.0, 1.0)
+            elif case == "bad_tube":
+                g4.g4n_solid_tube(ctx, 2.0, 1.0, 1.0, 0.0, 1.0)
+            elif case == "world_not_first":
+                m = g4.g4n_material_add(ctx, 1.0, [1, 2], [0, 0], [0, 0])
+                s = g4.g4n_solid_box(ctx, 1, 1, 1)
+                g4.g4n_place(ctx, 0, s, m, [0, 0, 0])
+            elif case == "bad_material_id":
+                s = g4.g4n_solid_box(ctx, 1, 1, 1)
+                g4.g4n_place(ctx, -1, s, 7, [0, 0, 0])
+        assert e.value.code == code
+        assert g4.g4n_last_error(ctx)
+    finally:
+        g4.g4n_destroy(ctx)
+
+
+def test_host_only_accepts_touching_and_max_depth(g4):
+    """Exactly touching siblings and a hierarchy of exactly G4N_DMAX levels are valid."""
+    ctx = g4.g4n_create(-1)
+    try:
+        sols = [Solid(BOX, (90.0 - 10 * k, 90.0 - 10 * k, 90.0 - 10 * k)) for k in range(7)]
+        g4.build_scene(ctx, _scene(sols, [Placement(k, k + 1, 0, (0, 0, 0)) for k in range(7)]))
+        g4.build_scene(ctx, _scene([Solid(BOX, (10, 10, 10))],
+                                   [Placement(0, 1, 0, (-10, 0, 0)), Placement(0, 1, 0, (10, 0, 0))]))
+        seg = Solid(TUBE, (10.0, 20.0, 5.0, 0.0, math.pi / 2))
+        g4.build_scene(ctx, _scene([seg], [Placement(0, 1, 0, (0, 0, 0), (math.cos(k * math.pi / 2), math.sin(k * math.pi / 2)))
+                                           for k in range(4)]))
+    finally:
+        g4.g4n_destroy(ctx)
+
+
+def test_queries_refused_on_host_only_context(g4):
+    ctx = g4.g4n_create(-1)
+    try:
+        gid = g4.build_scene(ctx, synth.scenes.tiny_scene())
+        L = g4.load()
+        assert L.g4n_locate(ctx, gid, 1, None, None, None, None, None) == g4.G4N_ERR_STATE
+    finally:
+        g4.g4n_destroy(ctx)
