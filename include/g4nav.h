@@ -237,6 +237,33 @@ int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_e
 int g4n_transport_batch_host(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_edep, uint64_t *out_counters,
                              uint64_t *out_track_hash, double *out_track_len, g4n_stream stream);
 
+/* ---------------------------------------------------------------- allocation-free transport */
+
+/* No counterpart in the paper: a library-side convenience for callers that must not allocate
+ * device memory once they are running -- a process whose own allocator reserved the GPU's memory
+ * up front, or a latency-critical loop that forbids cudaMalloc/cudaFree (cudaFree synchronizes the
+ * whole device) after start-up.
+ *
+ * Same transport and arguments as g4n_transport_batch, but the queue head, status word and
+ * work-item table live in one fixed device array inside libg4nav (about 43 KB, held on every GPU
+ * that loads the library until the process exits) instead of the context's cudaMalloc'd
+ * workspace.  The call makes no device or host heap allocation: it only clears and fills that
+ * array with stream-ordered copies and launches the kernel.  (Building the geometry and creating
+ * the context still allocate; do that at start-up.)
+ *  - At most G4N_NOALLOC_MAX_ITEMS work items; more returns G4N_ERR_ARG.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the one array: calls whose work overlaps on the GPU (other streams, other
+ *    threads, other contexts in the process) race and give wrong results.  Serialize them.
+ *  - Device-side errors are not reported through g4n_sync: out_counters[G4N_NOALLOC_STATUS_SLOT] is
+ *    overwritten (on `stream`) with this call's status bits -- 1 step cap reached, 2 voxel-walk
+ *    cap, 4 rejection-sampling cap; 0 means no device-side error.
+ * out_edep, out_counters, out_track_hash, out_track_len: DEVICE pointers as in g4n_transport_batch. */
+#define G4N_NOALLOC_MAX_ITEMS 256
+#define G4N_NOALLOC_STATUS_SLOT (G4N_N_COUNTERS - 1)
+int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_edep, uint64_t *out_counters,
+                                uint64_t *out_track_hash, double *out_track_len, g4n_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,8 @@ G4N_MODE_FP64, G4N_MODE_FP32_RECHECK, G4N_MODE_LEARNED = 0, 1, 2
 G4N_LIM_PHYSICS, G4N_LIM_MOTHER = -2, -1
 G4N_DMAX = 8
 G4N_N_COUNTERS = 32
+G4N_NOALLOC_MAX_ITEMS = 256
+G4N_NOALLOC_STATUS_SLOT = G4N_N_COUNTERS - 1
 COUNTER_NAMES = {0: "tracks", 1: "steps", 2: "geom_steps", 3: "phys_steps", 4: "photo", 5: "compton", 6: "escaped",
                  7: "cutoff", 8: "pushes", 9: "step_limit", 16: "safety_skips", 17: "cand_box", 18: "cand_tube",
                  19: "cand_orb", 20: "dist_out", 21: "inside", 22: "vox_nodes", 23: "rechecks", 24: "proposals",
@@ -34,12 +36,14 @@ PARITY_COUNTERS = ["tracks", "steps", "geom_steps", "phys_steps", "photo", "comp
 
 EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_scale", "g4n_sync", "g4n_material_add",
             "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_place", "g4n_voxelize", "g4n_geom_finalize",
-            "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_transport_batch", "g4n_transport_batch_host"]
+            "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_transport_batch", "g4n_transport_batch_host",
+            "g4n_transport_batch_noalloc"]
 
 __all__ = EXPORTED + ["G4NError", "load", "lib_path", "build_scene", "make_items", "counters_dict", "voxel_params",
                       "COUNTER_NAMES", "PARITY_COUNTERS", "G4N_DMAX", "G4N_N_COUNTERS", "G4N_MODE_FP64",
                       "G4N_MODE_FP32_RECHECK", "G4N_MODE_LEARNED", "G4N_LIM_PHYSICS", "G4N_LIM_MOTHER",
                       "G4N_ERR_ARG", "G4N_ERR_GEOM", "G4N_ERR_STEP_LIMIT", "G4N_ERR_TIMEOUT", "G4N_ERR_STATE",
+                      "G4N_NOALLOC_MAX_ITEMS", "G4N_NOALLOC_STATUS_SLOT",
                       "g4n_voxel_params", "g4n_source", "g4n_work_item", "g4n_batch_desc"]
 
 
@@ -101,6 +105,7 @@ def load():
         "g4n_compute_step": [vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp],
         "g4n_transport_batch": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
         "g4n_transport_batch_host": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
+        "g4n_transport_batch_noalloc": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -331,6 +336,26 @@ def g4n_transport_batch(ctx, items, seed: int, edep, counters, track_hash=None, 
                                            _dptr(counters, torch.int64, "counters"),
                                            _dptr(track_hash, torch.int64, "track_hash"),
                                            _dptr(track_len, torch.float64, "track_len"), _stream(stream)))
+
+
+def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_hash=None, track_len=None,
+                                cutoff: float = 0.01, mode: int = G4N_MODE_FP64, n_batches: int = 100,
+                                max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0, chunk: int = 0,
+                                stream=None) -> None:
+    """The allocation-free variant of g4n_transport_batch (at most G4N_NOALLOC_MAX_ITEMS items).
+
+    For callers that must not allocate device memory while running: the library keeps this call's
+    scratch in a fixed device array instead of a cudaMalloc'd workspace.  Device-side errors are
+    written to counters[G4N_NOALLOC_STATUS_SLOT] (0 = none) instead of being reported by g4n_sync.
+    """
+    import torch
+    d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, chunk)
+    if edep.shape[0] != n_batches:
+        raise ValueError("edep rows must equal n_batches")
+    _check(ctx, load().g4n_transport_batch_noalloc(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
+                                                   _dptr(counters, torch.int64, "counters"),
+                                                   _dptr(track_hash, torch.int64, "track_hash"),
+                                                   _dptr(track_len, torch.float64, "track_len"), _stream(stream)))
 
 
 def g4n_transport_batch_host(ctx, items, seed: int, stride: int, n_tracks: int = 0, want_hash: bool = False,

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -648,3 +649,136 @@ int g4n_sync(g4n_ctx *ctx, g4n_stream stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free transport
+//
+// g4n_transport_batch keeps its queue head, status word and work-item table in
+// a workspace that the context allocates with cudaMalloc on first use.  Some
+// callers cannot allow that: a process whose own allocator has reserved the
+// device memory up front, or a latency-critical loop that forbids device
+// allocation (and the device-wide synchronization cudaFree implies) once it is
+// running.  g4n_transport_batch_noalloc runs the same transport kernel with that
+// scratch held in the fixed device array below instead, and calls no allocating
+// CUDA or library routine.
+
+namespace {
+
+constexpr size_t kNoAllocHeader = 256;
+constexpr size_t kNoAllocBytes = kNoAllocHeader + (size_t)G4N_NOALLOC_MAX_ITEMS * sizeof(DItem);
+
+// Shared by every call in the process; every GPU that loads this library keeps it until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `device` (which must be current), looked up once per device.
+int noalloc_scratch(g4n_ctx *ctx, int device, unsigned char **out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return g4n_fail(ctx, G4N_ERR_CUDA, std::string("transport_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+    g_noalloc_addr[device] = p;
+  }
+  *out = (unsigned char *)g_noalloc_addr[device];
+  return G4N_OK;
+}
+
+}  // namespace
+
+extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep,
+                                           uint64_t *out_counters, uint64_t *out_track_hash, double *out_track_len,
+                                           g4n_stream stream) {
+  if (!ctx || !b) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: null argument");
+  if (ctx->device < 0) return g4n_fail(ctx, G4N_ERR_STATE, "host-only context: no device queries");
+  if (b->n_items < 1 || !b->items) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: no work items");
+  if (b->n_items > G4N_NOALLOC_MAX_ITEMS)
+    return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: more than G4N_NOALLOC_MAX_ITEMS (" +
+                                          std::to_string(G4N_NOALLOC_MAX_ITEMS) + ") work items; use g4n_transport_batch");
+  if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: null output");
+  if (b->mode != G4N_MODE_FP64) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: mode not available");
+  if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: n_tally_batches < 1");
+  if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: cutoff must be >= 0");
+  DItem items[G4N_NOALLOC_MAX_ITEMS];  // host staging on the stack: no heap either
+  int64_t total = 0;
+  for (int i = 0; i < b->n_items; ++i) {
+    const g4n_work_item &w = b->items[i];
+    int rc = check_geom(ctx, w.geom);
+    if (rc) return rc;
+    const int64_t nv = ctx->geoms[w.geom]->dview.n_vol;
+    if (w.n_tracks < 0 || w.track_id0 < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: negative track count or id");
+    if (w.tally_offset < 0 || w.tally_offset + nv + 2 > b->tally_stride)
+      return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: tally columns out of range");
+    const g4n_source &s = w.source;
+    if (!s.isotropic) {
+      const double n2 = s.dir[0] * s.dir[0] + s.dir[1] * s.dir[1] + s.dir[2] * s.dir[2];
+      if (!(std::fabs(n2 - 1.0) <= 1e-12)) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: source direction not unit");
+    }
+    if (s.e_kind < 0 || s.e_kind > 2 || !(s.e0 > 0.0) || (s.e_kind > 0 && !(s.e1 >= s.e0)))
+      return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: bad source energy");
+    if (!(s.spot_sigma >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: negative spot sigma");
+    DItem &d = items[i];
+    std::memset(&d, 0, sizeof(d));
+    d.geom = w.geom;
+    d.n = w.n_tracks;
+    d.tid0 = w.track_id0;
+    d.tally_off = w.tally_offset;
+    d.start = total;
+    const double src[16] = {s.pos[0], s.pos[1], s.pos[2], s.spot_sigma, (double)(s.has_z != 0), s.z0, s.z1,
+                            (double)(s.isotropic != 0), s.dir[0], s.dir[1], s.dir[2], (double)s.e_kind, s.e0, s.e1,
+                            0.0, 0.0};
+    std::memcpy(d.src, src, sizeof(src));
+    total += w.n_tracks;
+  }
+  const int block = b->block_size > 0 ? b->block_size : 128;
+  if (block % 32 || block > 128)
+    return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: block_size must be a multiple of 32, <= 128");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_CUDA, "transport_noalloc: cudaSetDevice failed");
+  unsigned char *scratch = nullptr;
+  int rc = noalloc_scratch(ctx, ctx->device, &scratch);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // queue head and status start at zero on every call; the item table is rewritten
+  if (cudaMemsetAsync(scratch, 0, 16, st) != cudaSuccess)
+    return g4n_fail(ctx, G4N_ERR_CUDA, "transport_noalloc: scratch clear failed");
+  if (total > 0) {
+    if (cudaMemcpyAsync(scratch + kNoAllocHeader, items, (size_t)b->n_items * sizeof(DItem), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+      return g4n_fail(ctx, G4N_ERR_CUDA, "transport_noalloc: item upload failed");
+    TParams P;
+    P.geoms = ctx->d_geoms;
+    P.items = (const DItem *)(scratch + kNoAllocHeader);
+    P.n_items = b->n_items;
+    P.total = total;
+    P.q_head = (unsigned long long *)scratch;
+    P.status = (uint32_t *)(scratch + 8);
+    P.seed = b->seed;
+    P.cutoff = b->cutoff;
+    P.max_steps = b->max_steps > 0 ? b->max_steps : 1000000;
+    P.nb = b->n_tally_batches;
+    P.stride = b->tally_stride;
+    P.edep = out_edep;
+    P.counters = (unsigned long long *)out_counters;
+    P.out_hash = out_track_hash;
+    P.out_len = out_track_len;
+    int per_sm = b->blocks_per_sm;
+    if (per_sm <= 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport, block, 0);
+      per_sm = std::max(per_sm, 1);
+    }
+    int64_t grid = (int64_t)ctx->sm_count * per_sm;
+    grid = std::max<int64_t>(1, std::min(grid, (total + block - 1) / block));
+    k_transport<<<(int)grid, block, 0, st>>>(P);
+    rc = launch_error(ctx, "transport_noalloc launch");
+    if (rc) return rc;
+  }
+  // report this call's device status bits in the last counter slot
+  if (cudaMemcpyAsync(out_counters + G4N_NOALLOC_STATUS_SLOT, scratch + 8, sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                      st) != cudaSuccess)
+    return g4n_fail(ctx, G4N_ERR_CUDA, "transport_noalloc: status copy failed");
+  return G4N_OK;
+}
