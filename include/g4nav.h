@@ -206,7 +206,12 @@ typedef struct {
  * track's generator), interactions Compton (Kahn's method) or photoabsorption chosen by
  * U mu_tot < mu_photo, energy below `cutoff` after a Compton scatter deposited on the spot.
  * Tally rows: track id mod n_tally_batches; tally_stride doubles per row.  max_steps: per-track
- * cap (0 = 10^6).  block_size / blocks_per_sm / chunk: launch shape (0 = defaults). */
+ * cap (0 = 10^6).  Launch shape (0 = defaults): block_size (multiple of 32, <= 128),
+ * blocks_per_sm, refill_min (a warp refills its idle lanes once at least this many are idle,
+ * 1..32, default 8), interact_min (a warp runs its interaction phase once at least this many
+ * lanes wait for it, 1..32, default 8).  flags: G4N_FLAG_DIAGNOSTICS also fills the diagnostic
+ * counters (G4N_C_SAFETY_SKIPS and above).  Results never depend on the launch shape. */
+#define G4N_FLAG_DIAGNOSTICS 1
 typedef struct {
   int32_t n_items;
   const g4n_work_item *items;
@@ -218,7 +223,9 @@ typedef struct {
   int64_t max_steps;
   int32_t block_size;
   int32_t blocks_per_sm;
-  int32_t chunk;
+  int32_t refill_min;
+  int32_t interact_min;
+  int32_t flags;
 } g4n_batch_desc;
 
 /* Transport every track of the batch (Algorithm 2, phase 5).  out_edep: n_tally_batches x

@@ -25,6 +25,7 @@ G4N_MODE_FP64, G4N_MODE_FP32_RECHECK, G4N_MODE_LEARNED = 0, 1, 2
 G4N_LIM_PHYSICS, G4N_LIM_MOTHER = -2, -1
 G4N_DMAX = 8
 G4N_N_COUNTERS = 32
+G4N_FLAG_DIAGNOSTICS = 1
 G4N_NOALLOC_MAX_ITEMS = 256
 G4N_NOALLOC_STATUS_SLOT = G4N_N_COUNTERS - 1
 COUNTER_NAMES = {0: "tracks", 1: "steps", 2: "geom_steps", 3: "phys_steps", 4: "photo", 5: "compton", 6: "escaped",
@@ -39,7 +40,7 @@ EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_sc
             "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_transport_batch", "g4n_transport_batch_host",
             "g4n_transport_batch_noalloc"]
 
-__all__ = EXPORTED + ["G4NError", "load", "lib_path", "build_scene", "make_items", "counters_dict", "voxel_params",
+__all__ = EXPORTED + ["G4N_FLAG_DIAGNOSTICS", "G4NError", "load", "lib_path", "build_scene", "make_items", "counters_dict", "voxel_params",
                       "COUNTER_NAMES", "PARITY_COUNTERS", "G4N_DMAX", "G4N_N_COUNTERS", "G4N_MODE_FP64",
                       "G4N_MODE_FP32_RECHECK", "G4N_MODE_LEARNED", "G4N_LIM_PHYSICS", "G4N_LIM_MOTHER",
                       "G4N_ERR_ARG", "G4N_ERR_GEOM", "G4N_ERR_STEP_LIMIT", "G4N_ERR_TIMEOUT", "G4N_ERR_STATE",
@@ -75,7 +76,8 @@ class g4n_batch_desc(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_int32), ("items", ctypes.POINTER(g4n_work_item)), ("seed", ctypes.c_uint64),
                 ("cutoff", ctypes.c_double), ("mode", ctypes.c_int32), ("n_tally_batches", ctypes.c_int32),
                 ("tally_stride", ctypes.c_int64), ("max_steps", ctypes.c_int64), ("block_size", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("refill_min", ctypes.c_int32), ("interact_min", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
 
 
 _lib = None
@@ -310,7 +312,8 @@ def make_items(entries) -> "ctypes.Array":
     return arr
 
 
-def _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, chunk):
+def _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, refill_min=0,
+          interact_min=0, diagnostics=False):
     d = g4n_batch_desc()
     d.n_items = len(items)
     d.items = ctypes.cast(items, ctypes.POINTER(g4n_work_item))
@@ -320,16 +323,20 @@ def _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, b
     d.n_tally_batches = int(n_batches)
     d.tally_stride = int(stride)
     d.max_steps = int(max_steps)
-    d.block_size, d.blocks_per_sm, d.chunk = int(block_size), int(blocks_per_sm), int(chunk)
+    d.block_size, d.blocks_per_sm = int(block_size), int(blocks_per_sm)
+    d.refill_min, d.interact_min = int(refill_min), int(interact_min)
+    d.flags = G4N_FLAG_DIAGNOSTICS if diagnostics else 0
     return d
 
 
 def g4n_transport_batch(ctx, items, seed: int, edep, counters, track_hash=None, track_len=None, cutoff: float = 0.01,
                         mode: int = G4N_MODE_FP64, n_batches: int = 100, max_steps: int = 0, block_size: int = 0,
-                        blocks_per_sm: int = 0, chunk: int = 0, stream=None) -> None:
+                        blocks_per_sm: int = 0, refill_min: int = 0, interact_min: int = 0,
+                        diagnostics: bool = False, stream=None) -> None:
     """Device outputs (accumulated): edep (n_batches, stride) f64, counters (32,) int64 (as uint64 bits)."""
     import torch
-    d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, chunk)
+    d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
+              interact_min, diagnostics)
     if edep.shape[0] != n_batches:
         raise ValueError("edep rows must equal n_batches")
     _check(ctx, load().g4n_transport_batch(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
@@ -340,7 +347,9 @@ def g4n_transport_batch(ctx, items, seed: int, edep, counters, track_hash=None, 
 
 def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_hash=None, track_len=None,
                                 cutoff: float = 0.01, mode: int = G4N_MODE_FP64, n_batches: int = 100,
-                                max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0, chunk: int = 0,
+                                max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0, refill_min: int = 0,
+                                interact_min: int = 0,
+                        diagnostics: bool = False,
                                 stream=None) -> None:
     """The allocation-free variant of g4n_transport_batch (at most G4N_NOALLOC_MAX_ITEMS items).
 
@@ -349,7 +358,8 @@ def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_has
     written to counters[G4N_NOALLOC_STATUS_SLOT] (0 = none) instead of being reported by g4n_sync.
     """
     import torch
-    d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, chunk)
+    d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
+              interact_min, diagnostics)
     if edep.shape[0] != n_batches:
         raise ValueError("edep rows must equal n_batches")
     _check(ctx, load().g4n_transport_batch_noalloc(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
@@ -361,9 +371,11 @@ def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_has
 def g4n_transport_batch_host(ctx, items, seed: int, stride: int, n_tracks: int = 0, want_hash: bool = False,
                              want_len: bool = False, cutoff: float = 0.01, mode: int = G4N_MODE_FP64,
                              n_batches: int = 100, max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0,
-                             chunk: int = 0, stream=None, out=None):
+                             refill_min: int = 0, interact_min: int = 0, diagnostics: bool = False, stream=None,
+                             out=None):
     """Host-buffer variant: returns dict of numpy arrays (edep, counters, hashes, lengths)."""
-    d = _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, chunk)
+    d = _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, refill_min,
+              interact_min, diagnostics)
     if out is None:
         out = {"edep": np.zeros((n_batches, stride)), "counters": np.zeros(G4N_N_COUNTERS, dtype=np.uint64),
                "hashes": np.zeros(n_tracks, dtype=np.uint64) if want_hash else None,

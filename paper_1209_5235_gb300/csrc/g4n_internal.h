@@ -26,7 +26,7 @@ constexpr int kDMax = G4N_DMAX;
 constexpr int kMaxLevels = 3;
 
 enum SolidKind : int32_t { kBox = 0, kTube = 1, kOrb = 2 };
-enum TubeFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4 };
+enum VolFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4, kWorldAligned = 8 };  // tube bits; world rotation is identity
 
 struct alignas(128) DVol {
   double tx, ty, tz, c, s;  // placement: local = R(theta)^T (mother - t)
@@ -74,6 +74,8 @@ struct DGeom {
   const double *matE, *matC, *matP;
   const int32_t *mat_off, *mat_n;
   int32_t n_vol, n_mat;
+  int32_t shared_grid;  // all materials tabulated on one energy grid
+  int32_t pad;
   double tol, half;
 };
 

@@ -459,6 +459,7 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
       dau[pl.mother].push_back(i);
       g->vol[pl.mother].n_dau++;
     }
+    if (w.c == 1.0 && w.s == 0.0) v.flags |= kWorldAligned;
     if (v.depth > kDMax) {
       delete g;
       return g4n_fail(ctx, G4N_ERR_GEOM, "finalize: hierarchy deeper than G4N_DMAX at volume " + std::to_string(i));
@@ -608,6 +609,9 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
   d.mat_n = (const int32_t *)(base + off[11]);
   d.n_vol = n;
   d.n_mat = (int32_t)B.mats.size();
+  d.shared_grid = 1;
+  for (const HMat &m : B.mats)
+    if (m.E != B.mats[0].E) d.shared_grid = 0;
   d.tol = tol;
   d.half = 0.5 * tol;
   int32_t gid = (int32_t)ctx->geoms.size();

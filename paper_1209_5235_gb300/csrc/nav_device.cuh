@@ -10,8 +10,14 @@
 //    whose band holds the point;
 //  * DistanceToIn from a point that is not inside only reports crossings
 //    beyond the band; ties in compute_step go to the daughter over the mother
-//    and to the lower daughter id;
-//  * every distance here is FP64; the FP32 variants live in nav_fp32.cuh.
+//    and to the lower daughter id.
+//
+// Precision modes.  kFP64: every distance in FP64.  kFP32: rigorous FP32
+// interval bounds (directed rounding) on the padded bounding boxes decide which
+// candidates can still matter and whether the physics step wins; only those
+// candidates and the winning surface are evaluated in FP64, so every result is
+// the FP64 one.  GB300's FP64 rate is ~1/72 of its FP32 rate, which is why the
+// bounds are worth their extra FP32 work.
 #pragma once
 
 #include <cstdint>
@@ -22,6 +28,8 @@ namespace g4n {
 namespace dev {
 
 constexpr double kInf = __builtin_huge_val();
+constexpr float kInfF = __builtin_huge_valf();
+enum Mode : int { kFP64 = 0, kFP32 = 1 };
 
 struct V3 {
   double x, y, z;
@@ -29,10 +37,24 @@ struct V3 {
 
 __device__ __forceinline__ double comp(const V3 &v, int a) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); }
 
-// Per-thread event counters (registers), flushed once per warp at the end.
+// Per-thread event counters (registers; constant indices only), flushed once per warp.
 struct Counters {
   uint32_t c[G4N_N_COUNTERS];
 };
+
+template <bool COUNT>
+__device__ __forceinline__ void diag(Counters &c, int k) {
+  if (COUNT) c.c[k]++;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void diag_kind(Counters &c, int kind) {
+  if (COUNT) {
+    if (kind == kBox) c.c[G4N_C_CAND_BOX]++;
+    else if (kind == kTube) c.c[G4N_C_CAND_TUBE]++;
+    else c.c[G4N_C_CAND_ORB]++;
+  }
+}
 
 // ---------------------------------------------------------------- frames
 
@@ -46,8 +68,15 @@ __device__ __forceinline__ void to_local(const DVol &v, const V3 &pm, const V3 &
   vl.z = vm.z;
 }
 
-__device__ __forceinline__ void world_to_local(const DWorld &w, const V3 &p, const V3 &u, V3 &pl, V3 &vl) {
+// World -> local frame of a volume; world-aligned volumes need only the translation.
+__device__ __forceinline__ void world_to_local(const DWorld &w, bool aligned, const V3 &p, const V3 &u, V3 &pl,
+                                               V3 &vl) {
   const double dx = p.x - w.tx, dy = p.y - w.ty;
+  if (aligned) {
+    pl = V3{dx, dy, p.z - w.tz};
+    vl = u;
+    return;
+  }
   pl.x = w.c * dx + w.s * dy;
   pl.y = w.c * dy - w.s * dx;
   pl.z = p.z - w.tz;
@@ -55,6 +84,17 @@ __device__ __forceinline__ void world_to_local(const DWorld &w, const V3 &p, con
   vl.y = w.c * u.y - w.s * u.x;
   vl.z = u.z;
 }
+
+// Reciprocal direction components (0 where the component is 0: never used there).
+struct Inv3 {
+  double x, y, z;
+};
+
+__device__ __forceinline__ Inv3 inv_dir(const V3 &v) {
+  return Inv3{v.x != 0.0 ? 1.0 / v.x : 0.0, v.y != 0.0 ? 1.0 / v.y : 0.0, v.z != 0.0 ? 1.0 / v.z : 0.0};
+}
+
+__device__ __forceinline__ double icomp(const Inv3 &v, int a) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); }
 
 // ---------------------------------------------------------------- box
 
@@ -87,11 +127,12 @@ __device__ __forceinline__ double box_dist_in(const double *h, const V3 &p, cons
   return fmax(tin, 0.0);
 }
 
-__device__ __forceinline__ double box_dist_out(const double *h, const V3 &p, const V3 &v) {
+// DistanceToOut with the reciprocal direction of the same frame.
+__device__ __forceinline__ double box_dist_out(const double *h, const V3 &p, const V3 &v, const Inv3 &iv) {
   double t = kInf;
-  if (v.x != 0.0) t = fmin(t, (copysign(h[0], v.x) - p.x) / v.x);
-  if (v.y != 0.0) t = fmin(t, (copysign(h[1], v.y) - p.y) / v.y);
-  if (v.z != 0.0) t = fmin(t, (copysign(h[2], v.z) - p.z) / v.z);
+  if (v.x != 0.0) t = fmin(t, (copysign(h[0], v.x) - p.x) * iv.x);
+  if (v.y != 0.0) t = fmin(t, (copysign(h[1], v.y) - p.y) * iv.y);
+  if (v.z != 0.0) t = fmin(t, (copysign(h[2], v.z) - p.z) * iv.z);
   return fmax(t, 0.0);
 }
 
@@ -299,8 +340,8 @@ __device__ __forceinline__ double vol_dist_in(const DVol &d, const V3 &p, const 
   return tube_cross(d.p, d.flags, p, v, half, true);
 }
 
-__device__ __forceinline__ double vol_dist_out(const DVol &d, const V3 &p, const V3 &v, double half) {
-  if (d.kind == kBox) return box_dist_out(d.p, p, v);
+__device__ __forceinline__ double vol_dist_out(const DVol &d, const V3 &p, const V3 &v, const Inv3 &iv, double half) {
+  if (d.kind == kBox) return box_dist_out(d.p, p, v, iv);
   if (d.kind == kOrb) return orb_dist_out(d.p[0], p, v);
   const double t = tube_cross(d.p, d.flags, p, v, half, false);
   return t == kInf ? 0.0 : fmax(t, 0.0);
@@ -318,9 +359,184 @@ __device__ __forceinline__ double vol_safety_out(const DVol &d, const V3 &p) {
   return tube_safety_out(d.p, d.flags, p);
 }
 
+// ---------------------------------------------------------------- FP32 interval bounds
+// A point p (FP64) is enclosed by [lo, hi] = the float neighbours of (float)p; a
+// direction component by its float neighbours, whose reciprocals, rounded
+// outward, enclose 1/v.  All products and differences below are rounded in the
+// direction that keeps each bound valid, so every lower bound is <= the exact
+// FP64 quantity it bounds (and every upper bound >=).
+
+struct Ray32 {
+  float plo[3], phi[3];
+  float ilo[3], ihi[3];  // enclosure of 1/|v_a|
+  int sgn[3];            // sign of v_a (0 if |v_a| < 1e-30)
+};
+
+__device__ __forceinline__ void enclose(double x, float &lo, float &hi) {
+  const float f = (float)x;
+  lo = nextafterf(f, -kInfF);
+  hi = nextafterf(f, kInfF);
+}
+
+__device__ __forceinline__ Ray32 make_ray32(const V3 &p, const V3 &v) {
+  Ray32 r;
+  const double pp[3] = {p.x, p.y, p.z}, vv[3] = {v.x, v.y, v.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    enclose(pp[a], r.plo[a], r.phi[a]);
+    const double w = fabs(vv[a]);
+    if (w < 1e-30) {
+      r.sgn[a] = 0;
+      r.ilo[a] = r.ihi[a] = 0.f;
+      continue;
+    }
+    r.sgn[a] = vv[a] > 0.0 ? 1 : -1;
+    float wlo, whi;
+    enclose(w, wlo, whi);
+    r.ilo[a] = __frcp_rd(whi);
+    r.ihi[a] = wlo > 0.f ? __frcp_ru(wlo) : kInfF;
+  }
+  return r;
+}
+
+// Lower/upper bound of num / |v_a| given num in [nlo, nhi] (scalar num bounds).
+__device__ __forceinline__ float div_lo(float n, const Ray32 &r, int a) {
+  return n >= 0.f ? __fmul_rd(n, r.ilo[a]) : __fmul_rd(n, r.ihi[a]);
+}
+__device__ __forceinline__ float div_hi(float n, const Ray32 &r, int a) {
+  return n >= 0.f ? __fmul_ru(n, r.ihi[a]) : __fmul_ru(n, r.ilo[a]);
+}
+
+// Rigorous lower bound of the parameter at which the ray enters box [lo, hi]
+// (same frame), +inf when the ray certainly misses it.  Also the exit upper bound.
+__device__ __forceinline__ float box_entry_lb(const float *lo, const float *hi, const Ray32 &r, float *exit_ub) {
+  float tlo = 0.f, thi = kInfF;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (r.sgn[a] == 0) {
+      if (r.phi[a] < lo[a] || r.plo[a] > hi[a]) return kInfF;
+      continue;
+    }
+    float en, ex;
+    if (r.sgn[a] > 0) {
+      en = div_lo(__fsub_rd(lo[a], r.phi[a]), r, a);
+      ex = div_hi(__fsub_ru(hi[a], r.plo[a]), r, a);
+    } else {
+      en = div_lo(__fsub_rd(r.plo[a], hi[a]), r, a);
+      ex = div_hi(__fsub_ru(r.phi[a], lo[a]), r, a);
+    }
+    tlo = fmaxf(tlo, en);
+    thi = fminf(thi, ex);
+  }
+  if (exit_ub) *exit_ub = thi;
+  return tlo > thi ? kInfF : tlo;
+}
+
+// Lower bound of the Euclidean distance from the point to box [lo, hi].
+__device__ __forceinline__ float box_gap_lb(const float *lo, const float *hi, const Ray32 &r) {
+  float d = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d = fmaxf(d, fmaxf(__fsub_rd(lo[a], r.phi[a]), __fsub_rd(r.plo[a], hi[a])));
+  return d;
+}
+
+__device__ __forceinline__ float absmax(float lo, float hi) { return fmaxf(fabsf(lo), fabsf(hi)); }
+__device__ __forceinline__ float absmin(float lo, float hi) { return (lo <= 0.f && hi >= 0.f) ? 0.f : fminf(fabsf(lo), fabsf(hi)); }
+
+// Bounds of the leaf's DistanceToOut in its own frame: [*lo, *hi].  Boxes get the
+// directional interval; orbs and tubes the isotropic safety (lower) and the exit
+// of their bounding box (upper).  Also a lower bound of the isotropic safety.
+__device__ __forceinline__ void exit_bounds32(const DVol &V, const Ray32 &r, const V3 &p, float *lo, float *hi,
+                                              float *safety) {
+  float h[3];
+  if (V.kind == kBox) {
+    h[0] = __double2float_rd(V.p[0]);
+    h[1] = __double2float_rd(V.p[1]);
+    h[2] = __double2float_rd(V.p[2]);
+    float tlo = kInfF, thi = kInfF, s = kInfF;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s = fminf(s, __fsub_rd(h[a], absmax(r.plo[a], r.phi[a])));
+      if (r.sgn[a] == 0) continue;
+      // exit through the face +h (v > 0) or -h (v < 0): distance (h - s p) / |v| with s = sign(v)
+      const float hu = __double2float_ru(V.p[a]);
+      float nlo, nhi;
+      if (r.sgn[a] > 0) {
+        nlo = __fsub_rd(h[a], r.phi[a]);
+        nhi = __fsub_ru(hu, r.plo[a]);
+      } else {
+        nlo = __fadd_rd(h[a], r.plo[a]);
+        nhi = __fadd_ru(hu, r.phi[a]);
+      }
+      tlo = fminf(tlo, div_lo(nlo, r, a));
+      thi = fminf(thi, div_hi(nhi, r, a));
+    }
+    *lo = fmaxf(tlo, 0.f);
+    *hi = fmaxf(thi, 0.f);
+    *safety = fmaxf(s, 0.f);
+    return;
+  }
+  float ax = absmax(r.plo[0], r.phi[0]), ay = absmax(r.plo[1], r.phi[1]), az = absmax(r.plo[2], r.phi[2]);
+  float s;
+  float ext[3];
+  if (V.kind == kOrb) {
+    const float R = __double2float_rd(V.p[0]);
+    const float rr = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az)));
+    s = __fsub_rd(R, rr);
+    ext[0] = ext[1] = ext[2] = __double2float_ru(V.p[0]);
+  } else {
+    const float rmax = __double2float_rd(V.p[1]), hz = __double2float_rd(V.p[2]);
+    const float rup = __fsqrt_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)));
+    s = fminf(__fsub_rd(rmax, rup), __fsub_rd(hz, az));
+    if (V.flags & kHasRmin) {
+      const float mx = absmin(r.plo[0], r.phi[0]), my = absmin(r.plo[1], r.phi[1]);
+      const float rdn = __fsqrt_rd(__fadd_rd(__fmul_rd(mx, mx), __fmul_rd(my, my)));
+      s = fminf(s, __fsub_rd(rdn, __double2float_ru(V.p[0])));
+    }
+    if (V.flags & kSeg) {
+      // phi planes: exact FP64 distances to the two lines, rounded down
+      const double ds = fabs(V.p[3] * p.y - V.p[4] * p.x), de = fabs(V.p[6] * p.x - V.p[5] * p.y);
+      s = fminf(s, __double2float_rd(fmin(ds, de)));
+    }
+    ext[0] = ext[1] = __double2float_ru(V.p[1]);
+    ext[2] = __double2float_ru(V.p[2]);
+  }
+  const float mlo[3] = {-ext[0], -ext[1], -ext[2]};
+  float xub = kInfF;
+  box_entry_lb(mlo, ext, r, &xub);
+  *safety = fmaxf(s, 0.f);
+  *lo = *safety;
+  *hi = xub;
+}
+
+// Is the point inside the solid by more than the tolerance band whatever the direction?
+// (conservative: false when undecided).
+__device__ __forceinline__ bool certainly_inside32(const DVol &V, const Ray32 &r, float band) {
+  if (V.kind == kBox) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (!(absmax(r.plo[a], r.phi[a]) < __fsub_rd(__double2float_rd(V.p[a]), band))) return false;
+    return true;
+  }
+  const float ax = absmax(r.plo[0], r.phi[0]), ay = absmax(r.plo[1], r.phi[1]), az = absmax(r.plo[2], r.phi[2]);
+  if (V.kind == kOrb) {
+    const float R = __fsub_rd(__double2float_rd(V.p[0]), band);
+    return R > 0.f && __fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az)) < __fmul_rd(R, R);
+  }
+  if (V.flags & kSeg) return false;
+  const float rmax = __fsub_rd(__double2float_rd(V.p[1]), band);
+  if (!(az < __fsub_rd(__double2float_rd(V.p[2]), band))) return false;
+  if (!(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)) < __fmul_rd(rmax, rmax))) return false;
+  if (V.flags & kHasRmin) {
+    const float rmin = __fadd_ru(__double2float_ru(V.p[0]), band);
+    const float mx = absmin(r.plo[0], r.phi[0]), my = absmin(r.plo[1], r.phi[1]);
+    if (!(__fadd_rd(__fmul_rd(mx, mx), __fmul_rd(my, my)) > __fmul_ru(rmin, rmin))) return false;
+  }
+  return true;
+}
+
 // Conservative FP32 test: can the mother-frame point claim daughter box b?
-__device__ __forceinline__ bool box32_contains(const DBox32 &b, const V3 &p) {
-  const float x = (float)p.x, y = (float)p.y, z = (float)p.z;
+__device__ __forceinline__ bool box32_contains(const DBox32 &b, float x, float y, float z) {
   return x >= b.lo[0] && x <= b.hi[0] && y >= b.lo[1] && y <= b.hi[1] && z >= b.lo[2] && z <= b.hi[2];
 }
 
@@ -345,23 +561,37 @@ __device__ __forceinline__ int vox_lookup(const DGeom &G, int h, const V3 &p) {
 }
 
 // Descend from volume m (p, v in m's frame) into the first daughter, in id order,
-// that contains the point; repeat.  Returns the deepest volume.
-__device__ __noinline__ int descend(const DGeom &G, int m, V3 p, V3 v, Counters &cnt) {
+// that contains the point; repeat.  `blocked` is a daughter of m already known
+// not to contain the point (the volume just left).  Each round scans the node's
+// list with the FP32 box test, then the lanes that found a candidate run the
+// FP64 Inside test together.
+template <bool COUNT>
+__device__ __forceinline__ int descend(const DGeom &G, int m, V3 p, V3 v, int blocked, Counters &cnt) {
 #pragma unroll 1
   for (int lev = 0; lev < kDMax; ++lev) {
     const int h = G.vol[m].vox;
     if (h < 0) return m;
     const DCandList L = G.clist[vox_lookup(G, h, p)];
-    int found = -1;
+    const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
+    int i = 0, found = -1;
     V3 fp, fv;
 #pragma unroll 1
-    for (int i = 0; i < L.count; ++i) {
-      const int d = G.cand[L.offset + i];
-      if (!box32_contains(G.box[d], p)) continue;
+    for (;;) {
+      int d = -1;
+#pragma unroll 1
+      while (i < L.count) {
+        const int c = __ldg(&G.cand[L.offset + i]);
+        ++i;
+        if (c != blocked && box32_contains(G.box[c], px, py, pz)) {
+          d = c;
+          break;
+        }
+      }
+      if (d < 0) break;
       const DVol &D = G.vol[d];
       V3 dp, dv;
       to_local(D, p, v, dp, dv);
-      cnt.c[G4N_C_INSIDE]++;
+      diag<COUNT>(cnt, G4N_C_INSIDE);
       if (vol_inside(D, dp, dv, G.half)) {
         found = d;
         fp = dp;
@@ -373,28 +603,54 @@ __device__ __noinline__ int descend(const DGeom &G, int m, V3 p, V3 v, Counters 
     m = found;
     p = fp;
     v = fv;
+    blocked = -1;
   }
   return m;
 }
 
 // Locate from the world: returns the leaf, or -1 outside the world.
+template <bool COUNT>
 __device__ __forceinline__ int locate_world(const DGeom &G, const V3 &x, const V3 &u, Counters &cnt) {
   V3 p, v;
-  world_to_local(G.wxf[0], x, u, p, v);
-  cnt.c[G4N_C_INSIDE]++;
+  world_to_local(G.wxf[0], G.vol[0].flags & kWorldAligned, x, u, p, v);
+  diag<COUNT>(cnt, G4N_C_INSIDE);
   if (!vol_inside(G.vol[0], p, v, G.half)) return -1;
-  return descend(G, 0, p, v, cnt);
+  return descend<COUNT>(G, 0, p, v, -1, cnt);
 }
 
-// After a move: leave every volume that no longer contains the point, then descend.
-__device__ __noinline__ int relocate(const DGeom &G, int leaf, const V3 &x, const V3 &u, Counters &cnt) {
+// After a move: leave every volume that no longer contains the point, then
+// descend.  A step that ended on the leaf's own exit surface (limiter mother,
+// positive length) leaves the leaf for certain: the point is on that surface
+// moving outward, so the leaf's Inside test is false and is skipped.  A volume
+// left on the way up is blocked in the descent below its mother (its Inside is
+// already known to be false).
+template <int MODE, bool COUNT>
+__device__ __forceinline__ int relocate(const DGeom &G, int leaf, const V3 &x, const V3 &u, bool left_leaf,
+                                        Counters &cnt) {
+  int blocked = -1;
+  if (left_leaf) {
+    blocked = leaf;
+    leaf = G.vol[leaf].mother;
+  }
 #pragma unroll 1
   while (leaf >= 0) {
-    V3 p, v;
-    world_to_local(G.wxf[leaf], x, u, p, v);
     const DVol &L = G.vol[leaf];
-    cnt.c[G4N_C_INSIDE]++;
-    if (vol_inside(L, p, v, G.half)) return descend(G, leaf, p, v, cnt);
+    V3 p, v;
+    world_to_local(G.wxf[leaf], L.flags & kWorldAligned, x, u, p, v);
+    bool in;
+    if (MODE == kFP32) {
+      const Ray32 r = make_ray32(p, v);
+      in = certainly_inside32(L, r, (float)(4.0 * G.half) + 1e-30f);
+      if (!in) {
+        diag<COUNT>(cnt, G4N_C_INSIDE);
+        in = vol_inside(L, p, v, G.half);
+      }
+    } else {
+      diag<COUNT>(cnt, G4N_C_INSIDE);
+      in = vol_inside(L, p, v, G.half);
+    }
+    if (in) return descend<COUNT>(G, leaf, p, v, blocked, cnt);
+    blocked = leaf;
     leaf = L.mother;
   }
   return -1;
@@ -427,41 +683,74 @@ __device__ __forceinline__ void chain_fill(const DGeom &G, Chain &ch, int lev, i
   ch.list = 0;
 }
 
+struct StepResult {
+  double step;    // geometric step (valid when it is <= limit or when physics_sure is false)
+  double safety;  // isotropic lower bound
+  int lim;        // daughter id or G4N_LIM_MOTHER
+  bool physics;   // FP32 mode: proven that the limit comes first (no geometry evaluated in FP64)
+};
+
 // Geometric step inside `leaf` from local point p along v (Sec. 3.2, problem 2):
 // DistanceToOut of the leaf, then DistanceToIn of the daughters listed in the
 // voxel nodes the ray crosses, stopping once the node exit lies beyond the best
-// distance or `limit`.  Returns the step, *lim = daughter id or -1 (mother).
-// If want_safety, *safety = isotropic lower bound (mother, the first node's
-// candidates and that node's slab boundaries).  Sets *timeout on a runaway walk.
-__device__ __noinline__ double geom_step(const DGeom &G, int leaf, const V3 &p, const V3 &v, double limit, int *lim,
-                                         double *safety, bool want_safety, Counters &cnt, bool *timeout) {
+// distance or `limit`.  FP64 mode: every candidate in FP64.  FP32 mode: a
+// candidate is evaluated in FP64 only if its FP32 entry bound does not exceed the
+// best exact distance so far, and no FP64 geometry at all is done when the
+// bounds prove that `limit` comes first.  Both modes return the FP64 result.
+template <int MODE, bool COUNT>
+__device__ __forceinline__ StepResult geom_step(const DGeom &G, int leaf, const V3 &p, const V3 &v, const Inv3 &iv,
+                                                double limit, bool want_safety, Counters &cnt, bool *timeout) {
   const DVol &V = G.vol[leaf];
   const double half = G.half;
-  cnt.c[G4N_C_DIST_OUT]++;
-  double best = vol_dist_out(V, p, v, half);
+  StepResult R;
+  R.physics = false;
+  R.lim = G4N_LIM_MOTHER;
+  double best;       // best exact candidate distance so far
+  double stop;       // the walk may stop once a node exit reaches this
+  float out_lo = 0.f;
+  Ray32 r;
+  if (MODE == kFP32) {
+    r = make_ray32(p, v);
+    float out_hi, saf32;
+    exit_bounds32(V, r, p, &out_lo, &out_hi, &saf32);
+    R.safety = saf32;
+    best = kInf;
+    stop = fmin(limit, (double)out_hi);
+  } else {
+    diag<COUNT>(cnt, G4N_C_DIST_OUT);
+    best = vol_dist_out(V, p, v, iv, half);
+    R.safety = want_safety ? vol_safety_out(V, p) : 0.0;
+    stop = fmin(limit, best);
+  }
   int bl = G4N_LIM_MOTHER;
-  double saf = want_safety ? vol_safety_out(V, p) : 0.0;
   if (V.vox >= 0) {
     Chain ch;
     chain_fill(G, ch, 0, V.vox, p);
     bool first = true;
 #pragma unroll 1
     for (int it = 0; it < 1 << 16; ++it) {
-      cnt.c[G4N_C_VOX_NODES]++;
+      diag<COUNT>(cnt, G4N_C_VOX_NODES);
       const DCandList L = G.clist[ch.list];
 #pragma unroll 1
       for (int i = 0; i < L.count; ++i) {
-        const int d = G.cand[L.offset + i];
+        const int d = __ldg(&G.cand[L.offset + i]);
+        if (MODE == kFP32) {
+          const DBox32 B = G.box[d];
+          if (first && want_safety) R.safety = fmin(R.safety, (double)box_gap_lb(B.lo, B.hi, r));
+          const float lb = box_entry_lb(B.lo, B.hi, r, nullptr);
+          if (!((double)lb <= fmin(best, stop))) continue;
+          diag<COUNT>(cnt, G4N_C_RECHECKS);
+        }
         const DVol &D = G.vol[d];
         V3 dp, dv;
         to_local(D, p, v, dp, dv);
-        cnt.c[G4N_C_CAND_BOX + D.kind]++;
+        diag_kind<COUNT>(cnt, D.kind);
         const double t = vol_dist_in(D, dp, dv, half);
         if (t < kInf && (t < best || (t == best && (bl < 0 || d < bl)))) {
           best = t;
           bl = d;
         }
-        if (first && want_safety) saf = fmin(saf, vol_safety_in(D, dp));
+        if (MODE == kFP64 && first && want_safety) R.safety = fmin(R.safety, vol_safety_in(D, dp));
       }
       // exit of the current node along the ray; node slab boundaries bound the safety
       double texit = kInf;
@@ -471,17 +760,17 @@ __device__ __noinline__ double geom_step(const DGeom &G, int leaf, const V3 &p, 
         const DVoxHdr H = G.hdr[ch.h[l]];
         const double pa = comp(p, H.axis), va = comp(v, H.axis);
         const double blo = H.lo + ch.k0[l] * H.width, bhi = H.lo + (ch.k1[l] + 1) * H.width;
-        if (first && want_safety) saf = fmin(saf, fmax(fmin(pa - blo, bhi - pa), 0.0));
+        if (first && want_safety) R.safety = fmin(R.safety, fmax(fmin(pa - blo, bhi - pa), 0.0));
         double t = kInf;
-        if (va > 0.0) t = (bhi - pa) / va;
-        else if (va < 0.0) t = (blo - pa) / va;
+        if (va > 0.0) t = (bhi - pa) * icomp(iv, H.axis);
+        else if (va < 0.0) t = (blo - pa) * icomp(iv, H.axis);
         if (t < texit) {
           texit = t;
           lstar = l;
         }
       }
       first = false;
-      if (!(texit < fmin(best, limit))) break;
+      if (!(texit < fmin(best, stop))) break;
       // step into the neighbouring node at level lstar; deeper levels are looked up again
       const DVoxHdr H = G.hdr[ch.h[lstar]];
       const int nk = comp(v, H.axis) > 0.0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
@@ -499,24 +788,41 @@ __device__ __noinline__ double geom_step(const DGeom &G, int leaf, const V3 &p, 
       if (it == (1 << 16) - 1) *timeout = true;
     }
   }
-  *lim = bl;
-  if (want_safety) *safety = saf;
-  return best;
+  if (MODE == kFP32) {
+    // the FP32 bounds prove the limit comes first: no FP64 geometry needed
+    if (best > limit && (double)out_lo > limit) {
+      R.physics = true;
+      R.step = kInf;
+      R.lim = G4N_LIM_MOTHER;
+      return R;
+    }
+    diag<COUNT>(cnt, G4N_C_DIST_OUT);
+    const double tout = vol_dist_out(V, p, v, iv, half);
+    if (bl >= 0 && best <= tout) {
+      R.step = best;
+      R.lim = bl;
+    } else {
+      R.step = tout;
+      R.lim = G4N_LIM_MOTHER;
+    }
+    return R;
+  }
+  R.step = best;
+  R.lim = bl;
+  return R;
 }
 
 // ---------------------------------------------------------------- attenuation table
 
-// Binary search for E_k <= E < E_{k+1}, lin-lin interpolation, clamped at the ends.
-__device__ __forceinline__ void mu_lookup(const DGeom &G, int mat, double E, double &mu_tot, double &mu_pe) {
-  const int off = G.mat_off[mat], n = G.mat_n[mat];
-  const double *Eg = G.matE + off, *C = G.matC + off, *P = G.matP + off;
-  double mc, mp;
+// Bin k with E_k <= E < E_{k+1} and its interpolation fraction; clamped ends give
+// (0, 0) below the table and (n-2, 1) above.
+__device__ __forceinline__ void energy_bin(const double *Eg, int n, double E, int &k, double &f) {
   if (E <= Eg[0]) {
-    mc = C[0];
-    mp = P[0];
+    k = 0;
+    f = 0.0;
   } else if (E >= Eg[n - 1]) {
-    mc = C[n - 1];
-    mp = P[n - 1];
+    k = n - 2;
+    f = 1.0;
   } else {
     int lo = 0, hi = n - 1;
 #pragma unroll 1
@@ -525,12 +831,38 @@ __device__ __forceinline__ void mu_lookup(const DGeom &G, int mat, double E, dou
       if (Eg[mid] <= E) lo = mid;
       else hi = mid;
     }
-    const double f = (E - Eg[lo]) / (Eg[lo + 1] - Eg[lo]);
-    mc = C[lo] + f * (C[lo + 1] - C[lo]);
-    mp = P[lo] + f * (P[lo + 1] - P[lo]);
+    k = lo;
+    f = (E - Eg[lo]) / (Eg[lo + 1] - Eg[lo]);
+  }
+}
+
+// Lin-lin interpolation of both coefficients at a known bin.  At the clamped ends
+// the table value is returned exactly.
+__device__ __forceinline__ void mu_at(const DGeom &G, int mat, int k, double f, double &mu_tot, double &mu_pe) {
+  const int off = G.mat_off[mat];
+  const double *C = G.matC + off, *P = G.matP + off;
+  double mc, mp;
+  if (f == 0.0) {
+    mc = C[k];
+    mp = P[k];
+  } else if (f == 1.0) {
+    mc = C[k + 1];
+    mp = P[k + 1];
+  } else {
+    mc = C[k] + f * (C[k + 1] - C[k]);
+    mp = P[k] + f * (P[k + 1] - P[k]);
   }
   mu_tot = mc + mp;
   mu_pe = mp;
+}
+
+// Binary search for E_k <= E < E_{k+1}, lin-lin interpolation, clamped at the ends.
+__device__ __forceinline__ void mu_lookup(const DGeom &G, int mat, double E, double &mu_tot, double &mu_pe) {
+  const int off = G.mat_off[mat], n = G.mat_n[mat];
+  int k;
+  double f;
+  energy_bin(G.matE + off, n, E, k, f);
+  mu_at(G, mat, k, f, mu_tot, mu_pe);
 }
 
 // ---------------------------------------------------------------- Philox4x32-10 and FNV-1a

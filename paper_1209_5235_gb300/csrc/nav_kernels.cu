@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128) k_locate(const DGeom *__restrict__ geoms,
     const V3 u{dir[i], dir[n + i], dir[2 * n + i]};
     int leaf = -2;
     if (bad_dir(u) || !isfinite(x.x + x.y + x.z)) flag(status, kStBadInput);
-    else leaf = locate_world(G, x, u, cnt);
+    else leaf = locate_world<false>(G, x, u, cnt);
     int depth = leaf >= 0 ? G.vol[leaf].depth : (leaf == -1 ? 0 : -1);
     out_depth[i] = depth;
     int v = leaf;
@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(128) k_locate(const DGeom *__restrict__ geoms,
 
 // ---------------------------------------------------------------- compute_step
 
+template <int MODE>
 __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ geoms, int gid, int64_t n,
                                                       const double *__restrict__ pos, const double *__restrict__ dir,
                                                       const int32_t *__restrict__ depth, const int32_t *__restrict__ path,
@@ -108,30 +109,33 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
     }
     const double prop = proposed ? proposed[i] : kInf;
     V3 p, v;
-    world_to_local(G.wxf[leaf], x, u, p, v);
-    int lim;
-    double saf;
+    world_to_local(G.wxf[leaf], G.vol[leaf].flags & kWorldAligned, x, u, p, v);
     bool timeout = false;
-    double s = geom_step(G, leaf, p, v, prop, &lim, &saf, true, cnt, &timeout);
+    const StepResult R = geom_step<MODE, false>(G, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout);
     if (timeout) flag(status, kStTimeout);
-    if (prop < s) {
+    double s = R.step;
+    int lim = R.lim;
+    if (R.physics || prop < s) {
       s = prop;
       lim = G4N_LIM_PHYSICS;
     }
     out_step[i] = s;
-    out_safety[i] = saf;
+    out_safety[i] = R.safety;
     out_lim[i] = lim;
   }
 }
 
 // ---------------------------------------------------------------- transport
 
+enum Phase : int { kEmpty = 0, kStep = 1, kInteract = 2 };
+
 struct Track {
   V3 x, u;
-  double E, Y, len, safety, mu, mupe;
+  Inv3 iu;           // reciprocal of u (used in world-aligned volumes)
+  double E, Y, len, safety, mu, mupe, efrac;
   uint64_t h;
   int64_t tid, gidx;
-  int leaf, item, steps, nzero;
+  int leaf, item, steps, nzero, ebin;
   uint32_t draw;
 };
 
@@ -151,6 +155,8 @@ struct TParams {
   unsigned long long *counters;
   uint64_t *out_hash;
   double *out_len;
+  int refill_min;    // refill a warp's idle lanes once at least this many are idle
+  int interact_min;  // run the interaction phase once at least this many lanes wait for it
 };
 
 __device__ __forceinline__ int find_item(const DItem *items, int n_items, int64_t g) {
@@ -229,33 +235,55 @@ __device__ __forceinline__ void finish(const TParams &P, const Track &t) {
   if (P.out_len) P.out_len[t.gidx] = t.len;
 }
 
-// Start track number g of the concatenated items; false if it ended at once (outside the world).
-__device__ bool start_track(const TParams &P, int64_t g, Track &t, Counters &cnt) {
+// Attenuation of the track's leaf at its energy (cached energy bin when all materials share a grid).
+__device__ __forceinline__ void update_mu(const DGeom &G, Track &t) {
+  if (G.shared_grid) mu_at(G, G.vol[t.leaf].mat, t.ebin, t.efrac, t.mu, t.mupe);
+  else mu_lookup(G, G.vol[t.leaf].mat, t.E, t.mu, t.mupe);
+}
+
+__device__ __forceinline__ void set_energy(const DGeom &G, Track &t, double E) {
+  t.E = E;
+  if (G.shared_grid) energy_bin(G.matE, G.mat_n[0], E, t.ebin, t.efrac);
+}
+
+__device__ __forceinline__ void set_direction(Track &t, const V3 &u) {
+  t.u = u;
+  t.iu = inv_dir(u);
+}
+
+// Start track number g of the concatenated items; returns its phase (kEmpty if it ended at once).
+template <bool COUNT>
+__device__ int start_track(const TParams &P, int64_t g, Track &t, Counters &cnt) {
   t.gidx = g;
   t.item = find_item(P.items, P.n_items, g);
   const DItem &it = P.items[t.item];
   t.tid = it.tid0 + (g - it.start);
   const DGeom &G = P.geoms[it.geom];
-  make_source(it.src, P.seed, t.tid, t.x, t.u, t.E, P.status);
-  tally(P, t, G.n_vol + 1, t.E);
+  V3 u;
+  double E;
+  make_source(it.src, P.seed, t.tid, t.x, u, E, P.status);
+  set_direction(t, u);
+  tally(P, t, G.n_vol + 1, E);
   cnt.c[G4N_C_TRACKS]++;
   t.h = kFnvOffset;
   t.len = 0.0;
   t.steps = 0;
   t.nzero = 0;
   t.safety = 0.0;
-  t.leaf = locate_world(G, t.x, t.u, cnt);
+  t.E = E;
+  t.leaf = locate_world<COUNT>(G, t.x, t.u, cnt);
   if (t.leaf < 0) {
     cnt.c[G4N_C_ESCAPED]++;
     tally(P, t, G.n_vol, t.E);
     t.h = hash_step(t.h, -1, G4N_LIM_MOTHER, kEvEscape);
     finish(P, t);
-    return false;
+    return kEmpty;
   }
   t.draw = 0;
   t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
-  mu_lookup(G, G.vol[t.leaf].mat, t.E, t.mu, t.mupe);
-  return true;
+  set_energy(G, t, E);
+  update_mu(G, t);
+  return kStep;
 }
 
 // Kahn's rejection method for the Klein-Nishina law of eta = E / E'.
@@ -284,7 +312,7 @@ __device__ __forceinline__ bool kahn(double E, uint64_t seed, int64_t tid, uint3
 }
 
 // New direction at polar cosine ct and azimuth (cph, sph) about u.
-__device__ __forceinline__ void deflect(V3 &u, double ct, double cph, double sph) {
+__device__ __forceinline__ V3 deflect(const V3 &u, double ct, double cph, double sph) {
   const double st = sqrt(fmax(0.0, (1.0 - ct) * (1.0 + ct)));
   const double dx = st * cph, dy = st * sph, dz = ct;
   const double perp2 = u.x * u.x + u.y * u.y;
@@ -293,16 +321,17 @@ __device__ __forceinline__ void deflect(V3 &u, double ct, double cph, double sph
     const double nx = (u.x * u.z * dx - u.y * dy) / perp + u.x * dz;
     const double ny = (u.y * u.z * dx + u.x * dy) / perp + u.y * dz;
     const double nz = -perp * dx + u.z * dz;
-    u = V3{nx, ny, nz};
-  } else if (u.z >= 0.0) {
-    u = V3{dx, dy, dz};
-  } else {
-    u = V3{dx, -dy, -dz};
+    return V3{nx, ny, nz};
   }
+  if (u.z >= 0.0) return V3{dx, dy, dz};
+  return V3{dx, -dy, -dz};
 }
 
-// One step of Algorithm 1 for one track; returns false when the history ended.
-__device__ bool step_track(const TParams &P, Track &t, Counters &cnt) {
+// One transport step of Algorithm 1 for one track: the free path (Eq. 7) races
+// the geometric step; a boundary crossing relocates, a physics end point waits
+// for the interaction phase.  Returns the next phase.
+template <int MODE, bool COUNT>
+__device__ int step_track(const TParams &P, Track &t, Counters &cnt) {
   const DItem &it = P.items[t.item];
   const DGeom &G = P.geoms[it.geom];
   if (t.steps >= P.max_steps) {
@@ -310,26 +339,28 @@ __device__ bool step_track(const TParams &P, Track &t, Counters &cnt) {
     flag(P.status, kStStepLimit);
     t.h = hash_step(t.h, t.leaf, kLimStepLimit, kEvStepLimit);
     finish(P, t);
-    return false;
+    return kEmpty;
   }
   const double sphys = t.mu > 0.0 ? t.Y / t.mu : kInf;
-  double s;
+  double s = sphys;
   int lim = G4N_LIM_PHYSICS;
-  bool geo;
+  bool geo = false;
   if (sphys < t.safety) {
-    s = sphys;
-    geo = false;
-    cnt.c[G4N_C_SAFETY_SKIPS]++;
+    diag<COUNT>(cnt, G4N_C_SAFETY_SKIPS);
   } else {
+    const DVol &L = G.vol[t.leaf];
+    const bool aligned = L.flags & kWorldAligned;
     V3 p, v;
-    world_to_local(G.wxf[t.leaf], t.x, t.u, p, v);
-    double saf;
+    world_to_local(G.wxf[t.leaf], aligned, t.x, t.u, p, v);
     bool timeout = false;
-    const double sg = geom_step(G, t.leaf, p, v, sphys, &lim, &saf, true, cnt, &timeout);
+    const StepResult R = geom_step<MODE, COUNT>(G, t.leaf, p, v, aligned ? t.iu : inv_dir(v), sphys, true, cnt, &timeout);
     if (timeout) flag(P.status, kStTimeout);
-    t.safety = saf;
-    geo = sg <= sphys;
-    s = geo ? sg : sphys;
+    t.safety = R.safety;
+    if (!R.physics && R.step <= sphys) {
+      geo = true;
+      s = R.step;
+      lim = R.lim;
+    }
   }
   ++t.steps;
   cnt.c[G4N_C_STEPS]++;
@@ -337,96 +368,114 @@ __device__ bool step_track(const TParams &P, Track &t, Counters &cnt) {
   t.x.y += s * t.u.y;
   t.x.z += s * t.u.z;
   t.len += s;
-  if (geo) {
-    if (t.mu > 0.0) t.Y = fmax(t.Y - s * t.mu, 0.0);
-    cnt.c[G4N_C_GEOM_STEPS]++;
-    t.safety = 0.0;
-    int leaf = relocate(G, t.leaf, t.x, t.u, cnt);
-    t.nzero = (s <= G.half) ? t.nzero + 1 : 0;
-    if (leaf >= 0 && t.nzero >= 10) {
-      const double push = 100.0 * G.tol;
-      t.x.x += push * t.u.x;
-      t.x.y += push * t.u.y;
-      t.x.z += push * t.u.z;
-      t.len += push;
-      cnt.c[G4N_C_PUSHES]++;
-      t.nzero = 0;
-      leaf = relocate(G, leaf, t.x, t.u, cnt);
-      t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
-    }
-    if (leaf < 0) {
-      cnt.c[G4N_C_ESCAPED]++;
-      tally(P, t, G.n_vol, t.E);
-      t.h = hash_step(t.h, -1, lim, kEvEscape);
-      finish(P, t);
-      return false;
-    }
-    t.leaf = leaf;
-    t.h = hash_step(t.h, leaf, lim, kEvNone);
-    mu_lookup(G, G.vol[leaf].mat, t.E, t.mu, t.mupe);
-    return true;
+  if (!geo) {
+    // free path ends inside the volume: the interaction is done in the interaction phase
+    t.safety = fmax(t.safety - s, 0.0);
+    t.nzero = 0;
+    cnt.c[G4N_C_PHYS_STEPS]++;
+    return kInteract;
   }
-  // interaction at the end of the free path
-  t.safety = fmax(t.safety - s, 0.0);
-  t.nzero = 0;
-  cnt.c[G4N_C_PHYS_STEPS]++;
+  if (t.mu > 0.0) t.Y = fmax(t.Y - s * t.mu, 0.0);
+  cnt.c[G4N_C_GEOM_STEPS]++;
+  t.safety = 0.0;
+  int leaf = relocate<MODE, COUNT>(G, t.leaf, t.x, t.u, lim == G4N_LIM_MOTHER && s > 0.0, cnt);
+  t.nzero = (s <= G.half) ? t.nzero + 1 : 0;
+  if (leaf >= 0 && t.nzero >= 10) {
+    const double push = 100.0 * G.tol;
+    t.x.x += push * t.u.x;
+    t.x.y += push * t.u.y;
+    t.x.z += push * t.u.z;
+    t.len += push;
+    cnt.c[G4N_C_PUSHES]++;
+    t.nzero = 0;
+    leaf = relocate<MODE, COUNT>(G, leaf, t.x, t.u, false, cnt);
+    t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
+  }
+  if (leaf < 0) {
+    cnt.c[G4N_C_ESCAPED]++;
+    tally(P, t, G.n_vol, t.E);
+    t.h = hash_step(t.h, -1, lim, kEvEscape);
+    finish(P, t);
+    return kEmpty;
+  }
+  t.leaf = leaf;
+  t.h = hash_step(t.h, leaf, lim, kEvNone);
+  update_mu(G, t);
+  return kStep;
+}
+
+// The interaction at the end of a free path: photoabsorption if U mu_tot < mu_photo,
+// else a Compton scatter (Kahn), the cutoff, and a new Y = -log W.
+__device__ int interact(const TParams &P, Track &t, Counters &cnt) {
+  const DItem &it = P.items[t.item];
+  const DGeom &G = P.geoms[it.geom];
   const double U = philox_uniform(P.seed, t.tid, 1, t.draw);
   if (U * t.mu < t.mupe) {
     cnt.c[G4N_C_PHOTO]++;
     tally(P, t, t.leaf, t.E);
     t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvPhoto);
     finish(P, t);
-    return false;
+    return kEmpty;
   }
   cnt.c[G4N_C_COMPTON]++;
   double eta, cost, cph, sph;
   bool ok = kahn(t.E, P.seed, t.tid, t.draw, eta, cost);
   ok &= disc_azimuth(P.seed, t.tid, 1, t.draw, cph, sph);
   if (!ok) flag(P.status, kStRejection);
-  deflect(t.u, cost, cph, sph);
+  set_direction(t, deflect(t.u, cost, cph, sph));
   const double E1 = t.E / eta;
   if (E1 < P.cutoff) {
     cnt.c[G4N_C_CUTOFF]++;
     tally(P, t, t.leaf, t.E);
     t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCutoff);
     finish(P, t);
-    return false;
+    return kEmpty;
   }
   tally(P, t, t.leaf, t.E - E1);
-  t.E = E1;
+  set_energy(G, t, E1);
   t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
   t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCompton);
-  mu_lookup(G, G.vol[t.leaf].mat, t.E, t.mu, t.mupe);
-  return true;
+  update_mu(G, t);
+  return kStep;
 }
 
-__global__ void __launch_bounds__(128) k_transport(const TParams P) {
+// Persistent transport: every lane carries one track in registers.  Each round a
+// warp (1) refills its idle lanes from the device queue when enough are idle (one
+// atomic per refill), (2) runs the interaction phase when enough lanes wait for
+// it, (3) advances every stepping lane by one step.  Deferring the long
+// interaction and start-up code until many lanes need it keeps the warp's lanes
+// on the same code; the order of operations inside each history is unchanged.
+template <int MODE, bool COUNT>
+__global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
   Counters cnt;
 #pragma unroll
   for (int k = 0; k < G4N_N_COUNTERS; ++k) cnt.c[k] = 0;
   const unsigned lane = threadIdx.x & 31u;
   Track t;
-  bool active = false, drained = false;
+  int phase = kEmpty;
+  bool drained = false;
 #pragma unroll 1
   for (;;) {
-    // refill idle lanes from the device queue: one atomic per warp
-    const unsigned idle = __ballot_sync(0xffffffffu, !active);
-    if (idle && !drained) {
+    const unsigned idle = __ballot_sync(0xffffffffu, phase == kEmpty);
+    const unsigned busy = ~idle;
+    if (idle && !drained && (__popc(idle) >= P.refill_min || busy == 0)) {
       const int leader = __ffs(idle) - 1;
       unsigned long long base = 0;
       if ((int)lane == leader) base = atomicAdd(P.q_head, (unsigned long long)__popc(idle));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (base + __popc(idle) >= (unsigned long long)P.total) drained = true;
-      if (!active) {
+      if (phase == kEmpty) {
         const int64_t g = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
-        if (g < P.total) active = start_track(P, g, t, cnt);
+        if (g < P.total) phase = start_track<COUNT>(P, g, t, cnt);
       }
     }
-    if (!__any_sync(0xffffffffu, active)) {
-      if (drained) break;
-      continue;
+    const unsigned waiting = __ballot_sync(0xffffffffu, phase == kInteract);
+    const unsigned stepping = __ballot_sync(0xffffffffu, phase == kStep);
+    if (waiting && (__popc(waiting) >= P.interact_min || stepping == 0)) {
+      if (phase == kInteract) phase = interact(P, t, cnt);
     }
-    if (active) active = step_track(P, t, cnt);
+    if (phase == kStep) phase = step_track<MODE, COUNT>(P, t, cnt);
+    if (drained && __ballot_sync(0xffffffffu, phase != kEmpty) == 0) break;
   }
   // flush counters: warp reduction, one atomic per counter per warp
 #pragma unroll
@@ -436,6 +485,13 @@ __global__ void __launch_bounds__(128) k_transport(const TParams P) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0 && v) atomicAdd(&P.counters[k], v);
   }
+}
+
+using TransportKernel = void (*)(const TParams);
+
+TransportKernel transport_kernel(int mode, bool count) {
+  if (mode == G4N_MODE_FP64) return count ? k_transport<kFP64, true> : k_transport<kFP64, false>;
+  return count ? k_transport<kFP32, true> : k_transport<kFP32, false>;
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -465,6 +521,18 @@ int ensure_ws(g4n_ctx *ctx, size_t item_bytes) {
 int launch_error(g4n_ctx *ctx, const char *what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return g4n_fail(ctx, G4N_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return G4N_OK;
+}
+
+// Launch shape of a transport batch (validated); 0 fields take the defaults.
+int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refill, int *inter) {
+  *block = b->block_size > 0 ? b->block_size : 128;
+  if (*block % 32 || *block > 128) return g4n_fail(ctx, G4N_ERR_ARG, "transport: block_size must be a multiple of 32, <= 128");
+  *refill = b->refill_min > 0 ? b->refill_min : 8;
+  *inter = b->interact_min > 0 ? b->interact_min : 8;
+  if (*refill > 32 || *inter > 32) return g4n_fail(ctx, G4N_ERR_ARG, "transport: refill_min/interact_min must be 1..32");
+  if (b->mode != G4N_MODE_FP64 && b->mode != G4N_MODE_FP32_RECHECK)
+    return g4n_fail(ctx, G4N_ERR_ARG, "transport: mode must be G4N_MODE_FP64 or G4N_MODE_FP32_RECHECK");
   return G4N_OK;
 }
 
@@ -499,15 +567,17 @@ int g4n_compute_step(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, c
   int rc = check_geom(ctx, geom);
   if (rc) return rc;
   if (n < 0) return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: n < 0");
-  if (mode != G4N_MODE_FP64) return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: mode not available");
+  if (mode != G4N_MODE_FP64 && mode != G4N_MODE_FP32_RECHECK)
+    return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: mode must be G4N_MODE_FP64 or G4N_MODE_FP32_RECHECK");
   if (n == 0) return G4N_OK;
   if (!pos || !dir || !depth || !path || !out_step || !out_safety || !out_limiter)
     return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: null array");
   if ((rc = ensure_ws(ctx, 0))) return rc;
   cudaSetDevice(ctx->device);
   Workspace *ws = (Workspace *)ctx->ws;
-  k_compute_step<<<grid_for(ctx, n, 128), 128, 0, (cudaStream_t)stream>>>(
-      ctx->d_geoms, geom, n, pos, dir, depth, path, proposed, out_step, out_safety, out_limiter, &ws->status);
+  auto kern = mode == G4N_MODE_FP64 ? k_compute_step<kFP64> : k_compute_step<kFP32>;
+  kern<<<grid_for(ctx, n, 128), 128, 0, (cudaStream_t)stream>>>(ctx->d_geoms, geom, n, pos, dir, depth, path, proposed,
+                                                                 out_step, out_safety, out_limiter, &ws->status);
   return launch_error(ctx, "compute_step launch");
 }
 
@@ -516,7 +586,8 @@ int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep,
   if (!ctx || !b) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null argument");
   if (b->n_items < 1 || !b->items) return g4n_fail(ctx, G4N_ERR_ARG, "transport: no work items");
   if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null output");
-  if (b->mode != G4N_MODE_FP64) return g4n_fail(ctx, G4N_ERR_ARG, "transport: mode not available");
+  int block, refill, inter;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter)) return rc0;
   if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport: n_tally_batches < 1");
   if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: cutoff must be >= 0");
   std::vector<DItem> items(b->n_items);
@@ -575,17 +646,18 @@ int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep,
   P.counters = (unsigned long long *)out_counters;
   P.out_hash = out_track_hash;
   P.out_len = out_track_len;
-  const int block = b->block_size > 0 ? b->block_size : 128;
-  if (block % 32 || block > 128) return g4n_fail(ctx, G4N_ERR_ARG, "transport: block_size must be a multiple of 32, <= 128");
+  P.refill_min = refill;
+  P.interact_min = inter;
+  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
   int per_sm = b->blocks_per_sm;
   if (per_sm <= 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
     per_sm = std::max(per_sm, 1);
   }
   int64_t grid = (int64_t)ctx->sm_count * per_sm;
   const int64_t need = (total + block - 1) / block;
   grid = std::max<int64_t>(1, std::min(grid, need));
-  k_transport<<<(int)grid, block, 0, st>>>(P);
+  kern<<<(int)grid, block, 0, st>>>(P);
   return launch_error(ctx, "transport launch");
 }
 
@@ -700,7 +772,8 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: more than G4N_NOALLOC_MAX_ITEMS (" +
                                           std::to_string(G4N_NOALLOC_MAX_ITEMS) + ") work items; use g4n_transport_batch");
   if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: null output");
-  if (b->mode != G4N_MODE_FP64) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: mode not available");
+  int block, refill, inter;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter)) return rc0;
   if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: n_tally_batches < 1");
   if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: cutoff must be >= 0");
   DItem items[G4N_NOALLOC_MAX_ITEMS];  // host staging on the stack: no heap either
@@ -734,9 +807,6 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     std::memcpy(d.src, src, sizeof(src));
     total += w.n_tracks;
   }
-  const int block = b->block_size > 0 ? b->block_size : 128;
-  if (block % 32 || block > 128)
-    return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: block_size must be a multiple of 32, <= 128");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_CUDA, "transport_noalloc: cudaSetDevice failed");
   unsigned char *scratch = nullptr;
   int rc = noalloc_scratch(ctx, ctx->device, &scratch);
@@ -765,14 +835,17 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     P.counters = (unsigned long long *)out_counters;
     P.out_hash = out_track_hash;
     P.out_len = out_track_len;
+    P.refill_min = refill;
+    P.interact_min = inter;
+    const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
     int per_sm = b->blocks_per_sm;
     if (per_sm <= 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport, block, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
       per_sm = std::max(per_sm, 1);
     }
     int64_t grid = (int64_t)ctx->sm_count * per_sm;
     grid = std::max<int64_t>(1, std::min(grid, (total + block - 1) / block));
-    k_transport<<<(int)grid, block, 0, st>>>(P);
+    kern<<<(int)grid, block, 0, st>>>(P);
     rc = launch_error(ctx, "transport_noalloc launch");
     if (rc) return rc;
   }

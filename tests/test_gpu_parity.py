@@ -65,8 +65,12 @@ def test_locate_parity(env, name):
     assert (d_ref >= 2).sum() > 0  # the cases do reach daughters
 
 
+MODES = [0, 1]   # G4N_MODE_FP64, G4N_MODE_FP32_RECHECK
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name", list(SCENES))
-def test_compute_step_parity(env, name):
+def test_compute_step_parity(env, name, mode):
     g4, torch, ctx = env
     sc, og, gid = _build(env, name)
     n = 3000 if name in ("calorimeter", "spheres") else 20000
@@ -79,7 +83,7 @@ def test_compute_step_parity(env, name):
     s_ref, l_ref, _ = og.compute_step_many(p, v, d_ref, path_ref, prop)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
     s, saf, lim = g4.g4n_compute_step(ctx, gid, to_soa(p, torch), to_soa(v, torch), T(d_ref.astype(np.int32)),
-                                      T(np.ascontiguousarray(path_ref.T).astype(np.int32)), T(prop))
+                                      T(np.ascontiguousarray(path_ref.T).astype(np.int32)), T(prop), mode=mode)
     g4.g4n_sync(ctx)
     s, saf, lim = s.cpu().numpy(), saf.cpu().numpy(), lim.cpu().numpy()
     badl = np.nonzero(lim != l_ref)[0]
@@ -98,7 +102,7 @@ def test_compute_step_parity(env, name):
         assert np.all(dq == d_ref[i]) and np.all(pq == path_ref[i]), (i, p[i], saf[i])
     # geometry wins a tie with the proposed step
     s2, _, lim2 = g4.g4n_compute_step(ctx, gid, to_soa(p, torch), to_soa(v, torch), T(d_ref.astype(np.int32)),
-                                      T(np.ascontiguousarray(path_ref.T).astype(np.int32)), T(s))
+                                      T(np.ascontiguousarray(path_ref.T).astype(np.int32)), T(s), mode=mode)
     lim2 = lim2.cpu().numpy()
     geo = lim != g4.G4N_LIM_PHYSICS
     assert np.array_equal(lim2[geo], lim[geo])
@@ -138,9 +142,10 @@ def _compare_transport(g4, r, edep, cnt, h, ln, nv, exact_tally_rel=1e-9):
         assert abs(dg[:nv + 1].sum() - dg[nv + 1]) <= 1e-9 * dg[nv + 1]
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name,n", [("tiny", 10000), ("calorimeter", 20000), ("mixed_smart", 20000),
                                     ("barrel", 20000), ("nested", 20000), ("spheres", 5000)])
-def test_transport_parity(env, name, n):
+def test_transport_parity(env, name, n, mode):
     g4, torch, ctx = env
     sc, og, gid = _build(env, name)
     src = {"tiny": synth.scenes.tiny_source(), "calorimeter": synth.scenes.calorimeter_source(),
@@ -148,12 +153,13 @@ def test_transport_parity(env, name, n):
                                                                    e_kind="loguniform", e0=0.05, e1=5.0))
     seed = 0x7A0C0000
     r = og.transport(src, seed, n, threads=0)
-    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n)
+    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, diagnostics=(mode == 1))
     g4.g4n_sync(ctx)
     _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
 
 
-def test_transport_calorimeter_full_size_sampled(env):
+@pytest.mark.parametrize("mode", MODES)
+def test_transport_calorimeter_full_size_sampled(env, mode):
     """The benchmark workload (10^6 tracks, default launch shape): sampled histories replayed one by one
     by the oracle must match bit for bit; whole-run invariants hold at full size."""
     g4, torch, ctx = env
@@ -161,7 +167,7 @@ def test_transport_calorimeter_full_size_sampled(env):
     src = synth.scenes.calorimeter_source()
     seed = synth.scenes.CONFIG_SEEDS[1][1]
     n = 1_000_000
-    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n)
+    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode)
     g4.g4n_sync(ctx)
     hashes = h.cpu().numpy().view(np.uint64)
     lens = ln.cpu().numpy()
@@ -204,8 +210,9 @@ def test_transport_edge_cases(env):
     _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
     # odd launch shapes give identical histories
     r = og.transport(src, 7, 3001)
-    for bs, per_sm in ((32, 1), (96, 3), (128, 0)):
-        edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, 7, 3001, block_size=bs, blocks_per_sm=per_sm)
+    for bs, per_sm, rm, im, mode in ((32, 1, 1, 1, 0), (96, 3, 32, 32, 1), (128, 0, 0, 0, 1), (64, 2, 5, 17, 0)):
+        edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, 7, 3001, block_size=bs, blocks_per_sm=per_sm,
+                                          refill_min=rm, interact_min=im, mode=mode)
         g4.g4n_sync(ctx)
         _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
 
