@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "navigation steps/sec and γ tracks/sec on 1 GB300; chosen vs plain at matched results"
 WORKLOAD = ("sampling calorimeter: 50 alternating 5 mm lead-like / 10 mm scintillator-like layers x 10x10 "
-            "box cells of 100x100 mm (5000 cells) in a 2 m vacuum world, two voxel levels (z 50, x 10); "
+            "box cells of 100x100 mm (5000 cells) in a 2 m vacuum world, smart voxels; "
             "gamma energy U(0.1, 10) MeV along +z, Gaussian spot sigma 10 mm; Compton (Kahn) + photoabsorption, "
             "10 keV cutoff; per-cell energy deposit in 100 batches")
 
@@ -110,9 +110,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def calorimeter():
+def parse_voxel(spec: str):
+    """'default' | 'smart' | 'fixed:AXES:SLICES' e.g. fixed:2,0:51,11 (z then x)."""
+    from synth.scenes import VoxelSpec
+    if spec in ("default", ""):
+        return None
+    if spec == "smart":
+        return VoxelSpec(mode="smart")
+    _, axes, slices = spec.split(":")
+    return VoxelSpec(mode="fixed", axes=tuple(int(a) for a in axes.split(",")),
+                     slices=tuple(int(x) for x in slices.split(",")))
+
+
+def calorimeter(voxel: str = "default"):
     import synth
-    sc = synth.scenes.calorimeter_scene()
+    sc = synth.scenes.calorimeter_scene(voxel=parse_voxel(voxel))
     return sc, synth.scenes.calorimeter_source(), synth.scenes.CONFIG_SEEDS[1][1]
 
 
@@ -203,7 +215,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     b.build()
-    sc, src, seed = calorimeter()
+    sc, src, seed = calorimeter(args.voxel)
     ctx = g4.g4n_create(local)
     gid = g4.build_scene(ctx, sc)
     n = args.tracks
@@ -293,7 +305,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "tracks_per_gpu": n, "mode": chosen,
                    "l2": "flushed between timed steps (256 MB write)", "block": args.block or 128,
                    "blocks_per_sm": args.blocks_per_sm or "occupancy", "refill_min": args.refill_min or 8,
-                   "interact_min": args.interact_min or 8},
+                   "interact_min": args.interact_min or 8, "voxel": args.voxel},
         "tracks_per_s": R["tracks_per_s"],
         "steps_per_track": R["steps_per_track"],
         "modes": results,
@@ -332,6 +344,7 @@ def main():
     ap.add_argument("--refill-min", type=int, default=0)
     ap.add_argument("--interact-min", type=int, default=0)
     ap.add_argument("--mode", default="auto", choices=["auto", "fp64", "fp32_recheck"])
+    ap.add_argument("--voxel", default="smart")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -79,7 +79,12 @@ enum {
   G4N_C_VOX_NODES,           /* voxel nodes visited by the boundary search */
   G4N_C_RECHECKS,            /* FP64 rechecks in FP32_RECHECK mode */
   G4N_C_PROPOSALS,           /* learned proposals used */
-  G4N_C_PRUNED               /* candidates skipped by the proposal bound */
+  G4N_C_PRUNED,              /* candidates skipped by the proposal bound */
+  G4N_C_CYC_REFILL = 26,     /* warp clock cycles spent refilling idle lanes (diagnostics) */
+  G4N_C_CYC_INTERACT,        /* warp clock cycles spent in the interaction phase */
+  G4N_C_CYC_STEP,            /* warp clock cycles spent in the step phase */
+  G4N_C_STEP_LANES,          /* sum over step phases of the lanes stepping */
+  G4N_C_STEP_PHASES          /* number of step phases */
 };
 
 /* ---------------------------------------------------------------- context */

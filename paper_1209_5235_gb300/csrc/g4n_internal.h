@@ -26,7 +26,8 @@ constexpr int kDMax = G4N_DMAX;
 constexpr int kMaxLevels = 3;
 
 enum SolidKind : int32_t { kBox = 0, kTube = 1, kOrb = 2 };
-enum VolFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4, kWorldAligned = 8 };  // tube bits; world rotation is identity
+// tube bits; world rotation is identity; placement rotation (mother -> local) is identity
+enum VolFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4, kWorldAligned = 8, kPlacedAligned = 16 };
 
 struct alignas(128) DVol {
   double tx, ty, tz, c, s;  // placement: local = R(theta)^T (mother - t)

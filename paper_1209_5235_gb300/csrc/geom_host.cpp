@@ -460,6 +460,7 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
       g->vol[pl.mother].n_dau++;
     }
     if (w.c == 1.0 && w.s == 0.0) v.flags |= kWorldAligned;
+    if (pl.c == 1.0 && pl.s == 0.0) v.flags |= kPlacedAligned;
     if (v.depth > kDMax) {
       delete g;
       return g4n_fail(ctx, G4N_ERR_GEOM, "finalize: hierarchy deeper than G4N_DMAX at volume " + std::to_string(i));

@@ -60,6 +60,11 @@ __device__ __forceinline__ void diag_kind(Counters &c, int kind) {
 
 __device__ __forceinline__ void to_local(const DVol &v, const V3 &pm, const V3 &vm, V3 &pl, V3 &vl) {
   const double dx = pm.x - v.tx, dy = pm.y - v.ty;
+  if (v.flags & kPlacedAligned) {
+    pl = V3{dx, dy, pm.z - v.tz};
+    vl = vm;
+    return;
+  }
   pl.x = v.c * dx + v.s * dy;
   pl.y = v.c * dy - v.s * dx;
   pl.z = pm.z - v.tz;
@@ -560,100 +565,130 @@ __device__ __forceinline__ int vox_lookup(const DGeom &G, int h, const V3 &p) {
   return 0;
 }
 
+// Warp-collective navigation.  Every lane of the warp must call these functions
+// together (they synchronise with __syncwarp / __any_sync over the full warp);
+// lanes with `active` false only take part in the synchronisation.  The point is
+// SIMT efficiency: each round every searching lane first scans its candidate list
+// in cheap FP32/integer code to the next candidate that needs FP64 work, then the
+// warp meets and all those lanes run the FP64 test together.
+constexpr unsigned kFull = 0xffffffffu;
+
 // Descend from volume m (p, v in m's frame) into the first daughter, in id order,
 // that contains the point; repeat.  `blocked` is a daughter of m already known
-// not to contain the point (the volume just left).  Each round scans the node's
-// list with the FP32 box test, then the lanes that found a candidate run the
-// FP64 Inside test together.
+// not to contain the point (the volume just left).  Returns the deepest volume.
 template <bool COUNT>
-__device__ __forceinline__ int descend(const DGeom &G, int m, V3 p, V3 v, int blocked, Counters &cnt) {
+__device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, V3 p, V3 v, int blocked,
+                                            Counters &cnt) {
 #pragma unroll 1
   for (int lev = 0; lev < kDMax; ++lev) {
-    const int h = G.vol[m].vox;
-    if (h < 0) return m;
-    const DCandList L = G.clist[vox_lookup(G, h, p)];
-    const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
+    const bool want = active && G.vol[m].vox >= 0;
+    if (!__any_sync(kFull, want)) break;
+    DCandList L{0, 0};
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (want) {
+      L = G.clist[vox_lookup(G, G.vol[m].vox, p)];
+      px = (float)p.x;
+      py = (float)p.y;
+      pz = (float)p.z;
+    }
     int i = 0, found = -1;
-    V3 fp, fv;
+    bool searching = want;
+    V3 fp = p, fv = v;
 #pragma unroll 1
-    for (;;) {
+    while (__any_sync(kFull, searching)) {
       int d = -1;
+      if (searching) {
 #pragma unroll 1
-      while (i < L.count) {
-        const int c = __ldg(&G.cand[L.offset + i]);
-        ++i;
-        if (c != blocked && box32_contains(G.box[c], px, py, pz)) {
-          d = c;
-          break;
+        while (i < L.count) {
+          const int c = __ldg(&G.cand[L.offset + i]);
+          ++i;
+          if (c != blocked && box32_contains(G.box[c], px, py, pz)) {
+            d = c;
+            break;
+          }
+        }
+        if (d < 0) searching = false;
+      }
+      __syncwarp();
+      if (d >= 0) {
+        const DVol &D = G.vol[d];
+        V3 dp, dv;
+        to_local(D, p, v, dp, dv);
+        diag<COUNT>(cnt, G4N_C_INSIDE);
+        if (vol_inside(D, dp, dv, G.half)) {
+          found = d;
+          fp = dp;
+          fv = dv;
+          searching = false;
         }
       }
-      if (d < 0) break;
-      const DVol &D = G.vol[d];
-      V3 dp, dv;
-      to_local(D, p, v, dp, dv);
-      diag<COUNT>(cnt, G4N_C_INSIDE);
-      if (vol_inside(D, dp, dv, G.half)) {
-        found = d;
-        fp = dp;
-        fv = dv;
-        break;
-      }
     }
-    if (found < 0) return m;
-    m = found;
-    p = fp;
-    v = fv;
-    blocked = -1;
+    if (want && found >= 0) {
+      m = found;
+      p = fp;
+      v = fv;
+      blocked = -1;
+    } else {
+      active = false;
+    }
   }
   return m;
 }
 
-// Locate from the world: returns the leaf, or -1 outside the world.
+// Locate from the world (warp-collective): the leaf, or -1 outside the world.
 template <bool COUNT>
-__device__ __forceinline__ int locate_world(const DGeom &G, const V3 &x, const V3 &u, Counters &cnt) {
-  V3 p, v;
-  world_to_local(G.wxf[0], G.vol[0].flags & kWorldAligned, x, u, p, v);
-  diag<COUNT>(cnt, G4N_C_INSIDE);
-  if (!vol_inside(G.vol[0], p, v, G.half)) return -1;
-  return descend<COUNT>(G, 0, p, v, -1, cnt);
+__device__ __forceinline__ int locate_world_warp(const DGeom &G, bool active, const V3 &x, const V3 &u, Counters &cnt) {
+  V3 p{0, 0, 0}, v{0, 0, 1};
+  bool in = false;
+  if (active) {
+    world_to_local(G.wxf[0], G.vol[0].flags & kWorldAligned, x, u, p, v);
+    diag<COUNT>(cnt, G4N_C_INSIDE);
+    in = vol_inside(G.vol[0], p, v, G.half);
+  }
+  const int leaf = descend_warp<COUNT>(G, in, 0, p, v, -1, cnt);
+  return in ? leaf : -1;
 }
 
-// After a move: leave every volume that no longer contains the point, then
-// descend.  A step that ended on the leaf's own exit surface (limiter mother,
-// positive length) leaves the leaf for certain: the point is on that surface
-// moving outward, so the leaf's Inside test is false and is skipped.  A volume
-// left on the way up is blocked in the descent below its mother (its Inside is
-// already known to be false).
+// After a move (warp-collective): leave every volume that no longer contains the
+// point, then descend.  A step that ended on the leaf's own exit surface (limiter
+// mother, positive length) leaves the leaf for certain: the point is on that
+// surface moving outward, so the leaf's Inside test is false and is skipped.  A
+// volume left on the way up is blocked in the descent below its mother (its
+// Inside is already known to be false).  Returns the new leaf or -1 (left the world).
 template <int MODE, bool COUNT>
-__device__ __forceinline__ int relocate(const DGeom &G, int leaf, const V3 &x, const V3 &u, bool left_leaf,
-                                        Counters &cnt) {
+__device__ __forceinline__ int relocate_warp(const DGeom &G, bool active, int leaf, const V3 &x, const V3 &u,
+                                             bool left_leaf, Counters &cnt) {
   int blocked = -1;
-  if (left_leaf) {
+  if (active && left_leaf) {
     blocked = leaf;
     leaf = G.vol[leaf].mother;
   }
+  bool up = active && leaf >= 0;
+  bool in = false;
+  V3 p{0, 0, 0}, v{0, 0, 1};
 #pragma unroll 1
-  while (leaf >= 0) {
-    const DVol &L = G.vol[leaf];
-    V3 p, v;
-    world_to_local(G.wxf[leaf], L.flags & kWorldAligned, x, u, p, v);
-    bool in;
-    if (MODE == kFP32) {
-      const Ray32 r = make_ray32(p, v);
-      in = certainly_inside32(L, r, (float)(4.0 * G.half) + 1e-30f);
-      if (!in) {
+  while (__any_sync(kFull, up)) {
+    if (up) {
+      const DVol &L = G.vol[leaf];
+      world_to_local(G.wxf[leaf], L.flags & kWorldAligned, x, u, p, v);
+      bool ok = false;
+      if (MODE == kFP32) ok = certainly_inside32(L, make_ray32(p, v), (float)(4.0 * G.half) + 1e-30f);
+      if (!ok) {
         diag<COUNT>(cnt, G4N_C_INSIDE);
-        in = vol_inside(L, p, v, G.half);
+        ok = vol_inside(L, p, v, G.half);
       }
-    } else {
-      diag<COUNT>(cnt, G4N_C_INSIDE);
-      in = vol_inside(L, p, v, G.half);
+      if (ok) {
+        in = true;
+        up = false;
+      } else {
+        blocked = leaf;
+        leaf = L.mother;
+        if (leaf < 0) up = false;
+      }
     }
-    if (in) return descend<COUNT>(G, leaf, p, v, blocked, cnt);
-    blocked = leaf;
-    leaf = L.mother;
   }
-  return -1;
+  const int out = descend_warp<COUNT>(G, in, in ? leaf : 0, p, v, blocked, cnt);
+  return in ? out : -1;
 }
 
 // Voxel walk state: per level the header, the merged node's slice range.
@@ -684,131 +719,152 @@ __device__ __forceinline__ void chain_fill(const DGeom &G, Chain &ch, int lev, i
 }
 
 struct StepResult {
-  double step;    // geometric step (valid when it is <= limit or when physics_sure is false)
+  double step;    // geometric step (exact when it is <= the limit)
   double safety;  // isotropic lower bound
   int lim;        // daughter id or G4N_LIM_MOTHER
-  bool physics;   // FP32 mode: proven that the limit comes first (no geometry evaluated in FP64)
+  bool physics;   // FP32 mode: proven that the limit comes first (no FP64 geometry done)
 };
 
-// Geometric step inside `leaf` from local point p along v (Sec. 3.2, problem 2):
-// DistanceToOut of the leaf, then DistanceToIn of the daughters listed in the
-// voxel nodes the ray crosses, stopping once the node exit lies beyond the best
-// distance or `limit`.  FP64 mode: every candidate in FP64.  FP32 mode: a
-// candidate is evaluated in FP64 only if its FP32 entry bound does not exceed the
-// best exact distance so far, and no FP64 geometry at all is done when the
-// bounds prove that `limit` comes first.  Both modes return the FP64 result.
+// Geometric step inside `leaf` from local point p along v (Sec. 3.2, problem 2),
+// warp-collective: DistanceToOut of the leaf, then DistanceToIn of the daughters
+// listed in the voxel nodes the ray crosses, stopping once the node exit lies
+// beyond the best distance or `limit`.  FP64 mode: every candidate in FP64.  FP32
+// mode: a candidate is evaluated in FP64 only if its FP32 entry bound does not
+// exceed the best exact distance so far, and no FP64 geometry at all is done when
+// the bounds prove that `limit` comes first.  Both return the FP64 result.
 template <int MODE, bool COUNT>
-__device__ __forceinline__ StepResult geom_step(const DGeom &G, int leaf, const V3 &p, const V3 &v, const Inv3 &iv,
-                                                double limit, bool want_safety, Counters &cnt, bool *timeout) {
-  const DVol &V = G.vol[leaf];
+__device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active, int leaf, const V3 &p, const V3 &v,
+                                                     const Inv3 &iv, double limit, bool want_safety, Counters &cnt,
+                                                     bool *timeout) {
   const double half = G.half;
-  StepResult R;
-  R.physics = false;
-  R.lim = G4N_LIM_MOTHER;
-  double best;       // best exact candidate distance so far
-  double stop;       // the walk may stop once a node exit reaches this
+  StepResult R{kInf, 0.0, G4N_LIM_MOTHER, false};
+  double best = kInf, stop = 0.0, tout = kInf;
   float out_lo = 0.f;
   Ray32 r;
-  if (MODE == kFP32) {
-    r = make_ray32(p, v);
-    float out_hi, saf32;
-    exit_bounds32(V, r, p, &out_lo, &out_hi, &saf32);
-    R.safety = saf32;
-    best = kInf;
-    stop = fmin(limit, (double)out_hi);
-  } else {
-    diag<COUNT>(cnt, G4N_C_DIST_OUT);
-    best = vol_dist_out(V, p, v, iv, half);
-    R.safety = want_safety ? vol_safety_out(V, p) : 0.0;
-    stop = fmin(limit, best);
-  }
-  int bl = G4N_LIM_MOTHER;
-  if (V.vox >= 0) {
-    Chain ch;
-    chain_fill(G, ch, 0, V.vox, p);
-    bool first = true;
-#pragma unroll 1
-    for (int it = 0; it < 1 << 16; ++it) {
+  Chain ch;
+  bool walking = false, first = true;
+  int i = 0, it = 0, bl = G4N_LIM_MOTHER;
+  DCandList L{0, 0};
+  if (active) {
+    const DVol &V = G.vol[leaf];
+    if (MODE == kFP32) {
+      r = make_ray32(p, v);
+      float out_hi, saf32;
+      exit_bounds32(V, r, p, &out_lo, &out_hi, &saf32);
+      R.safety = saf32;
+      stop = fmin(limit, (double)out_hi);
+    } else {
+      diag<COUNT>(cnt, G4N_C_DIST_OUT);
+      tout = vol_dist_out(V, p, v, iv, half);
+      R.safety = want_safety ? vol_safety_out(V, p) : 0.0;
+      stop = fmin(limit, tout);
+    }
+    if (V.vox >= 0) {
+      chain_fill(G, ch, 0, V.vox, p);
+      L = G.clist[ch.list];
+      walking = true;
       diag<COUNT>(cnt, G4N_C_VOX_NODES);
-      const DCandList L = G.clist[ch.list];
-#pragma unroll 1
-      for (int i = 0; i < L.count; ++i) {
-        const int d = __ldg(&G.cand[L.offset + i]);
-        if (MODE == kFP32) {
-          const DBox32 B = G.box[d];
-          if (first && want_safety) R.safety = fmin(R.safety, (double)box_gap_lb(B.lo, B.hi, r));
-          const float lb = box_entry_lb(B.lo, B.hi, r, nullptr);
-          if (!((double)lb <= fmin(best, stop))) continue;
-          diag<COUNT>(cnt, G4N_C_RECHECKS);
-        }
-        const DVol &D = G.vol[d];
-        V3 dp, dv;
-        to_local(D, p, v, dp, dv);
-        diag_kind<COUNT>(cnt, D.kind);
-        const double t = vol_dist_in(D, dp, dv, half);
-        if (t < kInf && (t < best || (t == best && (bl < 0 || d < bl)))) {
-          best = t;
-          bl = d;
-        }
-        if (MODE == kFP64 && first && want_safety) R.safety = fmin(R.safety, vol_safety_in(D, dp));
-      }
-      // exit of the current node along the ray; node slab boundaries bound the safety
-      double texit = kInf;
-      int lstar = -1;
-#pragma unroll 1
-      for (int l = 0; l < ch.nlev; ++l) {
-        const DVoxHdr H = G.hdr[ch.h[l]];
-        const double pa = comp(p, H.axis), va = comp(v, H.axis);
-        const double blo = H.lo + ch.k0[l] * H.width, bhi = H.lo + (ch.k1[l] + 1) * H.width;
-        if (first && want_safety) R.safety = fmin(R.safety, fmax(fmin(pa - blo, bhi - pa), 0.0));
-        double t = kInf;
-        if (va > 0.0) t = (bhi - pa) * icomp(iv, H.axis);
-        else if (va < 0.0) t = (blo - pa) * icomp(iv, H.axis);
-        if (t < texit) {
-          texit = t;
-          lstar = l;
-        }
-      }
-      first = false;
-      if (!(texit < fmin(best, stop))) break;
-      // step into the neighbouring node at level lstar; deeper levels are looked up again
-      const DVoxHdr H = G.hdr[ch.h[lstar]];
-      const int nk = comp(v, H.axis) > 0.0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
-      if (nk < 0 || nk >= H.nslices) break;
-      const DVoxSlice S = G.slice[H.slice_base + nk];
-      ch.k0[lstar] = S.k0;
-      ch.k1[lstar] = S.k1;
-      if (S.child >= 0) {
-        ch.nlev = lstar + 1;
-        ch.list = S.child;
-      } else {
-        const V3 qpt{p.x + texit * v.x, p.y + texit * v.y, p.z + texit * v.z};
-        chain_fill(G, ch, lstar + 1, -S.child - 1, qpt);
-      }
-      if (it == (1 << 16) - 1) *timeout = true;
     }
   }
+#pragma unroll 1
+  while (__any_sync(kFull, walking)) {
+    int d = -1;
+    bool from_first = false;
+    if (walking) {
+      // scan to the next candidate that needs FP64 work, walking nodes as lists run out
+#pragma unroll 1
+      for (;;) {
+        if (i < L.count) {
+          const int c = __ldg(&G.cand[L.offset + i]);
+          ++i;
+          if (MODE == kFP32) {
+            const DBox32 B = G.box[c];
+            if (first && want_safety) R.safety = fmin(R.safety, (double)box_gap_lb(B.lo, B.hi, r));
+            const float lb = box_entry_lb(B.lo, B.hi, r, nullptr);
+            if (!((double)lb <= fmin(best, stop))) continue;
+            diag<COUNT>(cnt, G4N_C_RECHECKS);
+          }
+          d = c;
+          from_first = first;
+          break;
+        }
+        // list done: exit of the current node along the ray; its slab boundaries bound the safety
+        double texit = kInf;
+        int lstar = -1;
+#pragma unroll 1
+        for (int l = 0; l < ch.nlev; ++l) {
+          const DVoxHdr H = G.hdr[ch.h[l]];
+          const double pa = comp(p, H.axis), va = comp(v, H.axis);
+          const double blo = H.lo + ch.k0[l] * H.width, bhi = H.lo + (ch.k1[l] + 1) * H.width;
+          if (first && want_safety) R.safety = fmin(R.safety, fmax(fmin(pa - blo, bhi - pa), 0.0));
+          double t = kInf;
+          if (va > 0.0) t = (bhi - pa) * icomp(iv, H.axis);
+          else if (va < 0.0) t = (blo - pa) * icomp(iv, H.axis);
+          if (t < texit) {
+            texit = t;
+            lstar = l;
+          }
+        }
+        first = false;
+        if (!(texit < fmin(best, stop))) {
+          walking = false;
+          break;
+        }
+        // step into the neighbouring node at level lstar; deeper levels are looked up again
+        const DVoxHdr H = G.hdr[ch.h[lstar]];
+        const int nk = comp(v, H.axis) > 0.0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
+        if (nk < 0 || nk >= H.nslices || ++it >= (1 << 16)) {
+          if (it >= (1 << 16)) *timeout = true;
+          walking = false;
+          break;
+        }
+        const DVoxSlice S = G.slice[H.slice_base + nk];
+        ch.k0[lstar] = S.k0;
+        ch.k1[lstar] = S.k1;
+        if (S.child >= 0) {
+          ch.nlev = lstar + 1;
+          ch.list = S.child;
+        } else {
+          const V3 qpt{p.x + texit * v.x, p.y + texit * v.y, p.z + texit * v.z};
+          chain_fill(G, ch, lstar + 1, -S.child - 1, qpt);
+        }
+        L = G.clist[ch.list];
+        i = 0;
+        diag<COUNT>(cnt, G4N_C_VOX_NODES);
+      }
+    }
+    __syncwarp();
+    if (d >= 0) {
+      const DVol &D = G.vol[d];
+      V3 dp, dv;
+      to_local(D, p, v, dp, dv);
+      diag_kind<COUNT>(cnt, D.kind);
+      const double t = vol_dist_in(D, dp, dv, half);
+      if (t < kInf && (t < best || (t == best && (bl < 0 || d < bl)))) {
+        best = t;
+        bl = d;
+      }
+      if (MODE == kFP64 && from_first && want_safety) R.safety = fmin(R.safety, vol_safety_in(D, dp));
+    }
+  }
+  if (!active) return R;
   if (MODE == kFP32) {
     // the FP32 bounds prove the limit comes first: no FP64 geometry needed
     if (best > limit && (double)out_lo > limit) {
       R.physics = true;
-      R.step = kInf;
-      R.lim = G4N_LIM_MOTHER;
       return R;
     }
     diag<COUNT>(cnt, G4N_C_DIST_OUT);
-    const double tout = vol_dist_out(V, p, v, iv, half);
-    if (bl >= 0 && best <= tout) {
-      R.step = best;
-      R.lim = bl;
-    } else {
-      R.step = tout;
-      R.lim = G4N_LIM_MOTHER;
-    }
-    return R;
+    tout = vol_dist_out(G.vol[leaf], p, v, iv, half);
   }
-  R.step = best;
-  R.lim = bl;
+  // a daughter wins a tie with the mother; `best` already holds the lowest id among tied daughters
+  if (bl >= 0 && best <= tout) {
+    R.step = best;
+    R.lim = bl;
+  } else {
+    R.step = tout;
+    R.lim = G4N_LIM_MOTHER;
+  }
   return R;
 }
 

@@ -64,21 +64,31 @@ __global__ void __launch_bounds__(128) k_locate(const DGeom *__restrict__ geoms,
                                                 uint32_t *status) {
   const DGeom &G = geoms[gid];
   Counters cnt;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const V3 x{pos[i], pos[n + i], pos[2 * n + i]};
-    const V3 u{dir[i], dir[n + i], dir[2 * n + i]};
-    int leaf = -2;
-    if (bad_dir(u) || !isfinite(x.x + x.y + x.z)) flag(status, kStBadInput);
-    else leaf = locate_world<false>(G, x, u, cnt);
-    int depth = leaf >= 0 ? G.vol[leaf].depth : (leaf == -1 ? 0 : -1);
-    out_depth[i] = depth;
-    int v = leaf;
-    for (int k = kDMax - 1; k >= 0; --k) {
-      if (k < depth) {
-        out_path[k * n + i] = v;
-        v = G.vol[v].mother;
-      } else {
-        out_path[k * n + i] = -1;
+  const int64_t lane = threadIdx.x & 31;
+  // warp-uniform loop: the navigation below is warp-collective
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + lane;
+    V3 x{0, 0, 0}, u{0, 0, 1};
+    bool ok = false;
+    if (i < n) {
+      x = V3{pos[i], pos[n + i], pos[2 * n + i]};
+      u = V3{dir[i], dir[n + i], dir[2 * n + i]};
+      ok = !bad_dir(u) && isfinite(x.x + x.y + x.z);
+      if (!ok) flag(status, kStBadInput);
+    }
+    const int leaf = locate_world_warp<false>(G, ok, x, u, cnt);
+    if (i < n) {
+      const int depth = ok ? (leaf >= 0 ? G.vol[leaf].depth : 0) : -1;
+      out_depth[i] = depth;
+      int v = leaf;
+      for (int k = kDMax - 1; k >= 0; --k) {
+        if (k < depth) {
+          out_path[k * n + i] = v;
+          v = G.vol[v].mother;
+        } else {
+          out_path[k * n + i] = -1;
+        }
       }
     }
   }
@@ -95,33 +105,45 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
                                                       uint32_t *status) {
   const DGeom &G = geoms[gid];
   Counters cnt;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const V3 x{pos[i], pos[n + i], pos[2 * n + i]};
-    const V3 u{dir[i], dir[n + i], dir[2 * n + i]};
-    const int d = depth[i];
-    const int leaf = (d >= 1 && d <= kDMax) ? path[(int64_t)(d - 1) * n + i] : -1;
-    if (bad_dir(u) || leaf < 0 || leaf >= G.n_vol || G.vol[leaf].depth != d) {
-      flag(status, kStBadInput);
-      out_step[i] = nan("");
-      out_safety[i] = nan("");
-      out_lim[i] = INT32_MIN;
-      continue;
+  const int64_t lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + lane;
+    bool ok = false;
+    int leaf = 0;
+    double prop = kInf;
+    V3 p{0, 0, 0}, v{0, 0, 1};
+    if (i < n) {
+      const V3 x{pos[i], pos[n + i], pos[2 * n + i]};
+      const V3 u{dir[i], dir[n + i], dir[2 * n + i]};
+      const int d = depth[i];
+      leaf = (d >= 1 && d <= kDMax) ? path[(int64_t)(d - 1) * n + i] : -1;
+      ok = !bad_dir(u) && leaf >= 0 && leaf < G.n_vol && G.vol[leaf].depth == d;
+      if (!ok) {
+        flag(status, kStBadInput);
+        out_step[i] = nan("");
+        out_safety[i] = nan("");
+        out_lim[i] = INT32_MIN;
+        leaf = 0;
+      } else {
+        prop = proposed ? proposed[i] : kInf;
+        world_to_local(G.wxf[leaf], G.vol[leaf].flags & kWorldAligned, x, u, p, v);
+      }
     }
-    const double prop = proposed ? proposed[i] : kInf;
-    V3 p, v;
-    world_to_local(G.wxf[leaf], G.vol[leaf].flags & kWorldAligned, x, u, p, v);
     bool timeout = false;
-    const StepResult R = geom_step<MODE, false>(G, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout);
-    if (timeout) flag(status, kStTimeout);
-    double s = R.step;
-    int lim = R.lim;
-    if (R.physics || prop < s) {
-      s = prop;
-      lim = G4N_LIM_PHYSICS;
+    const StepResult R = geom_step_warp<MODE, false>(G, ok, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout);
+    if (ok) {
+      if (timeout) flag(status, kStTimeout);
+      double s = R.step;
+      int lim = R.lim;
+      if (R.physics || prop < s) {
+        s = prop;
+        lim = G4N_LIM_PHYSICS;
+      }
+      out_step[i] = s;
+      out_safety[i] = R.safety;
+      out_lim[i] = lim;
     }
-    out_step[i] = s;
-    out_safety[i] = R.safety;
-    out_lim[i] = lim;
   }
 }
 
@@ -251,37 +273,46 @@ __device__ __forceinline__ void set_direction(Track &t, const V3 &u) {
   t.iu = inv_dir(u);
 }
 
-// Start track number g of the concatenated items; returns its phase (kEmpty if it ended at once).
+// Start track number g of the concatenated items on the lanes with `active` set
+// (warp-collective: locate runs across the warp).  Returns the new phase of the
+// lane: kStep, or kEmpty if the track ended at once (or the lane was not active).
 template <bool COUNT>
-__device__ int start_track(const TParams &P, int64_t g, Track &t, Counters &cnt) {
-  t.gidx = g;
-  t.item = find_item(P.items, P.n_items, g);
-  const DItem &it = P.items[t.item];
-  t.tid = it.tid0 + (g - it.start);
-  const DGeom &G = P.geoms[it.geom];
-  V3 u;
-  double E;
-  make_source(it.src, P.seed, t.tid, t.x, u, E, P.status);
-  set_direction(t, u);
-  tally(P, t, G.n_vol + 1, E);
-  cnt.c[G4N_C_TRACKS]++;
-  t.h = kFnvOffset;
-  t.len = 0.0;
-  t.steps = 0;
-  t.nzero = 0;
-  t.safety = 0.0;
-  t.E = E;
-  t.leaf = locate_world<COUNT>(G, t.x, t.u, cnt);
-  if (t.leaf < 0) {
+__device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Counters &cnt) {
+  const DGeom *Gp = &P.geoms[P.items[0].geom];
+  if (active) {
+    t.gidx = g;
+    t.item = find_item(P.items, P.n_items, g);
+    const DItem &it = P.items[t.item];
+    t.tid = it.tid0 + (g - it.start);
+    Gp = &P.geoms[it.geom];
+    V3 u;
+    double E;
+    make_source(it.src, P.seed, t.tid, t.x, u, E, P.status);
+    set_direction(t, u);
+    tally(P, t, Gp->n_vol + 1, E);
+    cnt.c[G4N_C_TRACKS]++;
+    t.h = kFnvOffset;
+    t.len = 0.0;
+    t.steps = 0;
+    t.nzero = 0;
+    t.safety = 0.0;
+    t.E = E;
+  }
+  const DGeom &G = *Gp;
+  const int leaf = locate_world_warp<COUNT>(G, active, t.x, t.u, cnt);
+  if (!active) return kEmpty;
+  t.leaf = leaf;
+  if (leaf < 0) {
     cnt.c[G4N_C_ESCAPED]++;
     tally(P, t, G.n_vol, t.E);
     t.h = hash_step(t.h, -1, G4N_LIM_MOTHER, kEvEscape);
     finish(P, t);
+    t.leaf = 0;
     return kEmpty;
   }
   t.draw = 0;
   t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
-  set_energy(G, t, E);
+  set_energy(G, t, t.E);
   update_mu(G, t);
   return kStep;
 }
@@ -327,81 +358,108 @@ __device__ __forceinline__ V3 deflect(const V3 &u, double ct, double cph, double
   return V3{dx, -dy, -dz};
 }
 
-// One transport step of Algorithm 1 for one track: the free path (Eq. 7) races
-// the geometric step; a boundary crossing relocates, a physics end point waits
-// for the interaction phase.  Returns the next phase.
+// One transport step of Algorithm 1 on every lane in phase kStep
+// (warp-collective): the free path (Eq. 7) races the geometric step; a boundary
+// crossing relocates, a physics end point waits for the interaction phase.
+// Returns the lane's next phase.
 template <int MODE, bool COUNT>
-__device__ int step_track(const TParams &P, Track &t, Counters &cnt) {
-  const DItem &it = P.items[t.item];
-  const DGeom &G = P.geoms[it.geom];
-  if (t.steps >= P.max_steps) {
+__device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt) {
+  bool act = phase == kStep;
+  const DGeom &G = P.geoms[P.items[act ? t.item : 0].geom];
+  int next = phase;
+  if (act && t.steps >= P.max_steps) {
     cnt.c[G4N_C_STEP_LIMIT]++;
     flag(P.status, kStStepLimit);
     t.h = hash_step(t.h, t.leaf, kLimStepLimit, kEvStepLimit);
     finish(P, t);
-    return kEmpty;
+    next = kEmpty;
+    act = false;
   }
-  const double sphys = t.mu > 0.0 ? t.Y / t.mu : kInf;
-  double s = sphys;
-  int lim = G4N_LIM_PHYSICS;
-  bool geo = false;
-  if (sphys < t.safety) {
-    diag<COUNT>(cnt, G4N_C_SAFETY_SKIPS);
-  } else {
-    const DVol &L = G.vol[t.leaf];
-    const bool aligned = L.flags & kWorldAligned;
-    V3 p, v;
-    world_to_local(G.wxf[t.leaf], aligned, t.x, t.u, p, v);
-    bool timeout = false;
-    const StepResult R = geom_step<MODE, COUNT>(G, t.leaf, p, v, aligned ? t.iu : inv_dir(v), sphys, true, cnt, &timeout);
-    if (timeout) flag(P.status, kStTimeout);
-    t.safety = R.safety;
-    if (!R.physics && R.step <= sphys) {
-      geo = true;
-      s = R.step;
-      lim = R.lim;
+  double sphys = kInf;
+  bool need_geo = false;
+  V3 p{0, 0, 0}, v{0, 0, 1};
+  Inv3 iv{0, 0, 0};
+  if (act) {
+    sphys = t.mu > 0.0 ? t.Y / t.mu : kInf;
+    need_geo = !(sphys < t.safety);
+    if (!need_geo) {
+      diag<COUNT>(cnt, G4N_C_SAFETY_SKIPS);
+    } else {
+      const bool aligned = G.vol[t.leaf].flags & kWorldAligned;
+      world_to_local(G.wxf[t.leaf], aligned, t.x, t.u, p, v);
+      iv = aligned ? t.iu : inv_dir(v);
     }
   }
-  ++t.steps;
-  cnt.c[G4N_C_STEPS]++;
-  t.x.x += s * t.u.x;
-  t.x.y += s * t.u.y;
-  t.x.z += s * t.u.z;
-  t.len += s;
-  if (!geo) {
-    // free path ends inside the volume: the interaction is done in the interaction phase
-    t.safety = fmax(t.safety - s, 0.0);
-    t.nzero = 0;
-    cnt.c[G4N_C_PHYS_STEPS]++;
-    return kInteract;
+  bool timeout = false;
+  const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, sphys, true, cnt,
+                                                   &timeout);
+  bool geo = false;
+  double s = sphys;
+  int lim = G4N_LIM_PHYSICS;
+  if (act) {
+    if (timeout) flag(P.status, kStTimeout);
+    if (need_geo) {
+      t.safety = R.safety;
+      if (!R.physics && R.step <= sphys) {
+        geo = true;
+        s = R.step;
+        lim = R.lim;
+      }
+    }
+    ++t.steps;
+    cnt.c[G4N_C_STEPS]++;
+    t.x.x += s * t.u.x;
+    t.x.y += s * t.u.y;
+    t.x.z += s * t.u.z;
+    t.len += s;
+    if (!geo) {
+      // free path ends inside the volume: the interaction is done in the interaction phase
+      t.safety = fmax(t.safety - s, 0.0);
+      t.nzero = 0;
+      cnt.c[G4N_C_PHYS_STEPS]++;
+      next = kInteract;
+    } else {
+      if (t.mu > 0.0) t.Y = fmax(t.Y - s * t.mu, 0.0);
+      cnt.c[G4N_C_GEOM_STEPS]++;
+      t.safety = 0.0;
+    }
   }
-  if (t.mu > 0.0) t.Y = fmax(t.Y - s * t.mu, 0.0);
-  cnt.c[G4N_C_GEOM_STEPS]++;
-  t.safety = 0.0;
-  int leaf = relocate<MODE, COUNT>(G, t.leaf, t.x, t.u, lim == G4N_LIM_MOTHER && s > 0.0, cnt);
-  t.nzero = (s <= G.half) ? t.nzero + 1 : 0;
-  if (leaf >= 0 && t.nzero >= 10) {
-    const double push = 100.0 * G.tol;
-    t.x.x += push * t.u.x;
-    t.x.y += push * t.u.y;
-    t.x.z += push * t.u.z;
-    t.len += push;
-    cnt.c[G4N_C_PUSHES]++;
-    t.nzero = 0;
-    leaf = relocate<MODE, COUNT>(G, leaf, t.x, t.u, false, cnt);
+  int leaf = relocate_warp<MODE, COUNT>(G, geo, geo ? t.leaf : 0, t.x, t.u, geo && lim == G4N_LIM_MOTHER && s > 0.0,
+                                        cnt);
+  bool pushing = false;
+  if (geo) {
+    t.nzero = (s <= G.half) ? t.nzero + 1 : 0;
+    if (leaf >= 0 && t.nzero >= 10) {
+      const double push = 100.0 * G.tol;
+      t.x.x += push * t.u.x;
+      t.x.y += push * t.u.y;
+      t.x.z += push * t.u.z;
+      t.len += push;
+      cnt.c[G4N_C_PUSHES]++;
+      t.nzero = 0;
+      pushing = true;
+    }
+  }
+  const int pushed = relocate_warp<MODE, COUNT>(G, pushing, pushing ? leaf : 0, t.x, t.u, false, cnt);
+  if (pushing) {
+    leaf = pushed;
     t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
   }
-  if (leaf < 0) {
-    cnt.c[G4N_C_ESCAPED]++;
-    tally(P, t, G.n_vol, t.E);
-    t.h = hash_step(t.h, -1, lim, kEvEscape);
-    finish(P, t);
-    return kEmpty;
+  if (geo) {
+    if (leaf < 0) {
+      cnt.c[G4N_C_ESCAPED]++;
+      tally(P, t, G.n_vol, t.E);
+      t.h = hash_step(t.h, -1, lim, kEvEscape);
+      finish(P, t);
+      next = kEmpty;
+    } else {
+      t.leaf = leaf;
+      t.h = hash_step(t.h, leaf, lim, kEvNone);
+      update_mu(G, t);
+      next = kStep;
+    }
   }
-  t.leaf = leaf;
-  t.h = hash_step(t.h, leaf, lim, kEvNone);
-  update_mu(G, t);
-  return kStep;
+  return next;
 }
 
 // The interaction at the end of a free path: photoabsorption if U mu_tot < mu_photo,
@@ -452,29 +510,49 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
   for (int k = 0; k < G4N_N_COUNTERS; ++k) cnt.c[k] = 0;
   const unsigned lane = threadIdx.x & 31u;
   Track t;
+  t.item = 0;
+  t.leaf = 0;
   int phase = kEmpty;
   bool drained = false;
 #pragma unroll 1
   for (;;) {
     const unsigned idle = __ballot_sync(0xffffffffu, phase == kEmpty);
     const unsigned busy = ~idle;
+    const long long c0 = COUNT ? clock64() : 0;
     if (idle && !drained && (__popc(idle) >= P.refill_min || busy == 0)) {
       const int leader = __ffs(idle) - 1;
       unsigned long long base = 0;
       if ((int)lane == leader) base = atomicAdd(P.q_head, (unsigned long long)__popc(idle));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (base + __popc(idle) >= (unsigned long long)P.total) drained = true;
-      if (phase == kEmpty) {
-        const int64_t g = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
-        if (g < P.total) phase = start_track<COUNT>(P, g, t, cnt);
-      }
+      const int64_t g = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
+      const bool take = phase == kEmpty && g < P.total;
+      const int started = start_warp<COUNT>(P, take, g, t, cnt);
+      if (take) phase = started;
     }
     const unsigned waiting = __ballot_sync(0xffffffffu, phase == kInteract);
     const unsigned stepping = __ballot_sync(0xffffffffu, phase == kStep);
+    const long long c1 = COUNT ? clock64() : 0;
     if (waiting && (__popc(waiting) >= P.interact_min || stepping == 0)) {
       if (phase == kInteract) phase = interact(P, t, cnt);
     }
-    if (phase == kStep) phase = step_track<MODE, COUNT>(P, t, cnt);
+    __syncwarp();
+    const long long c2 = COUNT ? clock64() : 0;
+    const unsigned stepping2 = __ballot_sync(0xffffffffu, phase == kStep);
+    phase = step_warp<MODE, COUNT>(P, t, phase, cnt);
+    if (COUNT) {
+      __syncwarp();
+      const long long c3 = clock64();
+      if (lane == 0) {
+        cnt.c[G4N_C_CYC_REFILL] += (uint32_t)((c1 - c0) >> 4);
+        cnt.c[G4N_C_CYC_INTERACT] += (uint32_t)((c2 - c1) >> 4);
+        cnt.c[G4N_C_CYC_STEP] += (uint32_t)((c3 - c2) >> 4);
+        if (stepping2) {
+          cnt.c[G4N_C_STEP_LANES] += __popc(stepping2);
+          cnt.c[G4N_C_STEP_PHASES] += 1;
+        }
+      }
+    }
     if (drained && __ballot_sync(0xffffffffu, phase != kEmpty) == 0) break;
   }
   // flush counters: warp reduction, one atomic per counter per warp
