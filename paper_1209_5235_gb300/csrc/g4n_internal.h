@@ -49,6 +49,16 @@ struct alignas(32) DBox32 {
   float pad[2];
 };
 
+// FP32 copy of a volume's placement and solid size (for conservative FP32 bounds);
+// err = relative rounding allowance of the FP32 local coordinates.
+struct alignas(16) DVol32 {
+  float tx, ty, tz, c, s;
+  float q0, q1, q2;   // box: hx hy hz | orb: r 0 0 | tube: rmin rmax hz
+  int32_t kind, flags;
+  float scale;        // |t| + extent: magnitude of the quantities involved
+  float pad;
+};
+
 struct DVoxHdr {
   double lo, width, inv_width;
   int32_t axis, nslices, slice_base, pad;
@@ -68,6 +78,7 @@ struct DGeom {
   const DVol *vol;
   const DWorld *wxf;
   const DBox32 *box;
+  const DVol32 *v32;
   const DVoxHdr *hdr;
   const DVoxSlice *slice;
   const DCandList *clist;
@@ -101,6 +112,7 @@ struct HGeom {
   std::vector<DVol> vol;
   std::vector<DWorld> wxf;
   std::vector<DBox32> box;
+  std::vector<DVol32> v32;
   std::vector<DVoxHdr> hdr;
   std::vector<DVoxSlice> slice;
   std::vector<DCandList> clist;

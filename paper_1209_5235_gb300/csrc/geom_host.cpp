@@ -487,6 +487,19 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
     box[i].pad[0] = box[i].pad[1] = 0.f;
     ext[i] = e;
   }
+  // --- FP32 copies for the conservative bounds
+  g->v32.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const DVol &v = g->vol[i];
+    DVol32 &w = g->v32[i];
+    std::memset(&w, 0, sizeof(w));
+    w.tx = (float)v.tx; w.ty = (float)v.ty; w.tz = (float)v.tz; w.c = (float)v.c; w.s = (float)v.s;
+    w.q0 = (float)v.p[0]; w.q1 = (float)v.p[1]; w.q2 = (float)v.p[2];
+    w.kind = v.kind;
+    w.flags = v.flags;
+    const double ext = v.kind == kOrb ? v.p[0] : (v.kind == kTube ? std::max(v.p[1], v.p[2]) : std::max({v.p[0], v.p[1], v.p[2]}));
+    w.scale = (float)(std::fabs(v.tx) + std::fabs(v.ty) + std::fabs(v.tz) + 2.0 * ext);
+  }
   // --- validation: containment (surface samples) and sibling overlaps (interior samples)
   std::mt19937_64 rng(0x9E3779B97F4A7C15ull);
   std::vector<double> pts;
@@ -565,11 +578,13 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
                             g->hdr.size() * sizeof(DVoxHdr), g->slice.size() * sizeof(DVoxSlice),
                             g->clist.size() * sizeof(DCandList), g->cand.size() * sizeof(int32_t),
                             g->matE.size() * sizeof(double), g->matC.size() * sizeof(double), g->matP.size() * sizeof(double),
-                            g->mat_off.size() * sizeof(int32_t), g->mat_n.size() * sizeof(int32_t), 0};
-  const void *src[12] = {g->vol.data(), g->wxf.data(), g->box.data(), g->hdr.data(), g->slice.data(), g->clist.data(),
-                         g->cand.data(), g->matE.data(), g->matC.data(), g->matP.data(), g->mat_off.data(), g->mat_n.data()};
+                            g->mat_off.size() * sizeof(int32_t), g->mat_n.size() * sizeof(int32_t),
+                            g->v32.size() * sizeof(DVol32)};
+  const void *src[13] = {g->vol.data(), g->wxf.data(), g->box.data(), g->hdr.data(), g->slice.data(), g->clist.data(),
+                         g->cand.data(), g->matE.data(), g->matC.data(), g->matP.data(), g->mat_off.data(), g->mat_n.data(),
+                         g->v32.data()};
   size_t total = 0;
-  for (int k = 0; k < 12; ++k) { off[k] = total; total += al(std::max<size_t>(sz[k], 8)); }
+  for (int k = 0; k < 13; ++k) { off[k] = total; total += al(std::max<size_t>(sz[k], 8)); }
   if (ctx->device < 0) {  // host-only context: keep the host tables
     g->blob_bytes = total;
     g->dview.n_vol = n;
@@ -588,7 +603,7 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
   }
   g->blob_bytes = total;
   char *base = (char *)g->blob;
-  for (int k = 0; k < 12; ++k) {
+  for (int k = 0; k < 13; ++k) {
     if (sz[k] && cudaMemcpy(base + off[k], src[k], sz[k], cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(g->blob);
       delete g;
@@ -608,6 +623,7 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
   d.matP = (const double *)(base + off[9]);
   d.mat_off = (const int32_t *)(base + off[10]);
   d.mat_n = (const int32_t *)(base + off[11]);
+  d.v32 = (const DVol32 *)(base + off[12]);
   d.n_vol = n;
   d.n_mat = (int32_t)B.mats.size();
   d.shared_grid = 1;

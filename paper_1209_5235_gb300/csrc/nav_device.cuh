@@ -540,6 +540,31 @@ __device__ __forceinline__ bool certainly_inside32(const DVol &V, const Ray32 &r
   return true;
 }
 
+// Lower bound of the Euclidean distance from mother-frame point (x, y, z) to daughter D's
+// solid, from FP32 copies of its placement and size: the FP32 local point is within
+// `e` of the exact one (a generous allowance: 2^-20 of the magnitudes involved).
+// Negative when the point may be inside.
+__device__ __forceinline__ float iso_lb32(const DVol32 &D, float x, float y, float z) {
+  const float dx = x - D.tx, dy = y - D.ty, lz = z - D.tz;
+  float lx = dx, ly = dy;
+  if (!(D.flags & kPlacedAligned)) {
+    lx = D.c * dx + D.s * dy;
+    ly = D.c * dy - D.s * dx;
+  }
+  const float e = 9.5367432e-7f * (fabsf(x) + fabsf(y) + fabsf(z) + D.scale) + 1e-30f;
+  float d;
+  if (D.kind == kBox) {
+    d = fmaxf(fabsf(lx) - D.q0, fmaxf(fabsf(ly) - D.q1, fabsf(lz) - D.q2));
+  } else if (D.kind == kOrb) {
+    d = sqrtf(lx * lx + ly * ly + lz * lz) - D.q0;
+  } else {
+    const float r = sqrtf(lx * lx + ly * ly);
+    d = fmaxf(r - D.q1, fabsf(lz) - D.q2);
+    if (D.flags & kHasRmin) d = fmaxf(d, D.q0 - r);
+  }
+  return d - e;
+}
+
 // Conservative FP32 test: can the mother-frame point claim daughter box b?
 __device__ __forceinline__ bool box32_contains(const DBox32 &b, float x, float y, float z) {
   return x >= b.lo[0] && x <= b.hi[0] && y >= b.lo[1] && y <= b.hi[1] && z >= b.lo[2] && z <= b.hi[2];
@@ -602,7 +627,8 @@ __device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, 
         while (i < L.count) {
           const int c = __ldg(&G.cand[L.offset + i]);
           ++i;
-          if (c != blocked && box32_contains(G.box[c], px, py, pz)) {
+          if (c != blocked && box32_contains(G.box[c], px, py, pz) &&
+              !(iso_lb32(G.v32[c], px, py, pz) > (float)(2.0 * G.half))) {
             d = c;
             break;
           }
@@ -779,8 +805,9 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
           ++i;
           if (MODE == kFP32) {
             const DBox32 B = G.box[c];
-            if (first && want_safety) R.safety = fmin(R.safety, (double)box_gap_lb(B.lo, B.hi, r));
-            const float lb = box_entry_lb(B.lo, B.hi, r, nullptr);
+            const float iso = iso_lb32(G.v32[c], r.plo[0], r.plo[1], r.plo[2]) - (float)(2.0 * G.half);
+            if (first && want_safety) R.safety = fmin(R.safety, (double)fmaxf(box_gap_lb(B.lo, B.hi, r), iso));
+            const float lb = fmaxf(box_entry_lb(B.lo, B.hi, r, nullptr), iso);
             if (!((double)lb <= fmin(best, stop))) continue;
             diag<COUNT>(cnt, G4N_C_RECHECKS);
           }
