@@ -249,6 +249,51 @@ int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_e
 int g4n_transport_batch_host(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_edep, uint64_t *out_counters,
                              uint64_t *out_track_hash, double *out_track_len, g4n_stream stream);
 
+/* ---------------------------------------------------------------- learned candidate proposal */
+
+/* A small network proposes which candidate daughter of the current voxel node the ray enters
+ * first; in G4N_MODE_LEARNED that candidate is evaluated exactly before the others, and its
+ * distance prunes every candidate whose rigorous FP32 lower bound exceeds it.  The exact
+ * navigator stays the judge: results are identical in every mode.  (No counterpart in the
+ * paper; part of the method's learned-proposal extension.)
+ *
+ * Network: 9 -> 64 -> 64 -> 32, GELU after the hidden layers, softmax over the node's first
+ * n_cand <= 32 slots.  Features (9 floats per sample): the point in the node's own coordinates
+ * (3, in [-1, 1]), the direction (3), (ln E[MeV] + 4.6) / 10, n_cand / 32, 1.  Label: the list
+ * slot of the daughter entered.  Parameters: G4N_MLP_N_PARAMS FP32 values packed as
+ * W1[9][64], b1[64], W2[64][64], b2[64], W3[64][32], b3[32] (W[k][n]: input k to output n). */
+#define G4N_MLP_N_PARAMS 6880
+
+/* Load FP32 parameters (HOST array) into the context; resets the optimizer state. */
+int g4n_mlp_load(g4n_ctx *ctx, const float *params);
+/* Read the current FP32 parameters into a HOST array of G4N_MLP_N_PARAMS floats. */
+int g4n_mlp_get(g4n_ctx *ctx, float *params);
+
+/* Log training samples with the plain FP64 navigator: transports the batch (batch->mode must be
+ * G4N_MODE_FP64; tallies and counters are discarded) and records, for each step whose boundary
+ * search entered a daughter listed in the first voxel node (2 to 32 candidates), the features,
+ * the label and n_cand.  feat (capacity x 9 floats), label, ncand (capacity int32): DEVICE
+ * buffers.  *out_count (HOST) = samples written (at most capacity).  Synchronous. */
+int g4n_mlp_log(g4n_ctx *ctx, const g4n_batch_desc *batch, float *feat, int32_t *label, int32_t *ncand,
+                int64_t capacity, int64_t *out_count, g4n_stream stream);
+
+/* Train on n logged samples (DEVICE buffers as above) with this library's kernels: BF16
+ * tensor-core GEMMs with FP32 accumulation, masked softmax cross-entropy, Adam (lr, beta
+ * 0.9/0.999) on FP32 master weights.  Minibatches of `batch` (multiple of 16) per epoch from a
+ * seeded permutation.  out_loss: HOST array of `epochs` mean losses, or NULL.  Synchronous. */
+int g4n_mlp_train(g4n_ctx *ctx, int64_t n, const float *feat, const int32_t *label, const int32_t *ncand,
+                  int32_t epochs, int32_t batch, float lr, uint64_t seed, float *out_loss, g4n_stream stream);
+
+/* Mean loss and its gradient (HOST array of G4N_MLP_N_PARAMS) over n samples (n a multiple of
+ * 16; DEVICE buffers) at the current parameters, without updating them.  precision 0: BF16
+ * tensor-core GEMMs (as in training); 1: FP32 GEMMs.  Synchronous. */
+int g4n_mlp_grad(g4n_ctx *ctx, int64_t n, const float *feat, const int32_t *label, const int32_t *ncand,
+                 int32_t precision, float *out_grads, double *out_loss);
+
+/* Logits (n x 32 FP32, DEVICE) of n feature rows (n x 9 FP32, DEVICE) through the same
+ * warp-level BF16 inference code the transport kernel uses. */
+int g4n_mlp_predict(g4n_ctx *ctx, int64_t n, const float *feat, float *out_logits, g4n_stream stream);
+
 /* ---------------------------------------------------------------- allocation-free transport */
 
 /* No counterpart in the paper: a library-side convenience for callers that must not allocate

@@ -27,6 +27,7 @@ G4N_DMAX = 8
 G4N_N_COUNTERS = 32
 G4N_FLAG_DIAGNOSTICS = 1
 G4N_NOALLOC_MAX_ITEMS = 256
+G4N_MLP_N_PARAMS = 6880
 G4N_NOALLOC_STATUS_SLOT = G4N_N_COUNTERS - 1
 COUNTER_NAMES = {0: "tracks", 1: "steps", 2: "geom_steps", 3: "phys_steps", 4: "photo", 5: "compton", 6: "escaped",
                  7: "cutoff", 8: "pushes", 9: "step_limit", 16: "safety_skips", 17: "cand_box", 18: "cand_tube",
@@ -39,13 +40,14 @@ PARITY_COUNTERS = ["tracks", "steps", "geom_steps", "phys_steps", "photo", "comp
 EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_scale", "g4n_sync", "g4n_material_add",
             "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_place", "g4n_voxelize", "g4n_geom_finalize",
             "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_transport_batch", "g4n_transport_batch_host",
-            "g4n_transport_batch_noalloc"]
+            "g4n_transport_batch_noalloc", "g4n_mlp_load", "g4n_mlp_get", "g4n_mlp_log", "g4n_mlp_train",
+            "g4n_mlp_grad", "g4n_mlp_predict"]
 
 __all__ = EXPORTED + ["G4N_FLAG_DIAGNOSTICS", "G4NError", "load", "lib_path", "build_scene", "make_items", "counters_dict", "voxel_params",
                       "COUNTER_NAMES", "PARITY_COUNTERS", "G4N_DMAX", "G4N_N_COUNTERS", "G4N_MODE_FP64",
                       "G4N_MODE_FP32_RECHECK", "G4N_MODE_LEARNED", "G4N_LIM_PHYSICS", "G4N_LIM_MOTHER",
                       "G4N_ERR_ARG", "G4N_ERR_GEOM", "G4N_ERR_STEP_LIMIT", "G4N_ERR_TIMEOUT", "G4N_ERR_STATE",
-                      "G4N_NOALLOC_MAX_ITEMS", "G4N_NOALLOC_STATUS_SLOT",
+                      "G4N_NOALLOC_MAX_ITEMS", "G4N_NOALLOC_STATUS_SLOT", "G4N_MLP_N_PARAMS",
                       "g4n_voxel_params", "g4n_source", "g4n_work_item", "g4n_batch_desc"]
 
 
@@ -109,6 +111,11 @@ def load():
         "g4n_transport_batch": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
         "g4n_transport_batch_host": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
         "g4n_transport_batch_noalloc": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
+        "g4n_mlp_load": [vp, vp], "g4n_mlp_get": [vp, vp],
+        "g4n_mlp_log": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, i64, vp, vp],
+        "g4n_mlp_train": [vp, i64, vp, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp],
+        "g4n_mlp_grad": [vp, i64, vp, vp, vp, i32, vp, vp],
+        "g4n_mlp_predict": [vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -394,3 +401,67 @@ def counters_dict(counters) -> dict:
     a = counters.cpu().numpy() if hasattr(counters, "cpu") else np.asarray(counters)
     a = a.view(np.uint64) if a.dtype == np.int64 else a
     return {name: int(a[k]) for k, name in COUNTER_NAMES.items()}
+
+
+# ---------------------------------------------------------------- learned proposal
+
+def g4n_mlp_load(ctx, params) -> None:
+    """Load packed FP32 parameters (G4N_MLP_N_PARAMS floats)."""
+    a = _host(params, np.float32)
+    if a.size != G4N_MLP_N_PARAMS:
+        raise ValueError("need G4N_MLP_N_PARAMS parameters")
+    _check(ctx, load().g4n_mlp_load(ctx, a.ctypes.data))
+
+
+def g4n_mlp_get(ctx) -> np.ndarray:
+    out = np.zeros(G4N_MLP_N_PARAMS, dtype=np.float32)
+    _check(ctx, load().g4n_mlp_get(ctx, out.ctypes.data))
+    return out
+
+
+def g4n_mlp_log(ctx, items, seed: int, capacity: int, stride: int, cutoff: float = 0.01, n_batches: int = 100,
+                stream=None):
+    """Samples logged by the plain navigator: (feat (n, 9) f32, label (n,) i32, ncand (n,) i32) CUDA tensors."""
+    import torch
+    feat = torch.empty((capacity, 9), dtype=torch.float32, device="cuda")
+    label = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    ncand = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    d = _desc(items, seed, cutoff, G4N_MODE_FP64, n_batches, stride, 0, 0, 0)
+    count = ctypes.c_int64()
+    _check(ctx, load().g4n_mlp_log(ctx, ctypes.byref(d), _dptr(feat, torch.float32, "feat"),
+                                   _dptr(label, torch.int32, "label"), _dptr(ncand, torch.int32, "ncand"),
+                                   int(capacity), ctypes.byref(count), _stream(stream)))
+    n = count.value
+    return feat[:n], label[:n], ncand[:n]
+
+
+def g4n_mlp_train(ctx, feat, label, ncand, epochs: int = 1, batch: int = 4096, lr: float = 1e-3, seed: int = 1,
+                  stream=None) -> np.ndarray:
+    """Train in place on device samples; returns the mean loss of each epoch."""
+    import torch
+    out = np.zeros(epochs, dtype=np.float32)
+    _check(ctx, load().g4n_mlp_train(ctx, int(feat.shape[0]), _dptr(feat, torch.float32, "feat"),
+                                     _dptr(label, torch.int32, "label"), _dptr(ncand, torch.int32, "ncand"),
+                                     int(epochs), int(batch), float(lr), ctypes.c_uint64(seed), out.ctypes.data,
+                                     _stream(stream)))
+    return out
+
+
+def g4n_mlp_grad(ctx, feat, label, ncand, precision: int = 0):
+    """(mean loss, gradient (G4N_MLP_N_PARAMS,) float32) at the current parameters; precision 0 BF16, 1 FP32."""
+    import torch
+    g = np.zeros(G4N_MLP_N_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(ctx, load().g4n_mlp_grad(ctx, int(feat.shape[0]), _dptr(feat, torch.float32, "feat"),
+                                    _dptr(label, torch.int32, "label"), _dptr(ncand, torch.int32, "ncand"),
+                                    int(precision), g.ctypes.data, ctypes.byref(loss)))
+    return loss.value, g
+
+
+def g4n_mlp_predict(ctx, feat, stream=None):
+    """Logits (n, 32) float32 CUDA tensor for feature rows (n, 9)."""
+    import torch
+    out = torch.empty((feat.shape[0], 32), dtype=torch.float32, device=feat.device)
+    _check(ctx, load().g4n_mlp_predict(ctx, int(feat.shape[0]), _dptr(feat, torch.float32, "feat"),
+                                       _dptr(out, torch.float32, "logits"), _stream(stream)))
+    return out

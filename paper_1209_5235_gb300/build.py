@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libg4nav.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["geom_host.cpp", "nav_kernels.cu"]
+SOURCES = ["geom_host.cpp", "nav_kernels.cu", "mlp.cu"]
 
 
 def _nvcc() -> str:

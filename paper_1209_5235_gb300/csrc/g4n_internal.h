@@ -161,7 +161,18 @@ struct g4n_ctx {
   void *d_stage = nullptr;
   size_t d_stage_bytes = 0;
   int sm_count = 0;
+  // candidate-proposal MLP state (owned by mlp.cu)
+  void *mlp = nullptr;
 };
 
 // error helpers shared by the translation units
 int g4n_fail(g4n_ctx *ctx, int code, const std::string &msg);
+
+namespace g4n {
+namespace mlp {
+struct SmemWeights;
+}
+}  // namespace g4n
+// Device image of the loaded MLP weights (null if none) and its release.
+const g4n::mlp::SmemWeights *g4n_mlp_image(g4n_ctx *ctx);
+void g4n_mlp_free(g4n_ctx *ctx);

@@ -286,6 +286,7 @@ int g4n_destroy(g4n_ctx *ctx) {
     return G4N_OK;
   }
   cudaSetDevice(ctx->device);
+  g4n_mlp_free(ctx);
   for (HGeom *g : ctx->geoms) {
     if (g) { cudaFree(g->blob); delete g; }
   }

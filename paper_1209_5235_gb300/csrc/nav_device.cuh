@@ -23,13 +23,14 @@
 #include <cstdint>
 
 #include "g4n_internal.h"
+#include "mlp_device.cuh"
 
 namespace g4n {
 namespace dev {
 
 constexpr double kInf = __builtin_huge_val();
 constexpr float kInfF = __builtin_huge_valf();
-enum Mode : int { kFP64 = 0, kFP32 = 1 };
+enum Mode : int { kFP64 = 0, kFP32 = 1, kLearned = 2 };  // kLearned: FP32 bounds + proposal first
 
 struct V3 {
   double x, y, z;
@@ -698,7 +699,7 @@ __device__ __forceinline__ int relocate_warp(const DGeom &G, bool active, int le
       const DVol &L = G.vol[leaf];
       world_to_local(G.wxf[leaf], L.flags & kWorldAligned, x, u, p, v);
       bool ok = false;
-      if (MODE == kFP32) ok = certainly_inside32(L, make_ray32(p, v), (float)(4.0 * G.half) + 1e-30f);
+      if (MODE != kFP64) ok = certainly_inside32(L, make_ray32(p, v), (float)(4.0 * G.half) + 1e-30f);
       if (!ok) {
         diag<COUNT>(cnt, G4N_C_INSIDE);
         ok = vol_inside(L, p, v, G.half);
@@ -744,6 +745,59 @@ __device__ __forceinline__ void chain_fill(const DGeom &G, Chain &ch, int lev, i
   ch.list = 0;
 }
 
+// Training-sample log written by the plain navigator (features, label = list slot of the
+// daughter entered, candidate count); `count` may exceed `capacity` (extra samples dropped).
+struct MlpLog {
+  float *feat;
+  int32_t *label;
+  int32_t *ncand;
+  unsigned long long *count;
+  int64_t capacity;
+};
+
+// What geom_step needs for the proposal: the weights and this warp's scratch (learned
+// mode), the sample log (plain mode, optional) and the track's log-energy feature.
+struct MlpCtx {
+  const mlp::SmemWeights *w;
+  mlp::SmemWarp *scratch;
+  const MlpLog *log;
+  float loge;
+};
+
+// Proposal features of the node holding p (leaf frame): the point in the node's own
+// coordinates (axes the node does not slice use the leaf's half extent), the direction,
+// log E, n / 32 and 1.
+__device__ __forceinline__ void node_features(const DGeom &G, const DVol &V, const Chain &ch, const V3 &p, const V3 &v,
+                                              float loge, int n, float *f) {
+  double c[3] = {0.0, 0.0, 0.0};
+  double h[3];
+  if (V.kind == kBox) {
+    h[0] = V.p[0];
+    h[1] = V.p[1];
+    h[2] = V.p[2];
+  } else if (V.kind == kOrb) {
+    h[0] = h[1] = h[2] = V.p[0];
+  } else {
+    h[0] = h[1] = V.p[1];
+    h[2] = V.p[2];
+  }
+  for (int l = 0; l < ch.nlev; ++l) {
+    const DVoxHdr H = G.hdr[ch.h[l]];
+    const double lo = H.lo + ch.k0[l] * H.width, hi = H.lo + (ch.k1[l] + 1) * H.width;
+    c[H.axis] = 0.5 * (lo + hi);
+    h[H.axis] = 0.5 * (hi - lo);
+  }
+  f[0] = fminf(fmaxf((float)((p.x - c[0]) / h[0]), -2.f), 2.f);
+  f[1] = fminf(fmaxf((float)((p.y - c[1]) / h[1]), -2.f), 2.f);
+  f[2] = fminf(fmaxf((float)((p.z - c[2]) / h[2]), -2.f), 2.f);
+  f[3] = (float)v.x;
+  f[4] = (float)v.y;
+  f[5] = (float)v.z;
+  f[6] = loge;
+  f[7] = (float)n * (1.0f / 32.0f);
+  f[8] = 1.0f;
+}
+
 struct StepResult {
   double step;    // geometric step (exact when it is <= the limit)
   double safety;  // isotropic lower bound
@@ -761,7 +815,7 @@ struct StepResult {
 template <int MODE, bool COUNT>
 __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active, int leaf, const V3 &p, const V3 &v,
                                                      const Inv3 &iv, double limit, bool want_safety, Counters &cnt,
-                                                     bool *timeout) {
+                                                     bool *timeout, const MlpCtx &mc) {
   const double half = G.half;
   StepResult R{kInf, 0.0, G4N_LIM_MOTHER, false};
   double best = kInf, stop = 0.0, tout = kInf;
@@ -770,10 +824,13 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
   Chain ch;
   bool walking = false, first = true;
   int i = 0, it = 0, bl = G4N_LIM_MOTHER;
-  DCandList L{0, 0};
+  DCandList L{0, 0}, L0{0, 0};
+  int prop_done = -1;
+  float feat[mlp::kIn];
+  bool have_feat = false;
   if (active) {
     const DVol &V = G.vol[leaf];
-    if (MODE == kFP32) {
+    if (MODE != kFP64) {
       r = make_ray32(p, v);
       float out_hi, saf32;
       exit_bounds32(V, r, p, &out_lo, &out_hi, &saf32);
@@ -788,9 +845,29 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
     if (V.vox >= 0) {
       chain_fill(G, ch, 0, V.vox, p);
       L = G.clist[ch.list];
+      L0 = L;
       walking = true;
       diag<COUNT>(cnt, G4N_C_VOX_NODES);
+      if ((MODE == kLearned || mc.log) && L.count >= 2 && L.count <= mlp::kOut) {
+        node_features(G, V, ch, p, v, mc.loge, L.count, feat);
+        have_feat = true;
+      }
     }
+  }
+  // learned mode: the network proposes which first-node candidate is entered first; it is
+  // evaluated before the others so that its exact distance prunes them (warp-collective)
+  int prop = -1;
+  if (MODE == kLearned && __any_sync(kFull, have_feat)) {
+    float f0[mlp::kIn];
+#pragma unroll
+    for (int k = 0; k < mlp::kIn; ++k) f0[k] = have_feat ? feat[k] : 0.f;
+    mlp::put_features(*mc.scratch, f0);
+    mlp::forward_warp(*mc.w, *mc.scratch);
+    if (have_feat) {
+      prop = mlp::argmax_row(*mc.scratch, L.count);
+      diag<COUNT>(cnt, G4N_C_PROPOSALS);
+    }
+    __syncwarp();
   }
 #pragma unroll 1
   while (__any_sync(kFull, walking)) {
@@ -800,15 +877,32 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       // scan to the next candidate that needs FP64 work, walking nodes as lists run out
 #pragma unroll 1
       for (;;) {
+        if (MODE == kLearned && prop >= 0) {
+          // the proposal goes first if its bound still allows it to matter
+          const int c = __ldg(&G.cand[L0.offset + prop]);
+          const DBox32 B = G.box[c];
+          const float iso = iso_lb32(G.v32[c], r.plo[0], r.plo[1], r.plo[2]) - (float)(2.0 * G.half);
+          const float lb = fmaxf(box_entry_lb(B.lo, B.hi, r, nullptr), iso);
+          if ((double)lb <= fmin(best, stop)) {
+            d = c;
+            from_first = true;
+            break;
+          }
+          prop = -1;  // not worth it: the scan treats the slot like any other
+        }
         if (i < L.count) {
           const int c = __ldg(&G.cand[L.offset + i]);
           ++i;
-          if (MODE == kFP32) {
+          if (MODE != kFP64) {
             const DBox32 B = G.box[c];
             const float iso = iso_lb32(G.v32[c], r.plo[0], r.plo[1], r.plo[2]) - (float)(2.0 * G.half);
             if (first && want_safety) R.safety = fmin(R.safety, (double)fmaxf(box_gap_lb(B.lo, B.hi, r), iso));
+            if (MODE == kLearned && first && i - 1 == prop_done) continue;  // already evaluated exactly
             const float lb = fmaxf(box_entry_lb(B.lo, B.hi, r, nullptr), iso);
-            if (!((double)lb <= fmin(best, stop))) continue;
+            if (!((double)lb <= fmin(best, stop))) {
+              if (MODE == kLearned) diag<COUNT>(cnt, G4N_C_PRUNED);
+              continue;
+            }
             diag<COUNT>(cnt, G4N_C_RECHECKS);
           }
           d = c;
@@ -861,6 +955,11 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       }
     }
     __syncwarp();
+    if (MODE == kLearned && prop >= 0 && d >= 0) {
+      prop_done = prop;  // the proposed slot is skipped when the first node is scanned
+      prop = -1;
+      diag<COUNT>(cnt, G4N_C_RECHECKS);
+    }
     if (d >= 0) {
       const DVol &D = G.vol[d];
       V3 dp, dv;
@@ -875,7 +974,24 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
     }
   }
   if (!active) return R;
-  if (MODE == kFP32) {
+  if (MODE == kFP64 && mc.log && have_feat && bl >= 0 && best <= tout) {
+    // training sample: the daughter entered, if it is listed in the first node
+    int slot = -1;
+    for (int k = 0; k < L0.count; ++k)
+      if (__ldg(&G.cand[L0.offset + k]) == bl) {
+        slot = k;
+        break;
+      }
+    if (slot >= 0) {
+      const unsigned long long at = atomicAdd(mc.log->count, 1ull);
+      if ((int64_t)at < mc.log->capacity) {
+        for (int k = 0; k < mlp::kIn; ++k) mc.log->feat[at * mlp::kIn + k] = feat[k];
+        mc.log->label[at] = slot;
+        mc.log->ncand[at] = L0.count;
+      }
+    }
+  }
+  if (MODE != kFP64) {
     // the FP32 bounds prove the limit comes first: no FP64 geometry needed
     if (best > limit && (double)out_lo > limit) {
       R.physics = true;

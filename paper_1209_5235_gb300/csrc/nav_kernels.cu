@@ -38,6 +38,9 @@ struct Workspace {
   unsigned long long q_head;
   uint32_t status;
   uint32_t pad[13];
+  dev::MlpLog log;        // training-sample log of g4n_mlp_log
+  unsigned long long log_count;
+  unsigned long long pad2[7];
 };
 
 }  // namespace g4n
@@ -102,10 +105,20 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
                                                       const int32_t *__restrict__ depth, const int32_t *__restrict__ path,
                                                       const double *__restrict__ proposed, double *__restrict__ out_step,
                                                       double *__restrict__ out_safety, int32_t *__restrict__ out_lim,
-                                                      uint32_t *status) {
+                                                      uint32_t *status, const mlp::SmemWeights *__restrict__ mlp_w) {
   const DGeom &G = geoms[gid];
   Counters cnt;
   const int64_t lane = threadIdx.x & 31;
+  MlpCtx mc{nullptr, nullptr, nullptr, 0.f};
+  if (MODE == kLearned) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    mlp::SmemWeights *sw = reinterpret_cast<mlp::SmemWeights *>(smem);
+    mlp::load_weights(*sw, mlp_w);
+    __syncthreads();
+    mc.w = sw;
+    mc.scratch = reinterpret_cast<mlp::SmemWarp *>(smem + sizeof(mlp::SmemWeights)) + (threadIdx.x >> 5);
+    mc.loge = 0.46f;  // log-energy feature at 1 MeV: the query carries no energy
+  }
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + lane;
@@ -131,7 +144,7 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
       }
     }
     bool timeout = false;
-    const StepResult R = geom_step_warp<MODE, false>(G, ok, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout);
+    const StepResult R = geom_step_warp<MODE, false>(G, ok, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout, mc);
     if (ok) {
       if (timeout) flag(status, kStTimeout);
       double s = R.step;
@@ -179,6 +192,8 @@ struct TParams {
   double *out_len;
   int refill_min;    // refill a warp's idle lanes once at least this many are idle
   int interact_min;  // run the interaction phase once at least this many lanes wait for it
+  const mlp::SmemWeights *mlp_w;  // learned mode: weights (device image)
+  const MlpLog *log;              // plain mode: training-sample log (null: none)
 };
 
 __device__ __forceinline__ int find_item(const DItem *items, int n_items, int64_t g) {
@@ -363,7 +378,7 @@ __device__ __forceinline__ V3 deflect(const V3 &u, double ct, double cph, double
 // crossing relocates, a physics end point waits for the interaction phase.
 // Returns the lane's next phase.
 template <int MODE, bool COUNT>
-__device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt) {
+__device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, MlpCtx mc) {
   bool act = phase == kStep;
   const DGeom &G = P.geoms[P.items[act ? t.item : 0].geom];
   int next = phase;
@@ -391,8 +406,9 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt) {
     }
   }
   bool timeout = false;
+  if (MODE == kLearned || mc.log) mc.loge = act ? (logf((float)t.E) + 4.6f) * 0.1f : 0.f;
   const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, sphys, true, cnt,
-                                                   &timeout);
+                                                   &timeout, mc);
   bool geo = false;
   double s = sphys;
   int lim = G4N_LIM_PHYSICS;
@@ -509,6 +525,15 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
 #pragma unroll
   for (int k = 0; k < G4N_N_COUNTERS; ++k) cnt.c[k] = 0;
   const unsigned lane = threadIdx.x & 31u;
+  MlpCtx mc{nullptr, nullptr, P.log, 0.f};
+  if (MODE == kLearned) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    mlp::SmemWeights *sw = reinterpret_cast<mlp::SmemWeights *>(smem);
+    mlp::load_weights(*sw, P.mlp_w);
+    __syncthreads();
+    mc.w = sw;
+    mc.scratch = reinterpret_cast<mlp::SmemWarp *>(smem + sizeof(mlp::SmemWeights)) + (threadIdx.x >> 5);
+  }
   Track t;
   t.item = 0;
   t.leaf = 0;
@@ -539,7 +564,7 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
     __syncwarp();
     const long long c2 = COUNT ? clock64() : 0;
     const unsigned stepping2 = __ballot_sync(0xffffffffu, phase == kStep);
-    phase = step_warp<MODE, COUNT>(P, t, phase, cnt);
+    phase = step_warp<MODE, COUNT>(P, t, phase, cnt, mc);
     if (COUNT) {
       __syncwarp();
       const long long c3 = clock64();
@@ -569,7 +594,13 @@ using TransportKernel = void (*)(const TParams);
 
 TransportKernel transport_kernel(int mode, bool count) {
   if (mode == G4N_MODE_FP64) return count ? k_transport<kFP64, true> : k_transport<kFP64, false>;
-  return count ? k_transport<kFP32, true> : k_transport<kFP32, false>;
+  if (mode == G4N_MODE_FP32_RECHECK) return count ? k_transport<kFP32, true> : k_transport<kFP32, false>;
+  return count ? k_transport<kLearned, true> : k_transport<kLearned, false>;
+}
+
+// Dynamic shared memory of a launch: the MLP weights and one scratch tile per warp (learned mode).
+size_t mlp_smem_bytes(int mode, int block) {
+  return mode == G4N_MODE_LEARNED ? sizeof(mlp::SmemWeights) + (size_t)(block / 32) * sizeof(mlp::SmemWarp) : 0;
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -609,9 +640,29 @@ int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refi
   *refill = b->refill_min > 0 ? b->refill_min : 8;
   *inter = b->interact_min > 0 ? b->interact_min : 8;
   if (*refill > 32 || *inter > 32) return g4n_fail(ctx, G4N_ERR_ARG, "transport: refill_min/interact_min must be 1..32");
-  if (b->mode != G4N_MODE_FP64 && b->mode != G4N_MODE_FP32_RECHECK)
-    return g4n_fail(ctx, G4N_ERR_ARG, "transport: mode must be G4N_MODE_FP64 or G4N_MODE_FP32_RECHECK");
+  if (b->mode != G4N_MODE_FP64 && b->mode != G4N_MODE_FP32_RECHECK && b->mode != G4N_MODE_LEARNED)
+    return g4n_fail(ctx, G4N_ERR_ARG, "transport: unknown mode");
+  if (b->mode == G4N_MODE_LEARNED && !g4n_mlp_image(ctx))
+    return g4n_fail(ctx, G4N_ERR_STATE, "transport: learned mode needs MLP weights (g4n_mlp_load / g4n_mlp_train)");
   return G4N_OK;
+}
+
+// Launch the persistent transport kernel of mode b->mode with parameters P on `st`.
+int launch_transport(g4n_ctx *ctx, const g4n_batch_desc *b, TParams &P, int block, cudaStream_t st) {
+  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
+  const size_t smem = mlp_smem_bytes(b->mode, block);
+  P.mlp_w = g4n_mlp_image(ctx);
+  if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = b->blocks_per_sm;
+  if (per_sm <= 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    per_sm = std::max(per_sm, 1);
+  }
+  int64_t grid = (int64_t)ctx->sm_count * per_sm;
+  const int64_t need = (P.total + block - 1) / block;
+  grid = std::max<int64_t>(1, std::min(grid, need));
+  kern<<<(int)grid, block, smem, st>>>(P);
+  return launch_error(ctx, "transport launch");
 }
 
 int grid_for(g4n_ctx *ctx, int64_t n, int block) {
@@ -645,22 +696,36 @@ int g4n_compute_step(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, c
   int rc = check_geom(ctx, geom);
   if (rc) return rc;
   if (n < 0) return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: n < 0");
-  if (mode != G4N_MODE_FP64 && mode != G4N_MODE_FP32_RECHECK)
-    return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: mode must be G4N_MODE_FP64 or G4N_MODE_FP32_RECHECK");
+  if (mode != G4N_MODE_FP64 && mode != G4N_MODE_FP32_RECHECK && mode != G4N_MODE_LEARNED)
+    return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: unknown mode");
+  if (mode == G4N_MODE_LEARNED && !g4n_mlp_image(ctx))
+    return g4n_fail(ctx, G4N_ERR_STATE, "compute_step: learned mode needs MLP weights");
   if (n == 0) return G4N_OK;
   if (!pos || !dir || !depth || !path || !out_step || !out_safety || !out_limiter)
     return g4n_fail(ctx, G4N_ERR_ARG, "compute_step: null array");
   if ((rc = ensure_ws(ctx, 0))) return rc;
   cudaSetDevice(ctx->device);
   Workspace *ws = (Workspace *)ctx->ws;
-  auto kern = mode == G4N_MODE_FP64 ? k_compute_step<kFP64> : k_compute_step<kFP32>;
-  kern<<<grid_for(ctx, n, 128), 128, 0, (cudaStream_t)stream>>>(ctx->d_geoms, geom, n, pos, dir, depth, path, proposed,
-                                                                 out_step, out_safety, out_limiter, &ws->status);
+  auto kern = mode == G4N_MODE_FP64 ? k_compute_step<kFP64>
+                                    : (mode == G4N_MODE_FP32_RECHECK ? k_compute_step<kFP32> : k_compute_step<kLearned>);
+  const size_t smem = mlp_smem_bytes(mode, 128);
+  if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<grid_for(ctx, n, 128), 128, smem, (cudaStream_t)stream>>>(ctx->d_geoms, geom, n, pos, dir, depth, path,
+                                                                    proposed, out_step, out_safety, out_limiter,
+                                                                    &ws->status, g4n_mlp_image(ctx));
   return launch_error(ctx, "compute_step launch");
 }
 
+static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, uint64_t *out_counters,
+                          uint64_t *out_track_hash, double *out_track_len, g4n_stream stream, bool logging);
+
 int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, uint64_t *out_counters,
                         uint64_t *out_track_hash, double *out_track_len, g4n_stream stream) {
+  return transport_impl(ctx, b, out_edep, out_counters, out_track_hash, out_track_len, stream, false);
+}
+
+static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, uint64_t *out_counters,
+                          uint64_t *out_track_hash, double *out_track_len, g4n_stream stream, bool logging) {
   if (!ctx || !b) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null argument");
   if (b->n_items < 1 || !b->items) return g4n_fail(ctx, G4N_ERR_ARG, "transport: no work items");
   if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null output");
@@ -726,17 +791,8 @@ int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep,
   P.out_len = out_track_len;
   P.refill_min = refill;
   P.interact_min = inter;
-  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
-  int per_sm = b->blocks_per_sm;
-  if (per_sm <= 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
-    per_sm = std::max(per_sm, 1);
-  }
-  int64_t grid = (int64_t)ctx->sm_count * per_sm;
-  const int64_t need = (total + block - 1) / block;
-  grid = std::max<int64_t>(1, std::min(grid, need));
-  kern<<<(int)grid, block, 0, st>>>(P);
-  return launch_error(ctx, "transport launch");
+  P.log = logging ? &ws->log : nullptr;
+  return launch_transport(ctx, b, P, block, st);
 }
 
 int g4n_transport_batch_host(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, uint64_t *out_counters,
@@ -776,6 +832,45 @@ int g4n_transport_batch_host(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_
       (d_l && cudaMemcpyAsync(out_track_len, d_l, l_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess))
     return g4n_fail(ctx, G4N_ERR_CUDA, "transport_host: copy back failed");
   return g4n_sync(ctx, stream);
+}
+
+int g4n_mlp_log(g4n_ctx *ctx, const g4n_batch_desc *b, float *feat, int32_t *label, int32_t *ncand, int64_t capacity,
+                int64_t *out_count, g4n_stream stream) {
+  if (!ctx || !b || !out_count) return g4n_fail(ctx, G4N_ERR_ARG, "mlp_log: null argument");
+  if (ctx->device < 0) return g4n_fail(ctx, G4N_ERR_STATE, "host-only context: no device queries");
+  if (capacity < 0 || (capacity > 0 && (!feat || !label || !ncand))) return g4n_fail(ctx, G4N_ERR_ARG, "mlp_log: bad buffers");
+  if (b->mode != G4N_MODE_FP64) return g4n_fail(ctx, G4N_ERR_ARG, "mlp_log: samples are logged by the plain FP64 navigator");
+  int rc = ensure_ws(ctx, (size_t)std::max(b->n_items, 1) * sizeof(DItem));
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace *ws = (Workspace *)ctx->ws;
+  dev::MlpLog L{feat, label, ncand, &ws->log_count, capacity};
+  if (cudaMemcpyAsync(&ws->log, &L, sizeof(L), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(&ws->log_count, 0, sizeof(unsigned long long), st) != cudaSuccess)
+    return g4n_fail(ctx, G4N_ERR_CUDA, "mlp_log: setup failed");
+  // scratch outputs of the logging run (tallies and counters are not returned)
+  int64_t stride = b->tally_stride;
+  double *edep = nullptr;
+  unsigned long long *cnt = nullptr;
+  if (cudaMalloc(&edep, (size_t)b->n_tally_batches * stride * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&cnt, G4N_N_COUNTERS * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaFree(edep);
+    return g4n_fail(ctx, G4N_ERR_OOM, "mlp_log: allocation failed");
+  }
+  cudaMemsetAsync(edep, 0, (size_t)b->n_tally_batches * stride * sizeof(double), st);
+  cudaMemsetAsync(cnt, 0, G4N_N_COUNTERS * sizeof(unsigned long long), st);
+  rc = transport_impl(ctx, b, edep, (uint64_t *)cnt, nullptr, nullptr, stream, true);
+  unsigned long long c = 0;
+  if (rc == G4N_OK) {
+    cudaMemcpyAsync(&c, &ws->log_count, sizeof(c), cudaMemcpyDeviceToHost, st);
+    rc = g4n_sync(ctx, stream);
+  }
+  cudaFree(edep);
+  cudaFree(cnt);
+  if (rc) return rc;
+  *out_count = (int64_t)std::min<unsigned long long>(c, (unsigned long long)capacity);
+  return G4N_OK;
 }
 
 int g4n_sync(g4n_ctx *ctx, g4n_stream stream) {
@@ -915,16 +1010,8 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     P.out_len = out_track_len;
     P.refill_min = refill;
     P.interact_min = inter;
-    const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
-    int per_sm = b->blocks_per_sm;
-    if (per_sm <= 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
-      per_sm = std::max(per_sm, 1);
-    }
-    int64_t grid = (int64_t)ctx->sm_count * per_sm;
-    grid = std::max<int64_t>(1, std::min(grid, (total + block - 1) / block));
-    kern<<<(int)grid, block, 0, st>>>(P);
-    rc = launch_error(ctx, "transport_noalloc launch");
+    P.log = nullptr;
+    rc = launch_transport(ctx, b, P, block, st);
     if (rc) return rc;
   }
   // report this call's device status bits in the last counter slot

@@ -24,7 +24,9 @@ def env():
     from paper_1209_5235_gb300 import build
     build.build()
     import paper_1209_5235_gb300 as g4
+    from synth.mlp_init import mlp_init
     ctx = g4.g4n_create(0)
+    g4.g4n_mlp_load(ctx, mlp_init(7))   # learned mode: any weights give the same results
     yield g4, torch, ctx
     g4.g4n_destroy(ctx)
 
@@ -65,7 +67,7 @@ def test_locate_parity(env, name):
     assert (d_ref >= 2).sum() > 0  # the cases do reach daughters
 
 
-MODES = [0, 1]   # G4N_MODE_FP64, G4N_MODE_FP32_RECHECK
+MODES = [0, 1, 2]   # G4N_MODE_FP64, G4N_MODE_FP32_RECHECK, G4N_MODE_LEARNED
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -153,7 +155,7 @@ def test_transport_parity(env, name, n, mode):
                                                                    e_kind="loguniform", e0=0.05, e1=5.0))
     seed = 0x7A0C0000
     r = og.transport(src, seed, n, threads=0)
-    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, diagnostics=(mode == 1))
+    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, diagnostics=(mode >= 1))
     g4.g4n_sync(ctx)
     _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
 
@@ -210,7 +212,7 @@ def test_transport_edge_cases(env):
     _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
     # odd launch shapes give identical histories
     r = og.transport(src, 7, 3001)
-    for bs, per_sm, rm, im, mode in ((32, 1, 1, 1, 0), (96, 3, 32, 32, 1), (128, 0, 0, 0, 1), (64, 2, 5, 17, 0)):
+    for bs, per_sm, rm, im, mode in ((32, 1, 1, 1, 0), (96, 3, 32, 32, 1), (128, 0, 0, 0, 2), (64, 2, 5, 17, 2)):
         edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, 7, 3001, block_size=bs, blocks_per_sm=per_sm,
                                           refill_min=rm, interact_min=im, mode=mode)
         g4.g4n_sync(ctx)
