@@ -110,6 +110,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+WORKLOADS = {
+    "tiny": "tiny scene: 1 m water-like cube with 10 boxes (2-10 cm), 8x8x8 voxels; 10^4 gamma at 1 MeV isotropic",
+    "batched": "256 independent water-like 1 m worlds with log-uniform 10-5000 mixed boxes/tubes/orbs rotated about z, "
+               "smart voxels; 10^3-10^5 gamma each (5.65e6 total), log-uniform 0.05-5 MeV, one persistent launch",
+    "barrel": "cylindrical barrel: 30 tube shells (r 50-1500 mm, 3 m) x 64 phi segments + 2000 lead-like orbs, smart "
+              "voxels; 10^7 gamma log-uniform 0.02-20 MeV isotropic from points on the axis",
+    "barrel_learned": "barrel scene with the learned candidate proposal (MLP trained on steps logged by the plain "
+                      "navigator); 10^7 gamma",
+}
+
+
 def parse_voxel(spec: str):
     """'default' | 'smart' | 'fixed:AXES:SLICES' e.g. fixed:2,0:51,11 (z then x)."""
     from synth.scenes import VoxelSpec
@@ -202,10 +213,79 @@ def time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream,
     return ms, g4.counters_dict(cnt), t_wall
 
 
+def time_graph(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream, launch):
+    """The same K timed launches replayed from a CUDA graph of the batch."""
+    graph = g4.g4n_graph_create(ctx, items, seed, edep, cnt, n_batches=edep.shape[0], mode=mode, **launch)
+    try:
+        for k in range(args.warmup):
+            g4.g4n_graph_launch(graph, seed + 1000 + k, stream)
+        g4.g4n_sync(ctx, stream)
+        edep.zero_()
+        cnt.zero_()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            g4.g4n_graph_launch(graph, seed + k, stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        g4.g4n_sync(ctx, stream)
+    finally:
+        g4.g4n_graph_destroy(graph)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    c = g4.counters_dict(cnt)
+    return c["steps"] / (sum(ms) / 1e3)
+
+
+def setup_workload(g4, ctx, args, rank):
+    """(items, stride, seed, n_tracks, description, modes) of the chosen workload on this rank."""
+    import synth
+    w = args.workload
+    if w == "calorimeter":
+        sc, src, seed = calorimeter(args.voxel)
+        gid = g4.build_scene(ctx, sc)
+        n = args.tracks
+        return g4.make_items([(gid, n, rank * n, src, 0)]), sc.n_volumes + 2, seed, n, WORKLOAD, ["fp64", "fp32_recheck"]
+    if w == "tiny":
+        sc = synth.scenes.tiny_scene()
+        gid = g4.build_scene(ctx, sc)
+        n = 10_000
+        return (g4.make_items([(gid, n, rank * n, synth.scenes.tiny_source(), 0)]), sc.n_volumes + 2,
+                synth.scenes.CONFIG_SEEDS[0][1], n, WORKLOADS["tiny"], ["fp64", "fp32_recheck"])
+    if w == "batched":
+        entries, off, tid = [], 0, 0
+        for s2, nt in synth.scenes.batched_scenes():
+            gid = g4.build_scene(ctx, s2)
+            entries.append((gid, nt, rank * 10_000_000 + tid, synth.scenes.batched_source(), off))
+            off += s2.n_volumes + 2
+            tid += nt
+        return g4.make_items(entries), off, synth.scenes.CONFIG_SEEDS[2][1], tid, WORKLOADS["batched"], \
+            ["fp64", "fp32_recheck"]
+    sc = synth.scenes.barrel_scene()
+    gid = g4.build_scene(ctx, sc)
+    n = 10_000_000
+    items = g4.make_items([(gid, n, rank * n, synth.scenes.barrel_source(), 0)])
+    seed = synth.scenes.CONFIG_SEEDS[3 if w == "barrel" else 4][1]
+    modes = ["fp64", "fp32_recheck"]
+    if w == "barrel_learned":
+        # the proposal network: 10^7 steps logged by the plain navigator, trained by the library's kernels
+        from synth.mlp_init import mlp_init
+        log_items = g4.make_items([(gid, 3_000_000, 50_000_000, synth.scenes.barrel_source(), 0)])
+        feat, label, ncand = g4.g4n_mlp_log(ctx, log_items, seed + 7, 10_000_000, sc.n_volumes + 2)
+        g4.g4n_mlp_load(ctx, mlp_init(41))
+        args.train_losses = g4.g4n_mlp_train(ctx, feat, label, ncand, epochs=2, batch=4096, lr=2e-3, seed=5).tolist()
+        args.train_samples = int(feat.shape[0])
+        del feat, label, ncand
+        modes = ["fp64", "fp32_recheck", "learned"]
+    return items, sc.n_volumes + 2, seed, n, WORKLOADS[w], modes
+
+
 def run_gpu(args):
     import torch
     import paper_1209_5235_gb300 as g4
     from paper_1209_5235_gb300 import build as b
+    from paper_1209_5235_gb300.autotune import autotune, DEFAULT
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -215,40 +295,47 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     b.build()
-    sc, src, seed = calorimeter(args.voxel)
     ctx = g4.g4n_create(local)
-    gid = g4.build_scene(ctx, sc)
-    n = args.tracks
-    tid0 = rank * n                      # weak scaling: every rank transports its own n track ids
-    items = g4.make_items([(gid, n, tid0, src, 0)])
-    nb, stride = 100, sc.n_volumes + 2
+    items, stride, seed, n, workload, mode_names = setup_workload(g4, ctx, args, rank)
+    nb = 100
     stream = torch.cuda.current_stream()
     edep = torch.zeros((nb, stride), dtype=torch.float64, device="cuda")
     cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
-    launch = dict(block_size=args.block, blocks_per_sm=args.blocks_per_sm, refill_min=args.refill_min,
-                  interact_min=args.interact_min)
-    modes = {"fp64": g4.G4N_MODE_FP64, "fp32_recheck": g4.G4N_MODE_FP32_RECHECK}
+    code = {"fp64": g4.G4N_MODE_FP64, "fp32_recheck": g4.G4N_MODE_FP32_RECHECK, "learned": g4.G4N_MODE_LEARNED}
     if args.mode != "auto":
-        modes = {args.mode: modes[args.mode]}
+        mode_names = [args.mode]
+    # launch shape per mode: autotuned on the same workload (untimed), or given
+    tuned = {}
+    if args.autotune:
+        tune = autotune(ctx, items, stride, seed + 500, modes=[code[m] for m in mode_names], budget_s=args.tune_s,
+                        stream=stream)
+        for m in mode_names:
+            tuned[m] = tune["per_mode"][code[m]]["cfg"]
+    manual = dict(block_size=args.block, blocks_per_sm=args.blocks_per_sm, refill_min=args.refill_min,
+                  interact_min=args.interact_min)
+    launch = {m: tuned.get(m, manual) for m in mode_names}
     # matched results: the same histories, bit for bit, in every mode (one launch with hashes each)
-    hashes = {}
-    for name, mode in modes.items():
+    ref_h = None
+    matched = True
+    for m in mode_names:
         h = torch.zeros(n, dtype=torch.int64, device="cuda")
         e2 = torch.zeros_like(edep)
         c2 = torch.zeros_like(cnt)
-        g4.g4n_transport_batch(ctx, items, seed, e2, c2, h, n_batches=nb, mode=mode, stream=stream, **launch)
+        g4.g4n_transport_batch(ctx, items, seed, e2, c2, h, n_batches=nb, mode=code[m], stream=stream, **launch[m])
         g4.g4n_sync(ctx, stream)
-        hashes[name] = h
-    ref = next(iter(hashes.values()))
-    matched = all(bool(torch.equal(h, ref)) for h in hashes.values())
-    del hashes
+        if ref_h is None:
+            ref_h = h
+        else:
+            matched = matched and bool(torch.equal(h, ref_h))
+        del h, e2, c2
+    del ref_h
     results = {}
     if dist:
         dist.barrier()
     with ClockSampler(local) as clk:
-        for name, mode in modes.items():
-            ms, c, t_wall = time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream, launch)
+        for m in mode_names:
+            ms, c, t_wall = time_mode(g4, torch, ctx, items, seed, code[m], args, edep, cnt, flush, stream, launch[m])
             t_dev = sum(ms) / 1e3
             steps_total, tracks_total = c["steps"], c["tracks"]
             if dist:
@@ -258,16 +345,17 @@ def run_gpu(args):
                 st = torch.tensor([steps_total, tracks_total], dtype=torch.int64, device="cuda")
                 dist.all_reduce(st)
                 steps_total, tracks_total = int(st[0].item()), int(st[1].item())
-            results[name] = {"steps_per_s": steps_total / t_dev, "tracks_per_s": tracks_total / t_dev,
-                             "ms_per_step": 1e3 * t_dev / args.steps, "ms_launch_mean": float(np.mean(ms)),
-                             "steps_per_track": steps_total / max(tracks_total, 1), "wall_s": t_wall}
+            results[m] = {"steps_per_s": steps_total / t_dev, "tracks_per_s": tracks_total / t_dev,
+                          "ms_per_step": 1e3 * t_dev / args.steps, "ms_launch_mean": float(np.mean(ms)),
+                          "steps_per_track": steps_total / max(tracks_total, 1), "launch": launch[m]}
     chosen = max(results, key=lambda k: results[k]["steps_per_s"]) if matched else "fp64"
-    mode = modes.get(chosen, g4.G4N_MODE_FP64)
+    mode = code[chosen]
+    graph_value = time_graph(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream, launch[chosen])
     # algorithmic work of one launch: a counting launch with the timed seed (outside the timed region)
     cnt.zero_()
     edep.zero_()
     g4.g4n_transport_batch(ctx, items, seed, edep, cnt, n_batches=nb, mode=mode, stream=stream, diagnostics=True,
-                           **launch)
+                           **launch[chosen])
     g4.g4n_sync(ctx, stream)
     cdiag = g4.counters_dict(cnt)
     # end to end through the host-buffer entry point: H2D of the batch description, D2H of the tallies
@@ -275,7 +363,7 @@ def run_gpu(args):
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         out = g4.g4n_transport_batch_host(ctx, items, seed + k, stride, n_batches=nb, mode=mode, stream=stream,
-                                          out=out, **launch)
+                                          out=out, **launch[chosen])
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             e2e_t += dt
@@ -285,7 +373,7 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_t = float(tt.item())
     e2e = {"value": e2e_steps * world / e2e_t, "unit": "steps/s",
-           "h2d_bytes_per_step": int(ctypes.sizeof(g4.g4n_work_item) + ctypes.sizeof(g4.g4n_batch_desc)),
+           "h2d_bytes_per_step": int(len(items) * ctypes.sizeof(g4.g4n_work_item) + ctypes.sizeof(g4.g4n_batch_desc)),
            "d2h_bytes_per_step": int(nb * stride * 8 + g4.G4N_N_COUNTERS * 8)}
     g4.g4n_destroy(ctx)
     if rank != 0:
@@ -302,15 +390,15 @@ def run_gpu(args):
         "metric": METRIC, "value": R["steps_per_s"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "tracks_per_gpu": n, "mode": chosen,
-                   "l2": "flushed between timed steps (256 MB write)", "block": args.block or 128,
-                   "blocks_per_sm": args.blocks_per_sm or "occupancy", "refill_min": args.refill_min or 8,
-                   "interact_min": args.interact_min or 8, "voxel": args.voxel},
+        "config": {"workload": workload, "tracks_per_gpu": n, "mode": chosen,
+                   "l2": "flushed between timed steps (256 MB write)", "launch": launch[chosen],
+                   "autotuned": bool(args.autotune), "voxel": args.voxel if args.workload == "calorimeter" else "smart"},
         "tracks_per_s": R["tracks_per_s"],
         "steps_per_track": R["steps_per_track"],
         "modes": results,
         "matched_results": matched,
         "plain_fp64_steps_per_s": results.get("fp64", {}).get("steps_per_s"),
+        "graph_replay_steps_per_s": graph_value,
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
@@ -321,11 +409,14 @@ def run_gpu(args):
                 "frac": (hbm_bytes / t_launch / 1e9) / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None},
         "clocks": clk.summary(),
         "e2e": e2e,
-        "counters": {k: cdiag[k] for k in ("steps", "geom_steps", "phys_steps", "safety_skips", "cand_box", "inside",
-                                           "vox_nodes", "dist_out", "rechecks")},
+        "counters": {k: cdiag[k] for k in ("steps", "geom_steps", "phys_steps", "safety_skips", "cand_box",
+                                           "cand_tube", "cand_orb", "inside", "vox_nodes", "dist_out", "rechecks",
+                                           "proposals", "pruned")},
     }
-    if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(sc, src, seed)
+    if getattr(args, "train_losses", None):
+        line["learned"] = {"train_samples": args.train_samples, "epoch_losses": args.train_losses}
+    if not args.no_cpu_baseline and world == 1 and args.workload == "calorimeter":
+        line["cpu_baseline"] = cpu_baseline(*calorimeter(args.voxel))
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -345,6 +436,10 @@ def main():
     ap.add_argument("--interact-min", type=int, default=0)
     ap.add_argument("--mode", default="auto", choices=["auto", "fp64", "fp32_recheck"])
     ap.add_argument("--voxel", default="smart")
+    ap.add_argument("--workload", default="calorimeter",
+                    choices=["calorimeter", "tiny", "batched", "barrel", "barrel_learned"])
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--tune-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

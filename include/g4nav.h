@@ -249,6 +249,19 @@ int g4n_transport_batch(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_e
 int g4n_transport_batch_host(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_edep, uint64_t *out_counters,
                              uint64_t *out_track_hash, double *out_track_len, g4n_stream stream);
 
+/* ---------------------------------------------------------------- CUDA graph of a batch */
+
+/* A batch launched repeatedly with new seeds (the same items and outputs) recorded once as a CUDA
+ * graph: a node resetting the graph's own queue head, then the persistent kernel.  The items are
+ * copied at creation; out_* are the DEVICE outputs every replay accumulates into (zero them between
+ * replays as needed).  g4n_graph_launch replays it on `stream` with `seed`; device-side errors are
+ * reported by g4n_sync of the context.  One replay in flight per graph. */
+typedef struct g4n_graph g4n_graph;
+int g4n_graph_create(g4n_ctx *ctx, const g4n_batch_desc *batch, double *out_edep, uint64_t *out_counters,
+                     uint64_t *out_track_hash, double *out_track_len, g4n_graph **out_graph);
+int g4n_graph_launch(g4n_graph *graph, uint64_t seed, g4n_stream stream);
+int g4n_graph_destroy(g4n_graph *graph);
+
 /* ---------------------------------------------------------------- learned candidate proposal */
 
 /* A small network proposes which candidate daughter of the current voxel node the ray enters

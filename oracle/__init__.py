@@ -79,6 +79,7 @@ def lib():
             "o_transport": (i, [i, vp, u64, i64, i64, d, i64, i, vp, vp, vp, vp, i]),
             "o_free_path": (d, [i, vp, vp, d, d, vp]),
             "o_locate_many": (None, [i, i64, vp, vp, vp, vp]),
+            "o_transport_trace": (i, [i, vp, u64, i64, d, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
             "o_compute_step_many": (None, [i, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -157,6 +158,18 @@ class Geometry:
         paths = np.full((n, DMAX), -1, dtype=np.int32)
         lib().o_locate_many(self.gid, int(n), _p(_f64(pos)), _p(_f64(dirs)), _p(depth), _p(paths))
         return depth, paths
+
+    def trace(self, source, seed: int, tid: int, cutoff: float = 0.01, cap: int = 100000):
+        """Per-step states of one history: dict of pos, dir, E, path, depth, step, limiter, sphys."""
+        src = _f64(source.as_array())
+        pos, dirs = np.zeros((cap, 3)), np.zeros((cap, 3))
+        E, steps, sph = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+        paths = np.zeros((cap, DMAX), dtype=np.int32)
+        depth, lim = np.zeros(cap, dtype=np.int32), np.zeros(cap, dtype=np.int32)
+        n = lib().o_transport_trace(self.gid, _p(src), ctypes.c_uint64(seed), int(tid), float(cutoff), int(cap),
+                                    _p(pos), _p(dirs), _p(E), _p(paths), _p(depth), _p(steps), _p(lim), _p(sph))
+        return {"pos": pos[:n], "dir": dirs[:n], "E": E[:n], "path": paths[:n], "depth": depth[:n],
+                "step": steps[:n], "limiter": lim[:n], "sphys": sph[:n]}
 
     def compute_step_many(self, pos, dirs, depth, paths, proposed=None):
         """Brute-force steps for n queries; returns (step, limiter, safety)."""

@@ -1018,3 +1018,68 @@ void o_compute_step_many(int gi, int64_t n, const double *pos, const double *dir
                    &step[i], &limiter[i], &safety[i]);
   }
 }
+
+/* Per-step trace of one history (debugging aid for parity failures): for every step the
+ * state before it (position, direction, energy, path) and its outcome (step length,
+ * limiter, event code of the record hashed after it).  Returns the steps recorded. */
+int o_transport_trace(int gi, const double *src, uint64_t seed, int64_t tid, double cutoff, int64_t cap,
+                      double *pos, double *dir, double *E_out, int *paths, int *depth_out, double *steps,
+                      int *limiters, double *sphys_out) {
+  const OGeom *g = G[gi];
+  double x[3], u[3], E;
+  gen_source(src, seed, tid, x, u, &E);
+  int path[O_DMAX];
+  for (int k = 0; k < O_DMAX; ++k) path[k] = -1;
+  int depth = locate_impl(g, x, u, path, NULL);
+  if (depth == 0) return 0;
+  ORng rp = {seed, tid, 1u, 0u};
+  double Y = -log(rng_u(&rp));
+  int64_t n = 0;
+  int nzero = 0;
+  while (n < cap) {
+    int leaf = path[depth - 1];
+    double mu, mupe;
+    mu_lookup(&g->mat[g->vol[leaf].mat], E, &mu, &mupe);
+    double sph = mu > 0.0 ? Y / mu : O_INF;
+    int lim;
+    double sgeo = geom_step(g, path, depth, x, u, &lim, NULL, NULL);
+    memcpy(pos + 3 * n, x, sizeof(x));
+    memcpy(dir + 3 * n, u, sizeof(u));
+    E_out[n] = E;
+    memcpy(paths + O_DMAX * n, path, sizeof(path));
+    depth_out[n] = depth;
+    sphys_out[n] = sph;
+    if (sgeo <= sph) {
+      steps[n] = sgeo;
+      limiters[n] = lim;
+      ++n;
+      x[0] += sgeo * u[0]; x[1] += sgeo * u[1]; x[2] += sgeo * u[2];
+      if (mu > 0.0) { Y = Y - sgeo * mu; if (Y < 0.0) Y = 0.0; }
+      depth = relocate_impl(g, path, depth, x, u, NULL);
+      if (sgeo <= kHalf) ++nzero; else nzero = 0;
+      if (depth > 0 && nzero >= 10) {
+        x[0] += 100.0 * kTol * u[0]; x[1] += 100.0 * kTol * u[1]; x[2] += 100.0 * kTol * u[2];
+        nzero = 0;
+        depth = relocate_impl(g, path, depth, x, u, NULL);
+      }
+      if (depth == 0) break;
+      continue;
+    }
+    steps[n] = sph;
+    limiters[n] = LIM_PHYS;
+    ++n;
+    x[0] += sph * u[0]; x[1] += sph * u[1]; x[2] += sph * u[2];
+    nzero = 0;
+    double U = rng_u(&rp);
+    if (U * mu < mupe) break;
+    double eta, cost, cph, sph2;
+    kahn(E, &rp, &eta, &cost);
+    azimuth(&rp, &cph, &sph2);
+    rotate_about(u, cost, cph, sph2);
+    double E1 = E / eta;
+    if (E1 < cutoff) break;
+    E = E1;
+    Y = -log(rng_u(&rp));
+  }
+  return (int)n;
+}

@@ -1,0 +1,72 @@
+"""Launch-shape autotuner of the persistent transport kernel.
+
+Results never depend on the launch shape (block size, blocks per SM, the warp
+refill and interaction thresholds) or on the precision mode, only speed does.
+The tuner times trial launches of the caller's batch with CUDA events and walks
+one parameter at a time from the defaults, keeping any value that is faster
+(coordinate descent), within a time budget.  It only calls the C ABI through the
+binding.
+"""
+from __future__ import annotations
+
+import itertools
+import time
+
+from . import binding as b
+
+SPACE = {
+    "block_size": (64, 96, 128),
+    "blocks_per_sm": (0, 2, 3),
+    "refill_min": (4, 6, 8, 12, 16),
+    "interact_min": (4, 6, 8, 12, 16),
+}
+DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8}
+
+
+def time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps=2, stream=None):
+    """Median device time (ms) of `reps` launches with launch shape `cfg`."""
+    import torch
+    st = stream or torch.cuda.current_stream()
+    ts = []
+    for r in range(reps):
+        edep.zero_()
+        cnt.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.g4n_transport_batch(ctx, items, seed + r, edep, cnt, n_batches=edep.shape[0], mode=mode, stream=st, **cfg)
+        e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    b.g4n_sync(ctx, st)
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def autotune(ctx, items, stride, seed, modes=(b.G4N_MODE_FP64, b.G4N_MODE_FP32_RECHECK), n_batches=100, reps=2,
+             budget_s=30.0, space=None, stream=None):
+    """Best (mode, launch shape) for the batch; returns dict(mode, cfg, ms, per_mode, trials)."""
+    import torch
+    space = space or SPACE
+    edep = torch.zeros((n_batches, stride), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(b.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
+    t_end = time.perf_counter() + budget_s
+    trials = []
+    per_mode = {}
+    for mode in modes:
+        time_launch(ctx, items, seed, edep, cnt, mode, DEFAULT, reps=1, stream=stream)   # warm-up
+        cfg = dict(DEFAULT)
+        best = time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps, stream)
+        trials.append((mode, dict(cfg), best))
+        for key in space:
+            for val in space[key]:
+                if val == cfg[key] or time.perf_counter() > t_end:
+                    continue
+                trial = dict(cfg, **{key: val})
+                ms = time_launch(ctx, items, seed, edep, cnt, mode, trial, reps, stream)
+                trials.append((mode, dict(trial), ms))
+                if ms < best:
+                    best, cfg = ms, trial
+        per_mode[mode] = {"cfg": cfg, "ms": best}
+    mode = min(per_mode, key=lambda m: per_mode[m]["ms"])
+    return {"mode": mode, "cfg": per_mode[mode]["cfg"], "ms": per_mode[mode]["ms"], "per_mode": per_mode,
+            "trials": len(trials)}

@@ -41,7 +41,7 @@ EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_sc
             "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_place", "g4n_voxelize", "g4n_geom_finalize",
             "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_transport_batch", "g4n_transport_batch_host",
             "g4n_transport_batch_noalloc", "g4n_mlp_load", "g4n_mlp_get", "g4n_mlp_log", "g4n_mlp_train",
-            "g4n_mlp_grad", "g4n_mlp_predict"]
+            "g4n_mlp_grad", "g4n_mlp_predict", "g4n_graph_create", "g4n_graph_launch", "g4n_graph_destroy"]
 
 __all__ = EXPORTED + ["G4N_FLAG_DIAGNOSTICS", "G4NError", "load", "lib_path", "build_scene", "make_items", "counters_dict", "voxel_params",
                       "COUNTER_NAMES", "PARITY_COUNTERS", "G4N_DMAX", "G4N_N_COUNTERS", "G4N_MODE_FP64",
@@ -116,6 +116,8 @@ def load():
         "g4n_mlp_train": [vp, i64, vp, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp],
         "g4n_mlp_grad": [vp, i64, vp, vp, vp, i32, vp, vp],
         "g4n_mlp_predict": [vp, i64, vp, vp, vp],
+        "g4n_graph_create": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, ctypes.POINTER(ctypes.c_void_p)],
+        "g4n_graph_launch": [vp, ctypes.c_uint64, vp], "g4n_graph_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -465,3 +467,30 @@ def g4n_mlp_predict(ctx, feat, stream=None):
     _check(ctx, load().g4n_mlp_predict(ctx, int(feat.shape[0]), _dptr(feat, torch.float32, "feat"),
                                        _dptr(out, torch.float32, "logits"), _stream(stream)))
     return out
+
+
+# ---------------------------------------------------------------- CUDA graphs
+
+def g4n_graph_create(ctx, items, seed: int, edep, counters, track_hash=None, track_len=None, cutoff: float = 0.01,
+                     mode: int = G4N_MODE_FP64, n_batches: int = 100, max_steps: int = 0, block_size: int = 0,
+                     blocks_per_sm: int = 0, refill_min: int = 0, interact_min: int = 0, diagnostics: bool = False):
+    """Record the batch as a CUDA graph writing into the given device outputs; returns the handle."""
+    import torch
+    d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
+              interact_min, diagnostics)
+    h = ctypes.c_void_p()
+    _check(ctx, load().g4n_graph_create(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
+                                        _dptr(counters, torch.int64, "counters"),
+                                        _dptr(track_hash, torch.int64, "track_hash"),
+                                        _dptr(track_len, torch.float64, "track_len"), ctypes.byref(h)))
+    return (ctx, h)
+
+
+def g4n_graph_launch(graph, seed: int, stream=None) -> None:
+    ctx, h = graph
+    _check(ctx, load().g4n_graph_launch(h, ctypes.c_uint64(seed), _stream(stream)))
+
+
+def g4n_graph_destroy(graph) -> None:
+    ctx, h = graph
+    load().g4n_graph_destroy(h)

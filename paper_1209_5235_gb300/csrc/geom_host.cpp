@@ -56,9 +56,11 @@ Box3 solid_extent(const HSolid &so, double c, double s, const double *t) {
     if (so.dphi >= kTwoPi - 1e-12) {
       b = {{-rmax, -rmax, -so.c}, {rmax, rmax, so.c}};
     } else {
-      // phi range in the mother frame
+      // phi range in the mother frame, starting in [0, 2 pi) so that axis angles 0 .. 4 pi cover it
       double th = std::atan2(s, c);
-      double a0 = so.sphi + th, a1 = a0 + so.dphi;
+      double a0 = std::fmod(so.sphi + th, kTwoPi);
+      if (a0 < 0.0) a0 += kTwoPi;
+      const double a1 = a0 + so.dphi;
       double xs[16], ys[16];
       int n = 0;
       double ang[2] = {a0, a1};
@@ -66,11 +68,10 @@ Box3 solid_extent(const HSolid &so, double c, double s, const double *t) {
         xs[n] = rmax * std::cos(a); ys[n++] = rmax * std::sin(a);
         xs[n] = rmin * std::cos(a); ys[n++] = rmin * std::sin(a);
       }
-      // axis directions inside the range
-      for (int k = -8; k <= 8; ++k) {
-        double a = k * (kTwoPi / 4.0);
+      // axis directions inside the range (a0 < 2 pi, a1 < 4 pi)
+      for (int k = 0; k <= 8; ++k) {
+        const double a = k * (kTwoPi / 4.0);
         if (a > a0 && a < a1) { xs[n] = rmax * std::cos(a); ys[n++] = rmax * std::sin(a); }
-        if (n >= 14) break;
       }
       b.lo[0] = b.hi[0] = xs[0];
       b.lo[1] = b.hi[1] = ys[0];

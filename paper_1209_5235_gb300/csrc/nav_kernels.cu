@@ -647,6 +647,41 @@ int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refi
   return G4N_OK;
 }
 
+// Validate the work items of a batch and build their device records.
+int build_items(g4n_ctx *ctx, const g4n_batch_desc *b, std::vector<DItem> &items, int64_t &total) {
+  items.assign(b->n_items, DItem{});
+  total = 0;
+  for (int i = 0; i < b->n_items; ++i) {
+    const g4n_work_item &w = b->items[i];
+    int rc = check_geom(ctx, w.geom);
+    if (rc) return rc;
+    const int64_t nv = ctx->geoms[w.geom]->dview.n_vol;
+    if (w.n_tracks < 0 || w.track_id0 < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: negative track count or id");
+    if (w.tally_offset < 0 || w.tally_offset + nv + 2 > b->tally_stride)
+      return g4n_fail(ctx, G4N_ERR_ARG, "transport: tally columns out of range");
+    const g4n_source &s = w.source;
+    if (!s.isotropic) {
+      const double n2 = s.dir[0] * s.dir[0] + s.dir[1] * s.dir[1] + s.dir[2] * s.dir[2];
+      if (!(std::fabs(n2 - 1.0) <= 1e-12)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: source direction not unit");
+    }
+    if (s.e_kind < 0 || s.e_kind > 2 || !(s.e0 > 0.0) || (s.e_kind > 0 && !(s.e1 >= s.e0)))
+      return g4n_fail(ctx, G4N_ERR_ARG, "transport: bad source energy");
+    if (!(s.spot_sigma >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: negative spot sigma");
+    DItem &d = items[i];
+    std::memset(&d, 0, sizeof(d));
+    d.geom = w.geom;
+    d.n = w.n_tracks;
+    d.tid0 = w.track_id0;
+    d.tally_off = w.tally_offset;
+    d.start = total;
+    double src[16] = {s.pos[0], s.pos[1], s.pos[2], s.spot_sigma, (double)(s.has_z != 0), s.z0, s.z1,
+                      (double)(s.isotropic != 0), s.dir[0], s.dir[1], s.dir[2], (double)s.e_kind, s.e0, s.e1, 0.0, 0.0};
+    std::memcpy(d.src, src, sizeof(src));
+    total += w.n_tracks;
+  }
+  return G4N_OK;
+}
+
 // Launch the persistent transport kernel of mode b->mode with parameters P on `st`.
 int launch_transport(g4n_ctx *ctx, const g4n_batch_desc *b, TParams &P, int block, cudaStream_t st) {
   const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
@@ -733,36 +768,9 @@ static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_ede
   if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter)) return rc0;
   if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport: n_tally_batches < 1");
   if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: cutoff must be >= 0");
-  std::vector<DItem> items(b->n_items);
+  std::vector<DItem> items;
   int64_t total = 0;
-  for (int i = 0; i < b->n_items; ++i) {
-    const g4n_work_item &w = b->items[i];
-    int rc = check_geom(ctx, w.geom);
-    if (rc) return rc;
-    const int64_t nv = ctx->geoms[w.geom]->dview.n_vol;
-    if (w.n_tracks < 0 || w.track_id0 < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: negative track count or id");
-    if (w.tally_offset < 0 || w.tally_offset + nv + 2 > b->tally_stride)
-      return g4n_fail(ctx, G4N_ERR_ARG, "transport: tally columns out of range");
-    const g4n_source &s = w.source;
-    if (!s.isotropic) {
-      const double n2 = s.dir[0] * s.dir[0] + s.dir[1] * s.dir[1] + s.dir[2] * s.dir[2];
-      if (!(std::fabs(n2 - 1.0) <= 1e-12)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: source direction not unit");
-    }
-    if (s.e_kind < 0 || s.e_kind > 2 || !(s.e0 > 0.0) || (s.e_kind > 0 && !(s.e1 >= s.e0)))
-      return g4n_fail(ctx, G4N_ERR_ARG, "transport: bad source energy");
-    if (!(s.spot_sigma >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: negative spot sigma");
-    DItem &d = items[i];
-    std::memset(&d, 0, sizeof(d));
-    d.geom = w.geom;
-    d.n = w.n_tracks;
-    d.tid0 = w.track_id0;
-    d.tally_off = w.tally_offset;
-    d.start = total;
-    double src[16] = {s.pos[0], s.pos[1], s.pos[2], s.spot_sigma, (double)(s.has_z != 0), s.z0, s.z1,
-                      (double)(s.isotropic != 0), s.dir[0], s.dir[1], s.dir[2], (double)s.e_kind, s.e0, s.e1, 0.0, 0.0};
-    std::memcpy(d.src, src, sizeof(src));
-    total += w.n_tracks;
-  }
+  if (int rc1 = build_items(ctx, b, items, total)) return rc1;
   if (total == 0) return G4N_OK;
   int rc = ensure_ws(ctx, items.size() * sizeof(DItem));
   if (rc) return rc;
@@ -1020,3 +1028,137 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     return g4n_fail(ctx, G4N_ERR_CUDA, "transport_noalloc: status copy failed");
   return G4N_OK;
 }
+
+// ---------------------------------------------------------------- CUDA graphs of a transport batch
+//
+// A batch that is launched again and again (the same geometry, items and outputs, a new seed)
+// is recorded once as a CUDA graph: a node that resets the graph's own queue head, then the
+// persistent kernel.  Replays change only the seed in the kernel node, so a replay costs one
+// cudaGraphLaunch instead of an item upload, a memset and a kernel launch.
+
+struct g4n_graph {
+  g4n_ctx *ctx = nullptr;
+  void *scratch = nullptr;  // queue head (first 256 B) and the device item table
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t kernel_node = nullptr;
+  cudaKernelNodeParams kp{};
+  TParams P{};
+  void *args[1] = {nullptr};
+};
+
+extern "C" {
+
+int g4n_graph_create(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, uint64_t *out_counters,
+                     uint64_t *out_track_hash, double *out_track_len, g4n_graph **out) {
+  if (!ctx || !b || !out) return g4n_fail(ctx, G4N_ERR_ARG, "graph_create: null argument");
+  *out = nullptr;
+  if (ctx->device < 0) return g4n_fail(ctx, G4N_ERR_STATE, "host-only context: no device queries");
+  if (b->n_items < 1 || !b->items || !out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "graph_create: no items or outputs");
+  int block, refill, inter;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter)) return rc0;
+  if (b->n_tally_batches < 1 || !(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "graph_create: bad tallies or cutoff");
+  std::vector<DItem> items;
+  int64_t total = 0;
+  if (int rc1 = build_items(ctx, b, items, total)) return rc1;
+  if (total == 0) return g4n_fail(ctx, G4N_ERR_ARG, "graph_create: no tracks");
+  if (int rc2 = ensure_ws(ctx, 0)) return rc2;
+  cudaSetDevice(ctx->device);
+  g4n_graph *g = new g4n_graph();
+  g->ctx = ctx;
+  const size_t bytes = 256 + items.size() * sizeof(DItem);
+  if (cudaMalloc(&g->scratch, bytes) != cudaSuccess) {
+    delete g;
+    return g4n_fail(ctx, G4N_ERR_OOM, "graph_create: allocation failed");
+  }
+  DItem *d_items = (DItem *)((char *)g->scratch + 256);
+  if (cudaMemcpy(d_items, items.data(), items.size() * sizeof(DItem), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(g->scratch);
+    delete g;
+    return g4n_fail(ctx, G4N_ERR_CUDA, "graph_create: item upload failed");
+  }
+  Workspace *ws = (Workspace *)ctx->ws;
+  TParams &P = g->P;
+  P.geoms = ctx->d_geoms;
+  P.items = d_items;
+  P.n_items = b->n_items;
+  P.total = total;
+  P.q_head = (unsigned long long *)g->scratch;
+  P.status = &ws->status;
+  P.seed = b->seed;
+  P.cutoff = b->cutoff;
+  P.max_steps = b->max_steps > 0 ? b->max_steps : 1000000;
+  P.nb = b->n_tally_batches;
+  P.stride = b->tally_stride;
+  P.edep = out_edep;
+  P.counters = (unsigned long long *)out_counters;
+  P.out_hash = out_track_hash;
+  P.out_len = out_track_len;
+  P.refill_min = refill;
+  P.interact_min = inter;
+  P.log = nullptr;
+  P.mlp_w = g4n_mlp_image(ctx);
+  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
+  const size_t smem = mlp_smem_bytes(b->mode, block);
+  if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = b->blocks_per_sm;
+  if (per_sm <= 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    per_sm = std::max(per_sm, 1);
+  }
+  int64_t grid = (int64_t)ctx->sm_count * per_sm;
+  grid = std::max<int64_t>(1, std::min(grid, (total + block - 1) / block));
+  bool ok = cudaGraphCreate(&g->graph, 0) == cudaSuccess;
+  cudaGraphNode_t reset = nullptr;
+  if (ok) {
+    cudaMemsetParams mp{};
+    mp.dst = g->scratch;
+    mp.value = 0;
+    mp.elementSize = 1;
+    mp.width = 16;
+    mp.height = 1;
+    mp.pitch = 0;
+    ok = cudaGraphAddMemsetNode(&reset, g->graph, nullptr, 0, &mp) == cudaSuccess;
+  }
+  if (ok) {
+    g->args[0] = &g->P;
+    g->kp.func = (void *)kern;
+    g->kp.gridDim = dim3((unsigned)grid);
+    g->kp.blockDim = dim3((unsigned)block);
+    g->kp.sharedMemBytes = (unsigned)smem;
+    g->kp.kernelParams = g->args;
+    g->kp.extra = nullptr;
+    ok = cudaGraphAddKernelNode(&g->kernel_node, g->graph, &reset, 1, &g->kp) == cudaSuccess;
+  }
+  if (ok) ok = cudaGraphInstantiate(&g->exec, g->graph, 0) == cudaSuccess;
+  if (!ok) {
+    if (g->graph) cudaGraphDestroy(g->graph);
+    cudaFree(g->scratch);
+    delete g;
+    return g4n_fail(ctx, G4N_ERR_CUDA, "graph_create: graph construction failed");
+  }
+  *out = g;
+  return G4N_OK;
+}
+
+int g4n_graph_launch(g4n_graph *g, uint64_t seed, g4n_stream stream) {
+  if (!g) return G4N_ERR_ARG;
+  cudaSetDevice(g->ctx->device);
+  g->P.seed = seed;
+  if (cudaGraphExecKernelNodeSetParams(g->exec, g->kernel_node, &g->kp) != cudaSuccess ||
+      cudaGraphLaunch(g->exec, (cudaStream_t)stream) != cudaSuccess)
+    return g4n_fail(g->ctx, G4N_ERR_CUDA, "graph_launch failed");
+  return G4N_OK;
+}
+
+int g4n_graph_destroy(g4n_graph *g) {
+  if (!g) return G4N_OK;
+  cudaSetDevice(g->ctx->device);
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  cudaFree(g->scratch);
+  delete g;
+  return G4N_OK;
+}
+
+}  // extern "C"

@@ -58,13 +58,37 @@ def nested_scene():
     return Scene("nested", mats, solids, places, VoxelSpec(mode="smart"))
 
 
-def random_queries(og, scene, n, seed, box_half=None, surface_frac=0.5):
+def segments_scene():
+    """Tube segments (narrow, wide, exactly pi; with and without bore) at a systematic grid of start
+    angles and rotations, including combinations whose rotated phi range runs past 4 pi."""
+    m = toy_materials()
+    solids = [Solid(BOX, (400.0, 400.0, 400.0))]
+    places = [Placement(-1, 0, 0, (0, 0, 0))]
+    k = 0
+    for i, sphi in enumerate(np.linspace(0.0, 2 * math.pi, 6, endpoint=False) + 0.1):
+        for j, dphi in enumerate((0.4, 2.0, math.pi, 4.0, 5.36, 6.0)):
+            th = (k * 0.7361) % (2 * math.pi) - math.pi
+            rmin = 0.0 if (i + j) % 2 else 8.0
+            solids.append(Solid(TUBE, (rmin, 17.0, 12.0, float(sphi), float(dphi))))
+            cx, cy, cz = -330.0 + 60.0 * i, -330.0 + 60.0 * j, 30.0 * ((k % 5) - 2)
+            places.append(Placement(0, len(solids) - 1, 1 + k % 3, (cx, cy, cz), (math.cos(th), math.sin(th))))
+            k += 1
+    return Scene("segments", [m["water"], m["lead"], m["scint"], m["al"]], solids, places, VoxelSpec(mode="smart"))
+
+
+def random_queries(og, scene, n, seed, box_half=None, surface_frac=0.5, aim_frac=0.0):
     """Points inside the world (half of them moved onto a boundary along a random ray) with
-    random unit directions.  Surface points are produced by the oracle's own compute_step."""
+    random unit directions, a fraction `aim_frac` of them aimed near a random daughter.
+    Surface points are produced by the oracle's own compute_step."""
     rng = np.random.default_rng(seed)
     h = np.asarray(box_half if box_half is not None else world_half(scene) * 0.98)
     p = rng.uniform(-h, h, size=(n, 3))
     v = rng.normal(size=(n, 3))
+    if aim_frac > 0 and scene.n_volumes > 1:
+        k = rng.uniform(size=n) < aim_frac
+        tgt = np.array([scene.placements[int(i)].t for i in rng.integers(1, scene.n_volumes, n)])
+        tgt += rng.uniform(-10.0, 10.0, size=(n, 3))
+        v[k] = tgt[k] - p[k]
     v /= np.linalg.norm(v, axis=1)[:, None]
     k = int(n * surface_frac)
     if k:

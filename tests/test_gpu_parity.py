@@ -9,7 +9,7 @@ import pytest
 import oracle
 import synth
 from synth.scenes import VoxelSpec, Source
-from gpu_common import mixed_scene, nested_scene, random_queries, to_soa
+from gpu_common import mixed_scene, nested_scene, random_queries, segments_scene, to_soa
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +41,11 @@ SCENES = {
     "nested": lambda: nested_scene(),
     "nested_core": lambda: nested_scene(),
     "spheres": lambda: synth.scenes.spheres_scene(),
+    "segments": lambda: segments_scene(),
 }
-BOX_HALF = {"barrel": (1600.0, 1600.0, 1600.0), "calorimeter": (600.0, 600.0, 400.0), "nested_core": (12.0, 12.0, 12.0)}
+BOX_HALF = {"barrel": (1600.0, 1600.0, 1600.0), "calorimeter": (600.0, 600.0, 400.0), "nested_core": (12.0, 12.0, 12.0),
+            "segments": (360.0, 360.0, 90.0)}
+AIM = {"segments": 0.8, "mixed_smart": 0.3, "mixed_fixed": 0.3, "mixed_none": 0.3}
 
 
 def _build(env, name):
@@ -56,7 +59,7 @@ def test_locate_parity(env, name):
     g4, torch, ctx = env
     sc, og, gid = _build(env, name)
     n = 4000 if name in ("calorimeter", "spheres") else 20000
-    p, v = random_queries(og, sc, n, seed=11, box_half=BOX_HALF.get(name))
+    p, v = random_queries(og, sc, n, seed=11, box_half=BOX_HALF.get(name), aim_frac=AIM.get(name, 0.0))
     d_ref, path_ref = og.locate_many(p, v)
     d, path = g4.g4n_locate(ctx, gid, to_soa(p, torch), to_soa(v, torch))
     g4.g4n_sync(ctx)
@@ -76,7 +79,7 @@ def test_compute_step_parity(env, name, mode):
     g4, torch, ctx = env
     sc, og, gid = _build(env, name)
     n = 3000 if name in ("calorimeter", "spheres") else 20000
-    p, v = random_queries(og, sc, n, seed=12, box_half=BOX_HALF.get(name))
+    p, v = random_queries(og, sc, n, seed=12, box_half=BOX_HALF.get(name), aim_frac=AIM.get(name, 0.0))
     d_ref, path_ref = og.locate_many(p, v)
     ok = d_ref > 0
     p, v, d_ref, path_ref = p[ok], v[ok], d_ref[ok], path_ref[ok]
@@ -146,7 +149,7 @@ def _compare_transport(g4, r, edep, cnt, h, ln, nv, exact_tally_rel=1e-9):
 
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name,n", [("tiny", 10000), ("calorimeter", 20000), ("mixed_smart", 20000),
-                                    ("barrel", 20000), ("nested", 20000), ("spheres", 5000)])
+                                    ("barrel", 20000), ("nested", 20000), ("spheres", 5000), ("segments", 20000)])
 def test_transport_parity(env, name, n, mode):
     g4, torch, ctx = env
     sc, og, gid = _build(env, name)
@@ -240,3 +243,92 @@ def test_query_edge_cases(env):
     assert ex.value.code == g4.G4N_ERR_ARG
     with pytest.raises(g4.G4NError):
         g4.g4n_locate(ctx, 999, pos, dirs)
+
+
+def test_graph_replay_identical(env):
+    """A batch recorded as a CUDA graph and replayed with new seeds gives the direct launches' histories."""
+    g4, torch, ctx = env
+    sc, og, gid = _build(env, "mixed_smart")
+    src = Source(pos=(1.0, 2.0, 3.0), isotropic=True, e_kind="loguniform", e0=0.05, e1=5.0)
+    n = 5000
+    items = g4.make_items([(gid, n, 0, src, 0)])
+    stride = sc.n_volumes + 2
+    out = [torch.zeros((100, stride), dtype=torch.float64, device="cuda"),
+           torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda"),
+           torch.zeros(n, dtype=torch.int64, device="cuda")]
+    graph = g4.g4n_graph_create(ctx, items, 0, out[0], out[1], out[2], mode=1)
+    try:
+        for seed in (17, 18, 17):
+            for t in out:
+                t.zero_()
+            g4.g4n_graph_launch(graph, seed)
+            g4.g4n_sync(ctx)
+            r = og.transport(src, seed, n)
+            assert np.array_equal(out[2].cpu().numpy().view(np.uint64), r["hashes"])
+            assert g4.counters_dict(out[1])["steps"] == int(r["counters"][1])
+    finally:
+        g4.g4n_graph_destroy(graph)
+
+
+def test_autotuned_shape_gives_identical_results(env):
+    from paper_1209_5235_gb300.autotune import autotune
+    g4, torch, ctx = env
+    sc, og, gid = _build(env, "barrel")
+    src = synth.scenes.barrel_source()
+    n = 20000
+    items = g4.make_items([(gid, n, 0, src, 0)])
+    res = autotune(ctx, items, sc.n_volumes + 2, 5, modes=(0, 1), budget_s=5.0, reps=1)
+    assert res["mode"] in (0, 1) and res["trials"] >= 2
+    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, 33, n, mode=res["mode"], **res["cfg"])
+    g4.g4n_sync(ctx)
+    r = og.transport(src, 33, n)
+    _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
+
+
+def _full_size_sampled(env, entries_fn, seed, n_sample=300):
+    """Both modes over a full-size launch: identical histories across modes, and a random sample
+    of them replayed one by one by the oracle."""
+    g4, torch, ctx = env
+    entries, stride, total, geoms = entries_fn(g4, ctx)
+    items = g4.make_items(entries)
+    hashes = {}
+    for mode in (0, 1):
+        edep = torch.zeros((100, stride), dtype=torch.float64, device="cuda")
+        cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
+        h = torch.zeros(total, dtype=torch.int64, device="cuda")
+        g4.g4n_transport_batch(ctx, items, seed, edep, cnt, h, mode=mode)
+        g4.g4n_sync(ctx)
+        hashes[mode] = h.cpu().numpy().view(np.uint64)
+        c = g4.counters_dict(cnt)
+        assert c["tracks"] == total and c["steps"] == c["geom_steps"] + c["phys_steps"]
+    bad = np.nonzero(hashes[0] != hashes[1])[0]
+    assert bad.size == 0, f"{bad.size} histories differ between modes, first global index {bad[:5]}"
+    rng = np.random.default_rng(seed)
+    starts = np.cumsum([0] + [e[1] for e in entries])
+    for gidx in np.unique(rng.integers(0, total, n_sample)):
+        k = int(np.searchsorted(starts, gidx, side="right") - 1)
+        gid, nt, tid0, src, off = entries[k]
+        r = geoms[k].transport(src, seed, 1, tid0=int(tid0 + gidx - starts[k]), threads=1)
+        assert hashes[0][gidx] == r["hashes"][0], (gidx, k)
+
+
+def test_batched_full_size_sampled(env):
+    def entries_fn(g4, ctx):
+        entries, geoms, off, tid = [], [], 0, 0
+        for sc, nt in synth.scenes.batched_scenes():
+            gid = g4.build_scene(ctx, sc)
+            entries.append((gid, nt, tid, synth.scenes.batched_source(), off))
+            geoms.append(oracle.Geometry(sc))
+            off += sc.n_volumes + 2
+            tid += nt
+        return entries, off, tid, geoms
+    _full_size_sampled(env, entries_fn, synth.scenes.CONFIG_SEEDS[2][1])
+
+
+def test_barrel_full_size_sampled(env):
+    def entries_fn(g4, ctx):
+        sc = synth.scenes.barrel_scene()
+        gid = g4.build_scene(ctx, sc)
+        n = 10_000_000
+        return [(gid, n, 0, synth.scenes.barrel_source(), 0)], sc.n_volumes + 2, n, [oracle.Geometry(sc)]
+    _full_size_sampled(env, entries_fn, synth.scenes.CONFIG_SEEDS[3][1])
