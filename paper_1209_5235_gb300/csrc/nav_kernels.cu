@@ -215,8 +215,9 @@ __device__ __forceinline__ bool disc_azimuth(uint64_t seed, int64_t tid, uint32_
     const double b = 2.0 * philox_uniform(seed, tid, stream, draw) - 1.0;
     const double r2 = a * a + b * b;
     if (r2 > 0.0 && r2 <= 1.0) {
-      c = (a * a - b * b) / r2;
-      s = 2.0 * a * b / r2;
+      const double inv = 1.0 / r2;
+      c = (a * a - b * b) * inv;
+      s = 2.0 * a * b * inv;
       return true;
     }
   }
@@ -332,23 +333,44 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
   return kStep;
 }
 
-// Kahn's rejection method for the Klein-Nishina law of eta = E / E'.
+// Kahn's rejection method for the Klein-Nishina law of eta = E / E' (three uniforms per
+// trial).  Each comparison of a uniform with its threshold is first made in FP32 and kept
+// when they differ by more than 1e-5.  All three thresholds lie in [0, 1] and their FP32
+// values (written without cancellation: 1 - (eta - 1) / alpha = 1 - 2 (1 - r2) / (1 + 2
+// alpha r2)) are within 2e-6 of the exact ones, so such a decision is the exact one; the
+// others are taken on the FP64 thresholds of the plain formulas.  The accepted trial's eta
+// and cos theta are computed in FP64.  FP64 work is left for the accepted trial and the
+// rare close calls.
 __device__ __forceinline__ bool kahn(double E, uint64_t seed, int64_t tid, uint32_t &draw, double &eta, double &cost) {
+  constexpr float kMargin = 1e-5f;
   const double al = E / kMeC2;
-  const double p1 = (1.0 + 2.0 * al) / (9.0 + 2.0 * al);
+  const float alf = (float)al;
+  const float p1f = (1.0f + 2.0f * alf) / (9.0f + 2.0f * alf);
 #pragma unroll 1
   for (int t = 0; t < 1000; ++t) {
     const double r1 = philox_uniform(seed, tid, 1, draw);
     const double r2 = philox_uniform(seed, tid, 1, draw);
     const double r3 = philox_uniform(seed, tid, 1, draw);
-    if (r1 <= p1) {
+    const float d1 = (float)r1 - p1f;
+    const bool first = fabsf(d1) > kMargin ? d1 <= 0.f : r1 <= (1.0 + 2.0 * al) / (9.0 + 2.0 * al);
+    const float r2f = (float)r2;
+    const float a2 = 2.0f * alf * r2f, den = 1.0f + a2;
+    if (first) {
+      const float d = (float)r3 - 4.0f * a2 / (den * den);
       eta = 1.0 + 2.0 * al * r2;
-      if (!(r3 <= 4.0 * (1.0 / eta - 1.0 / (eta * eta)))) continue;
+      if (fabsf(d) > kMargin) {
+        if (d > 0.f) continue;
+      } else if (!(r3 <= 4.0 * (1.0 / eta - 1.0 / (eta * eta)))) {
+        continue;
+      }
       cost = 1.0 - (eta - 1.0) / al;
     } else {
+      const float cf = 1.0f - 2.0f * (1.0f - r2f) / den;
+      const float d = (float)r3 - 0.5f * (cf * cf + den / (1.0f + 2.0f * alf));
+      if (fabsf(d) > kMargin && d > 0.f) continue;
       eta = (1.0 + 2.0 * al) / (1.0 + 2.0 * al * r2);
       cost = 1.0 - (eta - 1.0) / al;
-      if (!(r3 <= 0.5 * (cost * cost + 1.0 / eta))) continue;
+      if (!(fabsf(d) > kMargin) && !(r3 <= 0.5 * (cost * cost + 1.0 / eta))) continue;
     }
     return true;
   }
@@ -363,9 +385,9 @@ __device__ __forceinline__ V3 deflect(const V3 &u, double ct, double cph, double
   const double dx = st * cph, dy = st * sph, dz = ct;
   const double perp2 = u.x * u.x + u.y * u.y;
   if (perp2 > 0.0) {
-    const double perp = sqrt(perp2);
-    const double nx = (u.x * u.z * dx - u.y * dy) / perp + u.x * dz;
-    const double ny = (u.y * u.z * dx + u.x * dy) / perp + u.y * dz;
+    const double perp = sqrt(perp2), ip = 1.0 / perp;
+    const double nx = (u.x * u.z * dx - u.y * dy) * ip + u.x * dz;
+    const double ny = (u.y * u.z * dx + u.x * dy) * ip + u.y * dz;
     const double nz = -perp * dx + u.z * dz;
     return V3{nx, ny, nz};
   }
@@ -390,24 +412,36 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     next = kEmpty;
     act = false;
   }
+  // the free path s_phys = Y / mu (Eq. 7) races the geometric step; the division is only done
+  // when its value is needed (physics wins, or a voxel walk / FP32 bound needs the limit)
   double sphys = kInf;
   bool need_geo = false;
   V3 p{0, 0, 0}, v{0, 0, 1};
   Inv3 iv{0, 0, 0};
+  bool lazy = false;       // FP64 mode: sphys not computed, s * mu is compared with Y instead
+  double lim_geo = kInf;  // limit handed to the geometric step (an upper bound of sphys)
   if (act) {
-    sphys = t.mu > 0.0 ? t.Y / t.mu : kInf;
-    need_geo = !(sphys < t.safety);
+    const DVol &L = G.vol[t.leaf];
+    lazy = MODE == kFP64 && t.mu > 0.0 && !mc.log;
+    if (!lazy) sphys = t.mu > 0.0 ? t.Y / t.mu : kInf;
+    need_geo = lazy ? !(t.Y < t.safety * t.mu) : !(sphys < t.safety);
     if (!need_geo) {
       diag<COUNT>(cnt, G4N_C_SAFETY_SKIPS);
+      if (lazy) sphys = t.Y / t.mu;
     } else {
-      const bool aligned = G.vol[t.leaf].flags & kWorldAligned;
+      const bool aligned = L.flags & kWorldAligned;
       world_to_local(G.wxf[t.leaf], aligned, t.x, t.u, p, v);
       iv = aligned ? t.iu : inv_dir(v);
+      // the voxel walk may stop at any bound >= sphys: candidates found beyond sphys lose
+      // to the physics step all the same
+      lim_geo = !lazy ? sphys
+                : L.vox < 0 ? kInf
+                            : (double)__fdiv_ru(__double2float_ru(t.Y), __double2float_rd(t.mu));
     }
   }
   bool timeout = false;
   if (MODE == kLearned || mc.log) mc.loge = act ? (logf((float)t.E) + 4.6f) * 0.1f : 0.f;
-  const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, sphys, true, cnt,
+  const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, lim_geo, true, cnt,
                                                    &timeout, mc);
   bool geo = false;
   double s = sphys;
@@ -416,10 +450,12 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     if (timeout) flag(P.status, kStTimeout);
     if (need_geo) {
       t.safety = R.safety;
-      if (!R.physics && R.step <= sphys) {
+      if (!R.physics && (lazy ? R.step * t.mu <= t.Y : R.step <= sphys)) {
         geo = true;
         s = R.step;
         lim = R.lim;
+      } else if (lazy) {
+        s = sphys = t.Y / t.mu;
       }
     }
     ++t.steps;
