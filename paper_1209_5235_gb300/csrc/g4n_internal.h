@@ -11,6 +11,10 @@
 //                slice range [k0, k1] of the merged node it belongs to
 //   DCandList[]  (offset, count) into cand[]: daughter ids in increasing id
 //   materials    per material: energy grid, mu_compton, mu_photo (1/mm)
+//   DKeyBox[n]   world-aligned boxes: exact world-coordinate thresholds of
+//                their Inside test, as ordered integer keys of doubles
+//   skey[]       per slice of a world-aligned mother: the smallest world
+//                coordinate (as a key) that falls in that slice or above
 // All tables are small (a few MB at most) and stay L2-resident.
 #pragma once
 
@@ -27,7 +31,8 @@ constexpr int kMaxLevels = 3;
 
 enum SolidKind : int32_t { kBox = 0, kTube = 1, kOrb = 2 };
 // tube bits; world rotation is identity; placement rotation (mother -> local) is identity
-enum VolFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4, kWorldAligned = 8, kPlacedAligned = 16 };
+// kKeyBox: a world-aligned box whose Inside test is answered by its DKeyBox thresholds
+enum VolFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4, kWorldAligned = 8, kPlacedAligned = 16, kKeyBox = 32 };
 
 struct alignas(128) DVol {
   double tx, ty, tz, c, s;  // placement: local = R(theta)^T (mother - t)
@@ -46,7 +51,17 @@ struct alignas(64) DWorld {
 
 struct alignas(32) DBox32 {
   float lo[3], hi[3];       // in the mother frame
-  float pad[2];
+  int32_t keyed;            // the volume is a kKeyBox
+  float pad;
+};
+
+// Exact Inside thresholds of a world-aligned box with centre t (world frame) and
+// half-lengths h.  Per axis a, with p = fl(x_a - t_a) and g = fl(|p| - h_a) (the
+// operations of the FP64 test), and key() the order-preserving integer image of a
+// double: g > half  <=>  key(x_a) <= k[a][0] or key(x_a) >= k[a][3];
+// g >= -half  <=>  key(x_a) <= k[a][1] or key(x_a) >= k[a][2].
+struct alignas(32) DKeyBox {
+  int64_t k[3][4];
 };
 
 // FP32 copy of a volume's placement and solid size (for conservative FP32 bounds);
@@ -61,7 +76,9 @@ struct alignas(16) DVol32 {
 
 struct DVoxHdr {
   double lo, width, inv_width;
-  int32_t axis, nslices, slice_base, pad;
+  int32_t axis, nslices, slice_base;
+  int32_t keyed;            // the mother is world-aligned: skey[] holds this header's slice keys
+  float lo_wf, inv_wf;      // FP32 slice origin in world coordinates and 1/width (for a first guess)
 };
 
 struct DVoxSlice {
@@ -85,6 +102,8 @@ struct DGeom {
   const int32_t *cand;
   const double *matE, *matC, *matP;
   const int32_t *mat_off, *mat_n;
+  const DKeyBox *kbox;
+  const int64_t *skey;
   int32_t n_vol, n_mat;
   int32_t shared_grid;  // all materials tabulated on one energy grid
   int32_t pad;
@@ -119,6 +138,8 @@ struct HGeom {
   std::vector<int32_t> cand;
   std::vector<double> matE, matC, matP;
   std::vector<int32_t> mat_off, mat_n;
+  std::vector<DKeyBox> kbox;
+  std::vector<int64_t> skey;
   int32_t max_depth = 0;
   // device blob
   void *blob = nullptr;

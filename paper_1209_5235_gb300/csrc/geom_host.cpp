@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -215,7 +217,7 @@ struct VoxBuilder {
     if (!(w > 0.0)) { w = 1.0; n = 1; }
     int32_t h = (int32_t)g.hdr.size();
     int32_t base = (int32_t)g.slice.size();
-    g.hdr.push_back({region.lo[axis], w, 1.0 / w, axis, n, base, 0});
+    g.hdr.push_back({region.lo[axis], w, 1.0 / w, axis, n, base, 0, 0.f, 0.f});
     g.slice.resize(g.slice.size() + n);
     std::vector<std::vector<int32_t>> lists(n);
     for (int32_t d : D) {
@@ -250,6 +252,85 @@ struct VoxBuilder {
     return h;
   }
 };
+
+// ---------------------------------------------------------------- exact coordinate keys
+// key(x): the bit pattern of a double as a signed integer with the negative half
+// reflected, so that x < y <=> key(x) < key(y) for all non-NaN doubles (-0 < +0).
+// A predicate of a coordinate that is monotone in it is then answered exactly by
+// one integer comparison against the key of its first true (or last true) point,
+// found here by bisection over keys with the very IEEE operations the FP64 device
+// code performs.
+int64_t dkey(double x) {
+  int64_t b;
+  std::memcpy(&b, &x, 8);
+  return b ^ ((b >> 63) & INT64_C(0x7FFFFFFFFFFFFFFF));
+}
+
+double dunkey(int64_t k) {
+  const int64_t b = k ^ ((k >> 63) & INT64_C(0x7FFFFFFFFFFFFFFF));
+  double x;
+  std::memcpy(&x, &b, 8);
+  return x;
+}
+
+// Smallest key in [lo, hi] where pred (false ... true over the keys) holds; hi + 1 if none.
+template <class F>
+int64_t first_true(int64_t lo, int64_t hi, F pred) {
+  if (!pred(dunkey(hi))) return hi + 1;
+  while (lo < hi) {
+    const int64_t mid = (int64_t)((uint64_t)lo + (((uint64_t)hi - (uint64_t)lo) >> 1));
+    if (pred(dunkey(mid))) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+const int64_t kKeyMin = dkey(-DBL_MAX), kKeyMax = dkey(DBL_MAX);
+
+// The thresholds of a world-aligned box (centre t, half-lengths h) for the band half.
+DKeyBox key_box(const double *t, const double *h, double half) {
+  DKeyBox K;
+  for (int a = 0; a < 3; ++a) {
+    const double c = t[a], ha = h[a];
+    auto g = [c, ha](double x) { return std::fabs(x - c) - ha; };
+    const int64_t kc = dkey(c);
+    // low side: last key <= key(c) where the predicate holds (it holds below a threshold)
+    K.k[a][0] = first_true(kKeyMin, kc, [&](double x) { return !(g(x) > half); }) - 1;
+    K.k[a][1] = first_true(kKeyMin, kc, [&](double x) { return !(g(x) >= -half); }) - 1;
+    K.k[a][2] = first_true(kc, kKeyMax, [&](double x) { return g(x) >= -half; });
+    K.k[a][3] = first_true(kc, kKeyMax, [&](double x) { return g(x) > half; });
+  }
+  return K;
+}
+
+// Slice keys of the header tree rooted at h, for a mother whose world translation is wt.
+void key_headers(HGeom &g, int32_t h0, const double *wt) {
+  std::vector<int32_t> todo{h0};
+  std::vector<char> seen(g.hdr.size(), 0);
+  while (!todo.empty()) {
+    const int32_t h = todo.back();
+    todo.pop_back();
+    if (seen[h]) continue;
+    seen[h] = 1;
+    DVoxHdr &H = g.hdr[h];
+    const double t = wt[H.axis], lo = H.lo, iw = H.inv_width;
+    const int n = H.nslices;
+    auto slice_at = [t, lo, iw, n](double x) {
+      const double p = x - t;
+      double f = std::floor((p - lo) * iw);
+      f = std::fmin(std::fmax(f, 0.0), (double)(n - 1));
+      return (int)f;
+    };
+    H.keyed = 1;
+    H.lo_wf = (float)(t + lo);
+    H.inv_wf = (float)iw;
+    g.skey[H.slice_base] = INT64_MIN;
+    for (int k = 1; k < n; ++k)
+      g.skey[H.slice_base + k] = first_true(kKeyMin, kKeyMax, [&](double x) { return slice_at(x) >= k; });
+    for (int k = 0; k < n; ++k)
+      if (g.slice[H.slice_base + k].child < 0) todo.push_back(-g.slice[H.slice_base + k].child - 1);
+  }
+}
 
 }  // namespace
 
@@ -486,7 +567,8 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
       if ((double)box[i].lo[k] > e.lo[k]) box[i].lo[k] = std::nextafter(box[i].lo[k], -INFINITY);
       if ((double)box[i].hi[k] < e.hi[k]) box[i].hi[k] = std::nextafter(box[i].hi[k], INFINITY);
     }
-    box[i].pad[0] = box[i].pad[1] = 0.f;
+    box[i].keyed = 0;
+    box[i].pad = 0.f;
     ext[i] = e;
   }
   // --- FP32 copies for the conservative bounds
@@ -564,7 +646,7 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
   }
   if (g->clist.empty()) g->clist.push_back({0, 0});
   if (g->cand.empty()) g->cand.push_back(-1);
-  if (g->hdr.empty()) g->hdr.push_back({0, 1, 1, 0, 1, 0, 0});
+  if (g->hdr.empty()) g->hdr.push_back({0, 1, 1, 0, 1, 0, 0, 0.f, 0.f});
   if (g->slice.empty()) g->slice.push_back({0, 0, 0});
   // --- materials
   for (const HMat &m : B.mats) {
@@ -574,19 +656,37 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
     g->matC.insert(g->matC.end(), m.muC.begin(), m.muC.end());
     g->matP.insert(g->matP.end(), m.muP.begin(), m.muP.end());
   }
+  // --- exact coordinate keys: world-aligned boxes and the voxel slices of world-aligned mothers
+  g->kbox.assign(n, DKeyBox{});
+  g->skey.assign(g->slice.size(), INT64_MIN);
+  const double half = 0.5 * tol;
+  for (int i = 0; i < n; ++i) {
+    DVol &v = g->vol[i];
+    const DWorld &w = g->wxf[i];
+    const double wt[3] = {w.tx, w.ty, w.tz};
+    if (!(v.flags & kWorldAligned)) continue;
+    if (v.kind == kBox && half >= 1e-15 && v.p[0] >= 4.0 * half && v.p[1] >= 4.0 * half && v.p[2] >= 4.0 * half) {
+      g->kbox[i] = key_box(wt, v.p, half);
+      v.flags |= kKeyBox;
+      g->box[i].keyed = 1;
+    }
+    if (v.vox >= 0) key_headers(*g, v.vox, wt);
+  }
   // --- upload as one blob
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  size_t off[13], sz[13] = {g->vol.size() * sizeof(DVol), g->wxf.size() * sizeof(DWorld), g->box.size() * sizeof(DBox32),
+  constexpr int kTables = 15;
+  size_t off[kTables], sz[kTables] = {g->vol.size() * sizeof(DVol), g->wxf.size() * sizeof(DWorld), g->box.size() * sizeof(DBox32),
                             g->hdr.size() * sizeof(DVoxHdr), g->slice.size() * sizeof(DVoxSlice),
                             g->clist.size() * sizeof(DCandList), g->cand.size() * sizeof(int32_t),
                             g->matE.size() * sizeof(double), g->matC.size() * sizeof(double), g->matP.size() * sizeof(double),
                             g->mat_off.size() * sizeof(int32_t), g->mat_n.size() * sizeof(int32_t),
-                            g->v32.size() * sizeof(DVol32)};
-  const void *src[13] = {g->vol.data(), g->wxf.data(), g->box.data(), g->hdr.data(), g->slice.data(), g->clist.data(),
+                            g->v32.size() * sizeof(DVol32), g->kbox.size() * sizeof(DKeyBox),
+                            g->skey.size() * sizeof(int64_t)};
+  const void *src[kTables] = {g->vol.data(), g->wxf.data(), g->box.data(), g->hdr.data(), g->slice.data(), g->clist.data(),
                          g->cand.data(), g->matE.data(), g->matC.data(), g->matP.data(), g->mat_off.data(), g->mat_n.data(),
-                         g->v32.data()};
+                         g->v32.data(), g->kbox.data(), g->skey.data()};
   size_t total = 0;
-  for (int k = 0; k < 13; ++k) { off[k] = total; total += al(std::max<size_t>(sz[k], 8)); }
+  for (int k = 0; k < kTables; ++k) { off[k] = total; total += al(std::max<size_t>(sz[k], 8)); }
   if (ctx->device < 0) {  // host-only context: keep the host tables
     g->blob_bytes = total;
     g->dview.n_vol = n;
@@ -605,7 +705,7 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
   }
   g->blob_bytes = total;
   char *base = (char *)g->blob;
-  for (int k = 0; k < 13; ++k) {
+  for (int k = 0; k < kTables; ++k) {
     if (sz[k] && cudaMemcpy(base + off[k], src[k], sz[k], cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(g->blob);
       delete g;
@@ -626,6 +726,8 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
   d.mat_off = (const int32_t *)(base + off[10]);
   d.mat_n = (const int32_t *)(base + off[11]);
   d.v32 = (const DVol32 *)(base + off[12]);
+  d.kbox = (const DKeyBox *)(base + off[13]);
+  d.skey = (const int64_t *)(base + off[14]);
   d.n_vol = n;
   d.n_mat = (int32_t)B.mats.size();
   d.shared_grid = 1;

@@ -591,6 +591,104 @@ __device__ __forceinline__ int vox_lookup(const DGeom &G, int h, const V3 &p) {
   return 0;
 }
 
+// ---------------------------------------------------------------- exact coordinate keys
+// key(x): a double's bits as a signed integer with the negative half reflected,
+// so that x < y <=> key(x) < key(y).  The geometry carries, for world-aligned
+// boxes and for the voxel slices of world-aligned mothers, the keys at which the
+// FP64 predicates (Inside bands, slice index) change value; comparing keys then
+// gives the FP64 answer with integer instructions only.
+
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+
+// A float near x built from the high word of its bits (truncated; no FP64 instruction).
+__device__ __forceinline__ float approx_float(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned sg = hi & 0x80000000u;
+  if (e < 897) return __uint_as_float(sg);
+  if (e > 1150) return __uint_as_float(sg | 0x7f7fffffu);
+  return __uint_as_float(sg | ((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3));
+}
+
+// A world point and direction with the keys of the point and a float guess of it.
+struct WPos {
+  V3 x, u;
+  long long k[3];
+  float f[3];
+};
+
+__device__ __forceinline__ WPos make_wpos(const V3 &x, const V3 &u) {
+  WPos W;
+  W.x = x;
+  W.u = u;
+  W.k[0] = dkey(x.x);
+  W.k[1] = dkey(x.y);
+  W.k[2] = dkey(x.z);
+  W.f[0] = approx_float(x.x);
+  W.f[1] = approx_float(x.y);
+  W.f[2] = approx_float(x.z);
+  return W;
+}
+
+__device__ __forceinline__ long long kcomp(const long long *k, int a) { return a == 0 ? k[0] : (a == 1 ? k[1] : k[2]); }
+__device__ __forceinline__ float fcomp(const float *f, int a) { return a == 0 ? f[0] : (a == 1 ? f[1] : f[2]); }
+
+// box_inside on p = x - t of a kKeyBox volume d (the same answer, by its keys).
+// In the surface band of axis a the sign of p_a is known (the side of the band),
+// so p_a v_a >= 0 reduces to a sign test; only a subnormal v_a needs the product.
+__device__ __forceinline__ bool keybox_inside(const DGeom &G, int d, const WPos &W) {
+  const DKeyBox &K = G.kbox[d];
+  int near = 0;  // bit a: axis a in the band; bit a + 3: on its high side
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long k = W.k[a];
+    if (k <= K.k[a][0] || k >= K.k[a][3]) return false;
+    if (k <= K.k[a][1]) near |= 1 << a;
+    else if (k >= K.k[a][2]) near |= 9 << a;
+  }
+  if (!near) return true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!(near & (1 << a))) continue;
+    const double va = comp(W.u, a);
+    const long long vb = __double_as_longlong(va);
+    const long long mag = vb & 0x7FFFFFFFFFFFFFFFll;
+    if (mag == 0) return false;                      // p_a v_a = 0
+    if (mag < 0x0010000000000000ll) {                // subnormal v_a: the product decides
+      const DWorld &w = G.wxf[d];
+      const double pa = comp(W.x, a) - (a == 0 ? w.tx : (a == 1 ? w.ty : w.tz));
+      if (pa * va >= 0.0) return false;
+    } else if ((vb < 0) != ((near >> (a + 3)) & 1)) {
+      return false;                                  // v_a points outward
+    }
+  }
+  return true;
+}
+
+// vox_lookup for a keyed header tree (world-aligned mother), from the world point.
+__device__ __forceinline__ int vox_lookup_keys(const DGeom &G, int h, const WPos &W) {
+#pragma unroll 1
+  for (int lev = 0; lev < kMaxLevels; ++lev) {
+    const DVoxHdr H = G.hdr[h];
+    const int n = H.nslices;
+    const long long kx = kcomp(W.k, H.axis);
+    const long long *S = reinterpret_cast<const long long *>(G.skey) + H.slice_base;
+    int k = __float2int_rd((fcomp(W.f, H.axis) - H.lo_wf) * H.inv_wf);
+    k = max(0, min(k, n - 1));
+#pragma unroll 1
+    while (k > 0 && kx < __ldg(&S[k])) --k;
+#pragma unroll 1
+    while (k + 1 < n && kx >= __ldg(&S[k + 1])) ++k;
+    const DVoxSlice Sl = G.slice[H.slice_base + k];
+    if (Sl.child >= 0) return Sl.child;
+    h = -Sl.child - 1;
+  }
+  return 0;
+}
+
 // Warp-collective navigation.  Every lane of the warp must call these functions
 // together (they synchronise with __syncwarp / __any_sync over the full warp);
 // lanes with `active` false only take part in the synchronisation.  The point is
@@ -599,26 +697,36 @@ __device__ __forceinline__ int vox_lookup(const DGeom &G, int h, const V3 &p) {
 // warp meets and all those lanes run the FP64 test together.
 constexpr unsigned kFull = 0xffffffffu;
 
-// Descend from volume m (p, v in m's frame) into the first daughter, in id order,
-// that contains the point; repeat.  `blocked` is a daughter of m already known
-// not to contain the point (the volume just left).  Returns the deepest volume.
+// Descend from volume m into the first daughter, in id order, that contains the
+// point; repeat.  (p, v) is the point in m's frame when have_p is set; otherwise it
+// is derived from the world point when an FP64 test needs it.  kKeyBox daughters
+// and keyed voxel trees are answered from the world point's keys.  `blocked` is a
+// daughter of m already known not to contain the point (the volume just left).
+// Returns the deepest volume.
 template <bool COUNT>
-__device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, V3 p, V3 v, int blocked,
-                                            Counters &cnt) {
+__device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, V3 p, V3 v, bool have_p,
+                                            const WPos &W, int blocked, Counters &cnt) {
 #pragma unroll 1
   for (int lev = 0; lev < kDMax; ++lev) {
     const bool want = active && G.vol[m].vox >= 0;
     if (!__any_sync(kFull, want)) break;
     DCandList L{0, 0};
-    float px = 0.f, py = 0.f, pz = 0.f;
     if (want) {
-      L = G.clist[vox_lookup(G, G.vol[m].vox, p)];
-      px = (float)p.x;
-      py = (float)p.y;
-      pz = (float)p.z;
+      const int h = G.vol[m].vox;
+      if (G.hdr[h].keyed) {
+        L = G.clist[vox_lookup_keys(G, h, W)];
+      } else {
+        if (!have_p) {
+          world_to_local(G.wxf[m], G.vol[m].flags & kWorldAligned, W.x, W.u, p, v);
+          have_p = true;
+        }
+        L = G.clist[vox_lookup(G, h, p)];
+      }
     }
+    float px = 0.f, py = 0.f, pz = 0.f;
+    bool have_pf = false;
     int i = 0, found = -1;
-    bool searching = want;
+    bool searching = want, via_fp64 = false;
     V3 fp = p, fv = v;
 #pragma unroll 1
     while (__any_sync(kFull, searching)) {
@@ -628,8 +736,28 @@ __device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, 
         while (i < L.count) {
           const int c = __ldg(&G.cand[L.offset + i]);
           ++i;
-          if (c != blocked && box32_contains(G.box[c], px, py, pz) &&
-              !(iso_lb32(G.v32[c], px, py, pz) > (float)(2.0 * G.half))) {
+          if (c == blocked) continue;
+          const DBox32 &B = G.box[c];
+          if (B.keyed) {
+            diag<COUNT>(cnt, G4N_C_KEY_INSIDE);
+            if (keybox_inside(G, c, W)) {
+              found = c;
+              searching = false;
+              break;
+            }
+            continue;
+          }
+          if (!have_p) {
+            world_to_local(G.wxf[m], G.vol[m].flags & kWorldAligned, W.x, W.u, p, v);
+            have_p = true;
+          }
+          if (!have_pf) {
+            px = (float)p.x;
+            py = (float)p.y;
+            pz = (float)p.z;
+            have_pf = true;
+          }
+          if (box32_contains(B, px, py, pz) && !(iso_lb32(G.v32[c], px, py, pz) > (float)(2.0 * G.half))) {
             d = c;
             break;
           }
@@ -646,12 +774,14 @@ __device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, 
           found = d;
           fp = dp;
           fv = dv;
+          via_fp64 = true;
           searching = false;
         }
       }
     }
     if (want && found >= 0) {
       m = found;
+      have_p = via_fp64;
       p = fp;
       v = fv;
       blocked = -1;
@@ -666,13 +796,20 @@ __device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, 
 template <bool COUNT>
 __device__ __forceinline__ int locate_world_warp(const DGeom &G, bool active, const V3 &x, const V3 &u, Counters &cnt) {
   V3 p{0, 0, 0}, v{0, 0, 1};
-  bool in = false;
+  bool in = false, have_p = false;
+  const WPos W = make_wpos(x, u);
   if (active) {
-    world_to_local(G.wxf[0], G.vol[0].flags & kWorldAligned, x, u, p, v);
-    diag<COUNT>(cnt, G4N_C_INSIDE);
-    in = vol_inside(G.vol[0], p, v, G.half);
+    if (G.vol[0].flags & kKeyBox) {
+      diag<COUNT>(cnt, G4N_C_KEY_INSIDE);
+      in = keybox_inside(G, 0, W);
+    } else {
+      world_to_local(G.wxf[0], G.vol[0].flags & kWorldAligned, x, u, p, v);
+      have_p = true;
+      diag<COUNT>(cnt, G4N_C_INSIDE);
+      in = vol_inside(G.vol[0], p, v, G.half);
+    }
   }
-  const int leaf = descend_warp<COUNT>(G, in, 0, p, v, -1, cnt);
+  const int leaf = descend_warp<COUNT>(G, in, 0, p, v, have_p, W, -1, cnt);
   return in ? leaf : -1;
 }
 
@@ -691,18 +828,26 @@ __device__ __forceinline__ int relocate_warp(const DGeom &G, bool active, int le
     leaf = G.vol[leaf].mother;
   }
   bool up = active && leaf >= 0;
-  bool in = false;
+  bool in = false, have_p = false;
   V3 p{0, 0, 0}, v{0, 0, 1};
+  const WPos W = make_wpos(x, u);
 #pragma unroll 1
   while (__any_sync(kFull, up)) {
     if (up) {
       const DVol &L = G.vol[leaf];
-      world_to_local(G.wxf[leaf], L.flags & kWorldAligned, x, u, p, v);
       bool ok = false;
-      if (MODE != kFP64) ok = certainly_inside32(L, make_ray32(p, v), (float)(4.0 * G.half) + 1e-30f);
-      if (!ok) {
-        diag<COUNT>(cnt, G4N_C_INSIDE);
-        ok = vol_inside(L, p, v, G.half);
+      if (L.flags & kKeyBox) {
+        diag<COUNT>(cnt, G4N_C_KEY_INSIDE);
+        ok = keybox_inside(G, leaf, W);
+        have_p = false;
+      } else {
+        world_to_local(G.wxf[leaf], L.flags & kWorldAligned, x, u, p, v);
+        have_p = true;
+        if (MODE != kFP64) ok = certainly_inside32(L, make_ray32(p, v), (float)(4.0 * G.half) + 1e-30f);
+        if (!ok) {
+          diag<COUNT>(cnt, G4N_C_INSIDE);
+          ok = vol_inside(L, p, v, G.half);
+        }
       }
       if (ok) {
         in = true;
@@ -714,7 +859,7 @@ __device__ __forceinline__ int relocate_warp(const DGeom &G, bool active, int le
       }
     }
   }
-  const int out = descend_warp<COUNT>(G, in, in ? leaf : 0, p, v, blocked, cnt);
+  const int out = descend_warp<COUNT>(G, in, in ? leaf : 0, p, v, have_p, W, blocked, cnt);
   return in ? out : -1;
 }
 

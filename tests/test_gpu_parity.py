@@ -70,6 +70,59 @@ def test_locate_parity(env, name):
     assert (d_ref >= 2).sum() > 0  # the cases do reach daughters
 
 
+def _band_edge_points(sc, n, seed, half=0.5e-9):
+    """Points within a few ulps of the edges of the +-half surface band of world-level boxes
+    (and of the box centre planes' neighbours inside), on one, two or three axes at once,
+    with directions that are often axis-parallel or have zero components."""
+    rng = np.random.default_rng(seed)
+    boxes = [(np.array(pl.t, dtype=np.float64), np.array(sc.solids[pl.solid].params[:3], dtype=np.float64))
+             for pl in sc.placements[1:] if pl.mother == 0]
+    p = np.empty((n, 3))
+    v = rng.normal(size=(n, 3))
+    for q in range(n):
+        c, h = boxes[rng.integers(len(boxes))]
+        x = c + rng.uniform(-0.9, 0.9, 3) * h
+        for a in range(3):
+            if a == 0 or rng.uniform() < 0.3:
+                side = 1.0 if rng.uniform() < 0.5 else -1.0
+                delta = (half, -half, 0.0)[rng.integers(3)]
+                xa = c[a] + side * (h[a] + delta)
+                k = int(rng.integers(-3, 4))
+                for _ in range(abs(k)):
+                    xa = np.nextafter(xa, np.inf if k > 0 else -np.inf)
+                x[a] = xa
+        p[q] = x
+        for a in range(3):
+            if rng.uniform() < 0.3:
+                v[q, a] = 0.0
+        if not np.any(v[q]):
+            v[q, rng.integers(3)] = 1.0
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    return p, v
+
+
+@pytest.mark.parametrize("voxel", ["smart", "fixed", "none"])
+def test_locate_band_edges(env, voxel):
+    """Inside decisions on the edges of the surface band (x = c +- (h +- half), +-3 ulps): the
+    GPU's exact-threshold box tests and voxel lookups agree with the oracle's FP64 tests."""
+    g4, torch, ctx = env
+    spec = {"smart": VoxelSpec(mode="smart"), "fixed": VoxelSpec(mode="fixed", axes=(0, 1, 2), slices=(9, 7, 5)),
+            "none": VoxelSpec(mode="none")}[voxel]
+    sc = synth.scenes.tiny_scene(seed=123, n_boxes=40, voxel=spec)
+    og = oracle.Geometry(sc)
+    gid = g4.build_scene(ctx, sc)
+    p, v = _band_edge_points(sc, 30000, seed=5)
+    d_ref, path_ref = og.locate_many(p, v)
+    d, path = g4.g4n_locate(ctx, gid, to_soa(p, torch), to_soa(v, torch))
+    g4.g4n_sync(ctx)
+    d = d.cpu().numpy()
+    path = path.cpu().numpy().T
+    bad = np.nonzero((d != d_ref) | np.any(path != path_ref, axis=1))[0]
+    assert bad.size == 0, f"{bad.size} mismatches, first: {p[bad[0]]!r} {v[bad[0]]!r} gpu {path[bad[0]]} ref {path_ref[bad[0]]}"
+    # both outcomes of the band rule occur
+    assert 0 < (d_ref == 2).sum() < len(d_ref)
+
+
 MODES = [0, 1, 2]   # G4N_MODE_FP64, G4N_MODE_FP32_RECHECK, G4N_MODE_LEARNED
 
 
