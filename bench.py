@@ -120,7 +120,17 @@ WORKLOADS = {
               "voxels; 10^7 gamma log-uniform 0.02-20 MeV isotropic from points on the axis",
     "barrel_learned": "barrel scene with the learned candidate proposal (MLP trained on steps logged by the plain "
                       "navigator); 10^7 gamma",
+    "spheres_regular": "Spheres (Sec. 3.4): 8000 aluminium balls r 100 mm on a 250 mm grid in a 5 m vacuum cube, smart "
+                       "voxels, mu = rho x 0.06146 cm^2/g; 10^5 rays from the centre towards a 400 x 250 grid on the +z "
+                       "face, Y = 1; free path T of Algorithm 1 per ray (the raytraced image)",
+    "spheres_random": "Spheres (Sec. 3.4) as above; 10^5 rays from the centre, isotropic directions, Y ~ Exp(1); free "
+                      "path T of Algorithm 1 per ray",
 }
+
+# The paper's Table 1 times for these inputs (GTX 470 / 2 x 6-core Opteron 2427; 10^5 particles, compute phase only).
+PAPER_SPHERES_MS = {"spheres_regular": {"gpu_gtx470": 33.0, "cpu_1_thread": 442.0, "cpu_12_threads": 54.0},
+                    "spheres_random": {"gpu_gtx470": 114.0, "cpu_1_thread": 458.0, "cpu_12_threads": 56.0}}
+FREE_PATH_METRIC = "free paths (Algorithm 1) per second on 1 GB300, navigation steps/s beside it"
 
 
 def parse_voxel(spec: str):
@@ -424,6 +434,146 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_free_path(args):
+    """The Spheres benchmark: Algorithm 1 free paths of 10^5 rays (g4n_free_path), compute phase timed."""
+    import torch
+    import paper_1209_5235_gb300 as g4
+    from paper_1209_5235_gb300 import build as b
+    import synth
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    b.build()
+    ctx = g4.g4n_create(local)
+    sc = synth.scenes.spheres_scene()
+    gid = g4.build_scene(ctx, sc)
+    kind = args.workload.split("_")[1]
+    p, v, Y = synth.scenes.spheres_rays(kind, seed=0x7A0C0005 + rank)
+    n, E = len(Y), synth.scenes.SPHERES_ENERGY
+    pos = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float64, device="cuda")
+    dirs = torch.tensor(np.ascontiguousarray(v.T), dtype=torch.float64, device="cuda")
+    Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    T = torch.empty(n, dtype=torch.float64, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    code = {"fp64": g4.G4N_MODE_FP64, "fp32_recheck": g4.G4N_MODE_FP32_RECHECK}
+    modes = ["fp64", "fp32_recheck"] if args.mode == "auto" else [args.mode]
+    ref = None
+    matched = True
+    for m in modes:
+        g4.g4n_free_path(ctx, gid, pos, dirs, Yd, E, mode=code[m], out_T=T, out_steps=st, stream=stream)
+        g4.g4n_sync(ctx, stream)
+        if ref is None:
+            ref = T.clone()
+        else:
+            matched = matched and bool(torch.equal(torch.nan_to_num(T, posinf=-1.0), torch.nan_to_num(ref, posinf=-1.0)))
+    results = {}
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        for m in modes:
+            for k in range(args.warmup):
+                g4.g4n_free_path(ctx, gid, pos, dirs, Yd, E, mode=code[m], out_T=T, out_steps=st, stream=stream)
+            g4.g4n_sync(ctx, stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                g4.g4n_free_path(ctx, gid, pos, dirs, Yd, E, mode=code[m], out_T=T, out_steps=st, stream=stream)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            g4.g4n_sync(ctx, stream)
+            ms = [a.elapsed_time(c) for a, c in ev]
+            t_dev = sum(ms) / 1e3
+            if dist:
+                tt = torch.tensor([t_dev], device="cuda")
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+                t_dev = float(tt.item())
+            segs = int(st.to(torch.int64).sum().item())
+            results[m] = {"rays_per_s": world * n * args.steps / t_dev, "nav_steps_per_s": world * segs * args.steps / t_dev,
+                          "ms_per_step": 1e3 * t_dev / args.steps, "ms_launch_mean": float(np.mean(ms)),
+                          "steps_per_ray": segs / n}
+    chosen = max(results, key=lambda k: results[k]["rays_per_s"]) if matched else "fp64"
+    R = results[chosen]
+    cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
+    g4.g4n_free_path(ctx, gid, pos, dirs, Yd, E, mode=code[chosen], counters=cnt, diagnostics=True, out_T=T,
+                     out_steps=st, stream=stream)
+    g4.g4n_sync(ctx, stream)
+    cdiag = g4.counters_dict(cnt)
+    escaped = int(torch.isinf(T).sum().item())
+    # end to end through the public API: pinned host inputs copied in, T copied out, every step
+    hp = torch.from_numpy(np.ascontiguousarray(p.T)).pin_memory()
+    hv = torch.from_numpy(np.ascontiguousarray(v.T)).pin_memory()
+    hY = torch.from_numpy(Y.copy()).pin_memory()
+    hT = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_t = 0.0
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pos.copy_(hp, non_blocking=True)
+        dirs.copy_(hv, non_blocking=True)
+        Yd.copy_(hY, non_blocking=True)
+        g4.g4n_free_path(ctx, gid, pos, dirs, Yd, E, mode=code[chosen], out_T=T, out_steps=st, stream=stream)
+        hT.copy_(T, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_t += time.perf_counter() - t0
+    g4.g4n_sync(ctx, stream)
+    g4.g4n_destroy(ctx)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    flops = (FLOPS["steps"] * cdiag["steps"] + FLOPS["dist_out"] * cdiag["dist_out"] + FLOPS["cand_orb"] *
+             cdiag["cand_orb"] + FLOPS["cand_box"] * cdiag["cand_box"] + FLOPS["inside"] * (cdiag["inside"] + cdiag["key_inside"])
+             + FLOPS["vox_nodes"] * cdiag["vox_nodes"])
+    t_launch = R["ms_launch_mean"] / 1e3
+    paper = PAPER_SPHERES_MS[args.workload]
+    line = {
+        "metric": FREE_PATH_METRIC, "value": R["rays_per_s"], "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": R["rays_per_s"] / world / (1e5 / (paper["gpu_gtx470"] / 1e3)), "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "rays_per_gpu": n, "mode": chosen,
+                   "l2": "flushed between timed steps (256 MB write)", "energy_mev": E},
+        "nav_steps_per_s": R["nav_steps_per_s"], "steps_per_ray": R["steps_per_ray"], "escaped": escaped,
+        "modes": results, "matched_results": matched, "gpu_launches": args.steps,
+        "paper_table1_ms": paper,
+        "vs_baseline_note": "rays/s per GPU over the paper's GTX 470 rays/s (10^5 rays / its time): another machine, context",
+        "roofline": {"bound": "alu", "achieved": flops / t_launch / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops / t_launch / 1e12 / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_free_path",
+                     "flops_per_launch": flops},
+        "clocks": clk.summary(),
+        "e2e": {"value": world * n * args.steps / e2e_t, "unit": "rays/s", "h2d_bytes_per_step": int(7 * 8 * n),
+                "d2h_bytes_per_step": int(8 * n)},
+        "counters": {k: cdiag[k] for k in ("tracks", "steps", "geom_steps", "phys_steps", "escaped", "dist_out",
+                                           "cand_orb", "key_inside", "inside", "vox_nodes")},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        og = oracle.Geometry(sc)
+        t0 = time.perf_counter()
+        _, _, used = og.free_path_many(p, v, E, Y)
+        dt_all = time.perf_counter() - t0
+        m1 = 2000
+        t0 = time.perf_counter()
+        og.free_path_many(p[:m1], v[:m1], E, Y[:m1], threads=1)
+        dt_1 = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n / dt_all, "unit": "rays/s", "cores": int(used), "kind": "oracle",
+                                "single_thread_rays_per_s": m1 / dt_1,
+                                "sample": f"all {n} rays on {used} threads; the first {m1} rays on 1 thread; "
+                                          f"brute-force FP64 oracle (every step tests all 8000 balls)"}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,7 +589,8 @@ def main():
     ap.add_argument("--mode", default="auto", choices=["auto", "fp64", "fp32_recheck"])
     ap.add_argument("--voxel", default="smart")
     ap.add_argument("--workload", default="calorimeter",
-                    choices=["calorimeter", "tiny", "batched", "barrel", "barrel_learned"])
+                    choices=["calorimeter", "tiny", "batched", "barrel", "barrel_learned", "spheres_regular",
+                             "spheres_random"])
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tune-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -448,6 +599,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("spheres_"):
+        run_free_path(args)
     else:
         run_gpu(args)
 

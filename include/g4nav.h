@@ -178,6 +178,25 @@ int g4n_compute_step(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, c
                      const int32_t *depth, const int32_t *path, const double *proposed, double *out_step,
                      double *out_safety, int32_t *out_limiter, int32_t mode, g4n_stream stream);
 
+/* Free path of Algorithm 1 (Sec. 3.1, Eqs. 6-7; the benchmark of Sec. 3.4, Algorithm 2 phase 5) for n rays.
+ * Each ray starts at x0 along the unit direction omega.  The attenuation of a volume is its material's linear
+ * coefficient (mu_compton + mu_photo, 1/mm) at `energy` (MeV), constant along a segment.  With t_j the boundary
+ * crossings along the ray (t_0 = 0) and S_j the optical depth accumulated up to t_j, the result is
+ * T = t_{j-1} + (Y - S_{j-1}) / mu_j for the first segment j with mu_j > 0 and S_{j-1} + mu_j (t_j - t_{j-1}) >= Y.
+ * T = +inf if the ray leaves the world first or starts outside it; T = 0 if Y <= 0.  The ray only moves along its
+ * line (no zero-step push); positions are x0 + t omega.
+ *   pos, dir: 3 x n SoA device doubles; Y: n device doubles; out_T: n device doubles.
+ *   out_steps: n device int32 (segments walked), nullable.
+ *   out_counters: G4N_N_COUNTERS device uint64, accumulated (not cleared), nullable: G4N_C_TRACKS rays started,
+ *     G4N_C_STEPS segments, G4N_C_GEOM_STEPS boundary crossings, G4N_C_PHYS_STEPS rays whose T is finite and > 0,
+ *     G4N_C_ESCAPED rays that left the world; the diagnostic counters too with G4N_FLAG_DIAGNOSTICS in flags.
+ *   mode: as g4n_compute_step.  max_steps: per-ray segment cap (0 = 10^6); a ray reaching it gets T = NaN and
+ *   g4n_sync reports G4N_ERR_STEP_LIMIT.  Non-unit or non-finite directions give T = NaN and G4N_ERR_ARG at g4n_sync.
+ * Rays are handed out to the warps of a persistent grid from one device queue.  Asynchronous on `stream`. */
+int g4n_free_path(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, const double *dir, const double *Y,
+                  double energy, double *out_T, int32_t *out_steps, uint64_t *out_counters, int32_t mode,
+                  int64_t max_steps, int32_t flags, g4n_stream stream);
+
 /* ---------------------------------------------------------------- transport (device) */
 
 /* Per-track source.  Every random quantity is drawn from Philox4x32-10 keyed by the 64-bit seed

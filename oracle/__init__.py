@@ -78,6 +78,7 @@ def lib():
             "o_source_sample": (None, [vp, u64, i64, i64, vp, vp, vp]),
             "o_transport": (i, [i, vp, u64, i64, i64, d, i64, i, vp, vp, vp, vp, i]),
             "o_free_path": (d, [i, vp, vp, d, d, vp]),
+            "o_free_path_many": (i, [i, i64, vp, vp, d, vp, vp, vp, i]),
             "o_locate_many": (None, [i, i64, vp, vp, vp, vp]),
             "o_transport_trace": (i, [i, vp, u64, i64, d, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
             "o_compute_step_many": (None, [i, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -209,6 +210,15 @@ class Geometry:
         ns = np.zeros(1, dtype=np.int64)
         T = lib().o_free_path(self.gid, _p(_f64(p)), _p(_f64(v)), float(E), float(Y), _p(ns))
         return T, int(ns[0])
+
+    def free_path_many(self, p, v, E: float, Y, threads: int = 0):
+        """Algorithm 1 free paths of n rays (p, v: (n, 3)); returns (T (n,), steps (n,), threads used)."""
+        p, v, Y = _f64(p), _f64(v), _f64(Y)
+        n = p.shape[0]
+        T = np.empty(n)
+        ns = np.zeros(n, dtype=np.int64)
+        used = lib().o_free_path_many(self.gid, n, _p(p), _p(v), float(E), _p(Y), _p(T), _p(ns), int(threads))
+        return T, ns, used
 
     def transport(self, source, seed: int, n: int, tid0: int = 0, cutoff: float = 0.01, max_steps: int = 1_000_000,
                   n_batches: int = 100, want_hash: bool = True, want_len: bool = True, threads: int = 0):

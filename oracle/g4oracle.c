@@ -1002,6 +1002,18 @@ double o_free_path(int gi, const double *p, const double *v, double E, double Y,
   return O_INF;
 }
 
+/* o_free_path for n rays (pos, dir: n x 3 row-major), OpenMP over rays; returns the threads used. */
+int o_free_path_many(int gi, int64_t n, const double *pos, const double *dir, double E, const double *Y, double *T,
+                     int64_t *n_steps, int nthreads) {
+  int used = 1;
+#ifdef _OPENMP
+  used = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(used)
+#endif
+  for (int64_t i = 0; i < n; ++i) T[i] = o_free_path(gi, pos + 3 * i, dir + 3 * i, E, Y[i], n_steps ? n_steps + i : NULL);
+  return used;
+}
+
 /* ------------------------------------------------------------------ batch helpers for the tests */
 
 /* pos, dir: n x 3 row-major; depth: n; path: n x O_DMAX row-major. */

@@ -39,7 +39,7 @@ PARITY_COUNTERS = ["tracks", "steps", "geom_steps", "phys_steps", "photo", "comp
 
 EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_scale", "g4n_sync", "g4n_material_add",
             "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_place", "g4n_voxelize", "g4n_geom_finalize",
-            "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_transport_batch", "g4n_transport_batch_host",
+            "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_free_path", "g4n_transport_batch", "g4n_transport_batch_host",
             "g4n_transport_batch_noalloc", "g4n_mlp_load", "g4n_mlp_get", "g4n_mlp_log", "g4n_mlp_train",
             "g4n_mlp_grad", "g4n_mlp_predict", "g4n_graph_create", "g4n_graph_launch", "g4n_graph_destroy"]
 
@@ -108,6 +108,7 @@ def load():
         "g4n_geom_finalize": [vp, vp], "g4n_geom_info": [vp, i32, vp],
         "g4n_locate": [vp, i32, i64, vp, vp, vp, vp, vp],
         "g4n_compute_step": [vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp],
+        "g4n_free_path": [vp, i32, i64, vp, vp, vp, d, vp, vp, vp, i32, i64, i32, vp],
         "g4n_transport_batch": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
         "g4n_transport_batch_host": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
         "g4n_transport_batch_noalloc": [vp, ctypes.POINTER(g4n_batch_desc), vp, vp, vp, vp, vp],
@@ -301,6 +302,24 @@ def g4n_compute_step(ctx, geom: int, pos, dir, depth, path, proposed=None, mode:
                                         _dptr(step, torch.float64, "step"), _dptr(saf, torch.float64, "safety"),
                                         _dptr(lim, torch.int32, "limiter"), int(mode), _stream(stream)))
     return step, saf, lim
+
+
+def g4n_free_path(ctx, geom: int, pos, dir, Y, energy: float, mode: int = G4N_MODE_FP64, counters=None,
+                  max_steps: int = 0, diagnostics: bool = False, want_steps: bool = True, out_T=None, out_steps=None,
+                  stream=None):
+    """Free path T of Algorithm 1 per ray.  Returns (T (n,) f64, steps (n,) int32 or None); `counters`
+    (G4N_N_COUNTERS int64 device tensor) is accumulated if given."""
+    import torch
+    n = pos.shape[1]
+    T = out_T if out_T is not None else torch.empty(n, dtype=torch.float64, device=pos.device)
+    st = out_steps if out_steps is not None else (torch.empty(n, dtype=torch.int32, device=pos.device) if want_steps
+                                                  else None)
+    _check(ctx, load().g4n_free_path(ctx, int(geom), int(n), _dptr(pos, torch.float64, "pos"),
+                                     _dptr(dir, torch.float64, "dir"), _dptr(Y, torch.float64, "Y"), float(energy),
+                                     _dptr(T, torch.float64, "T"), _dptr(st, torch.int32, "steps"),
+                                     _dptr(counters, torch.int64, "counters"), int(mode), int(max_steps),
+                                     G4N_FLAG_DIAGNOSTICS if diagnostics else 0, _stream(stream)))
+    return T, st
 
 
 def make_items(entries) -> "ctypes.Array":

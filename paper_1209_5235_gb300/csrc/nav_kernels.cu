@@ -626,6 +626,166 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
   }
 }
 
+// ---------------------------------------------------------------- free path (Algorithm 1)
+
+struct FParams {
+  const DGeom *geoms;
+  int gid;
+  int64_t n;
+  const double *pos, *dir, *Y;
+  double energy;
+  double *out_T;
+  int32_t *out_steps;
+  unsigned long long *counters;
+  unsigned long long *q_head;
+  uint32_t *status;
+  int64_t max_steps;
+  const mlp::SmemWeights *mlp_w;
+};
+
+// One ray per lane: the segment loop of Algorithm 1 with the optical depth S
+// accumulated per segment.  Idle lanes take the next rays from the device
+// queue (one atomic per warp); navigation is warp-collective as in transport.
+template <int MODE, bool COUNT>
+__global__ void __launch_bounds__(128, 3) k_free_path(const FParams P) {
+  const DGeom &G = P.geoms[P.gid];
+  Counters cnt;
+#pragma unroll
+  for (int k = 0; k < G4N_N_COUNTERS; ++k) cnt.c[k] = 0;
+  const unsigned lane = threadIdx.x & 31u;
+  MlpCtx mc{nullptr, nullptr, nullptr, 0.f};
+  if (MODE == kLearned) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    mlp::SmemWeights *sw = reinterpret_cast<mlp::SmemWeights *>(smem);
+    mlp::load_weights(*sw, P.mlp_w);
+    __syncthreads();
+    mc.w = sw;
+    mc.scratch = reinterpret_cast<mlp::SmemWarp *>(smem + sizeof(mlp::SmemWeights)) + (threadIdx.x >> 5);
+    mc.loge = (logf((float)P.energy) + 4.6f) * 0.1f;
+  }
+  int64_t ray = -1, steps = 0;
+  V3 x0{0, 0, 0}, u{0, 0, 1}, x{0, 0, 0};
+  Inv3 iu{0, 0, 0};
+  double t = 0.0, S = 0.0, Y = 0.0, mu = 0.0;
+  int leaf = 0;
+  bool active = false, drained = false;
+#pragma unroll 1
+  for (;;) {
+    const unsigned idle = __ballot_sync(kFull, !active);
+    if (idle && !drained) {
+      const int leader = __ffs(idle) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(P.q_head, (unsigned long long)__popc(idle));
+      base = __shfl_sync(kFull, base, leader);
+      if (base + __popc(idle) >= (unsigned long long)P.n) drained = true;
+      const int64_t g = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
+      bool take = !active && g < P.n;
+      if (take) {
+        ray = g;
+        x0 = V3{P.pos[g], P.pos[P.n + g], P.pos[2 * P.n + g]};
+        u = V3{P.dir[g], P.dir[P.n + g], P.dir[2 * P.n + g]};
+        Y = P.Y[g];
+        steps = 0;
+        if (bad_dir(u) || !isfinite(x0.x + x0.y + x0.z)) {
+          flag(P.status, kStBadInput);
+          P.out_T[g] = nan("");
+          if (P.out_steps) P.out_steps[g] = 0;
+          take = false;
+        } else {
+          cnt.c[G4N_C_TRACKS]++;
+        }
+      }
+      const int l0 = locate_world_warp<COUNT>(G, take, x0, u, cnt);
+      if (take) {
+        if (!(Y > 0.0) || l0 < 0) {
+          // Y <= 0: the interaction is at the start point; outside the world: no segment at all
+          P.out_T[ray] = !(Y > 0.0) ? 0.0 : kInf;
+          if (P.out_steps) P.out_steps[ray] = 0;
+          if (Y > 0.0) cnt.c[G4N_C_ESCAPED]++;
+        } else {
+          leaf = l0;
+          x = x0;
+          iu = inv_dir(u);
+          t = 0.0;
+          S = 0.0;
+          double mupe;
+          mu_lookup(G, G.vol[leaf].mat, P.energy, mu, mupe);
+          active = true;
+        }
+      }
+    }
+    if (drained && !__any_sync(kFull, active)) break;
+    // one segment: the geometric step from x inside `leaf`
+    V3 p{0, 0, 0}, v{0, 0, 1};
+    Inv3 iv{0, 0, 0};
+    if (active) {
+      const bool aligned = G.vol[leaf].flags & kWorldAligned;
+      world_to_local(G.wxf[leaf], aligned, x, u, p, v);
+      iv = aligned ? iu : inv_dir(v);
+    }
+    bool timeout = false;
+    const StepResult R = geom_step_warp<MODE, COUNT>(G, active, active ? leaf : 0, p, v, iv, kInf, false, cnt, &timeout,
+                                                     mc);
+    bool cross = false;
+    double s = 0.0;
+    if (active) {
+      if (timeout) flag(P.status, kStTimeout);
+      s = R.step;
+      ++steps;
+      cnt.c[G4N_C_STEPS]++;
+      if (mu > 0.0 && S + s * mu >= Y) {
+        P.out_T[ray] = t + (Y - S) / mu;
+        if (P.out_steps) P.out_steps[ray] = (int32_t)steps;
+        cnt.c[G4N_C_PHYS_STEPS]++;
+        active = false;
+      } else if (steps >= P.max_steps) {
+        flag(P.status, kStStepLimit);
+        cnt.c[G4N_C_STEP_LIMIT]++;
+        P.out_T[ray] = nan("");
+        if (P.out_steps) P.out_steps[ray] = (int32_t)steps;
+        active = false;
+      } else {
+        S += s * mu;
+        t += s;
+        x = V3{x0.x + t * u.x, x0.y + t * u.y, x0.z + t * u.z};
+        cnt.c[G4N_C_GEOM_STEPS]++;
+        cross = true;
+      }
+    }
+    const int nl = relocate_warp<MODE, COUNT>(G, cross, cross ? leaf : 0, x, u,
+                                              cross && R.lim == G4N_LIM_MOTHER && s > 0.0, cnt);
+    if (cross) {
+      if (nl < 0) {
+        P.out_T[ray] = kInf;
+        if (P.out_steps) P.out_steps[ray] = (int32_t)steps;
+        cnt.c[G4N_C_ESCAPED]++;
+        active = false;
+      } else {
+        leaf = nl;
+        double mupe;
+        mu_lookup(G, G.vol[leaf].mat, P.energy, mu, mupe);
+      }
+    }
+  }
+  if (P.counters) {
+#pragma unroll
+    for (int k = 0; k < G4N_N_COUNTERS; ++k) {
+      unsigned long long c = cnt.c[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+      if (lane == 0 && c) atomicAdd(&P.counters[k], c);
+    }
+  }
+}
+
+using FreePathKernel = void (*)(const FParams);
+
+FreePathKernel free_path_kernel(int mode, bool count) {
+  if (mode == G4N_MODE_FP64) return count ? k_free_path<kFP64, true> : k_free_path<kFP64, false>;
+  if (mode == G4N_MODE_FP32_RECHECK) return count ? k_free_path<kFP32, true> : k_free_path<kFP32, false>;
+  return count ? k_free_path<kLearned, true> : k_free_path<kLearned, false>;
+}
+
 using TransportKernel = void (*)(const TParams);
 
 TransportKernel transport_kernel(int mode, bool count) {
@@ -915,6 +1075,53 @@ int g4n_mlp_log(g4n_ctx *ctx, const g4n_batch_desc *b, float *feat, int32_t *lab
   if (rc) return rc;
   *out_count = (int64_t)std::min<unsigned long long>(c, (unsigned long long)capacity);
   return G4N_OK;
+}
+
+int g4n_free_path(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, const double *dir, const double *Y,
+                  double energy, double *out_T, int32_t *out_steps, uint64_t *out_counters, int32_t mode,
+                  int64_t max_steps, int32_t flags, g4n_stream stream) {
+  int rc = check_geom(ctx, geom);
+  if (rc) return rc;
+  if (n < 0) return g4n_fail(ctx, G4N_ERR_ARG, "free_path: n < 0");
+  if (mode != G4N_MODE_FP64 && mode != G4N_MODE_FP32_RECHECK && mode != G4N_MODE_LEARNED)
+    return g4n_fail(ctx, G4N_ERR_ARG, "free_path: unknown mode");
+  if (mode == G4N_MODE_LEARNED && !g4n_mlp_image(ctx))
+    return g4n_fail(ctx, G4N_ERR_STATE, "free_path: learned mode needs MLP weights");
+  if (!(energy > 0.0) || !std::isfinite(energy)) return g4n_fail(ctx, G4N_ERR_ARG, "free_path: energy must be > 0");
+  if (max_steps < 0) return g4n_fail(ctx, G4N_ERR_ARG, "free_path: max_steps < 0");
+  if (n == 0) return G4N_OK;
+  if (!pos || !dir || !Y || !out_T) return g4n_fail(ctx, G4N_ERR_ARG, "free_path: null array");
+  if ((rc = ensure_ws(ctx, 0))) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace *ws = (Workspace *)ctx->ws;
+  if (cudaMemsetAsync(&ws->q_head, 0, sizeof(unsigned long long), st) != cudaSuccess)
+    return g4n_fail(ctx, G4N_ERR_CUDA, "free_path: queue reset failed");
+  FParams P;
+  P.geoms = ctx->d_geoms;
+  P.gid = geom;
+  P.n = n;
+  P.pos = pos;
+  P.dir = dir;
+  P.Y = Y;
+  P.energy = energy;
+  P.out_T = out_T;
+  P.out_steps = out_steps;
+  P.counters = reinterpret_cast<unsigned long long *>(out_counters);
+  P.q_head = &ws->q_head;
+  P.status = &ws->status;
+  P.max_steps = max_steps > 0 ? max_steps : 1000000;
+  P.mlp_w = g4n_mlp_image(ctx);
+  const FreePathKernel kern = free_path_kernel(mode, (flags & G4N_FLAG_DIAGNOSTICS) && out_counters);
+  const int block = 128;
+  const size_t smem = mlp_smem_bytes(mode, block);
+  if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+  int64_t grid = (int64_t)ctx->sm_count * std::max(per_sm, 1);
+  grid = std::max<int64_t>(1, std::min<int64_t>(grid, (n + block - 1) / block));
+  kern<<<(int)grid, block, smem, st>>>(P);
+  return launch_error(ctx, "free_path launch");
 }
 
 int g4n_sync(g4n_ctx *ctx, g4n_stream stream) {

@@ -332,6 +332,35 @@ def spheres_scene(n_side: int = 20, radius: float = 100.0, pitch: float = 250.0,
     return Scene("spheres", mats, solids, places, VoxelSpec(mode="smart"))
 
 
+SPHERES_GRID = (400, 250)      # Regular target grid on the +z face (pixels along x, along y)
+SPHERES_ENERGY = 1.0           # MeV: every particle of the Spheres benchmark has this energy
+
+
+def spheres_rays(kind: str, n: int = 100_000, seed: int = 0x7A0C0005, half: float = 2500.0):
+    """Inputs (x0, omega, Y) of the Spheres benchmark (Sec. 3.4, Algorithm 2 phases 2-3), all rays from the
+    centre of the geometry.  'regular': towards the centres of a 400 x 250 pixel grid on the +z face,
+    ray i*250 + j aims at x = -half + (i + 1/2) 2 half / 400, y = -half + (j + 1/2) 2 half / 250 (column-major
+    pixel order), Y = 1 for every ray.  'random': directions uniform on the unit sphere, Y ~ Exp(1).
+    Returns pos (n, 3), dir (n, 3), Y (n,) as float64 arrays."""
+    if kind == "regular":
+        nx, ny = SPHERES_GRID
+        if n != nx * ny:
+            raise ValueError("the regular grid has 400 x 250 rays")
+        i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+        tgt = np.stack([-half + (i.ravel() + 0.5) * (2 * half / nx), -half + (j.ravel() + 0.5) * (2 * half / ny),
+                        np.full(n, half)], axis=1)
+        d = tgt / np.linalg.norm(tgt, axis=1)[:, None]
+        Y = np.ones(n)
+    elif kind == "random":
+        rng = np.random.default_rng(seed)
+        d = rng.normal(size=(n, 3))
+        d /= np.linalg.norm(d, axis=1)[:, None]
+        Y = rng.exponential(1.0, size=n)
+    else:
+        raise ValueError(kind)
+    return np.zeros((n, 3)), np.ascontiguousarray(d), Y
+
+
 def slab_scene(thickness: float, material: Material, half_xy: float = 1.0e5) -> Scene:
     """One slab (z in [0, thickness]) of ``material`` inside a vacuum world: the Eq. 2-3 attenuation setup."""
     mats = [vacuum(material.energies), material]
