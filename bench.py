@@ -40,9 +40,11 @@ WORKLOAD = ("sampling calorimeter: 50 alternating 5 mm lead-like / 10 mm scintil
 
 # Algorithmic FP64 work per counted event (flops: add/sub/mul/compare/min/max = 1, fma = 2, div/sqrt = 1).
 # An Inside test of a world-aligned box answered by exact coordinate keys (key_inside) counts as the FP64
-# box test whose answer it gives: the work the method defines, not the instructions the kernel executes.
+# box test whose answer it gives, and a relocation answered by a face record (face_reloc) as the two Inside
+# tests (mother, entered volume) the method needs at least: the work the method defines, not the
+# instructions the kernel executes.
 FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube": 90, "inside": 24,
-         "key_inside": 24, "vox_nodes": 14, "phys_steps": 60}
+         "key_inside": 24, "face_reloc": 48, "vox_nodes": 14, "phys_steps": 60}
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
 
 
@@ -422,8 +424,8 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
         "counters": {k: cdiag[k] for k in ("steps", "geom_steps", "phys_steps", "safety_skips", "cand_box",
-                                           "cand_tube", "cand_orb", "inside", "vox_nodes", "dist_out", "rechecks",
-                                           "proposals", "pruned")},
+                                           "cand_tube", "cand_orb", "inside", "key_inside", "face_reloc", "vox_nodes",
+                                           "dist_out", "rechecks", "proposals", "pruned")},
     }
     if getattr(args, "train_losses", None):
         line["learned"] = {"train_samples": args.train_samples, "epoch_losses": args.train_losses}
@@ -533,7 +535,7 @@ def run_free_path(args):
         return
     flops = (FLOPS["steps"] * cdiag["steps"] + FLOPS["dist_out"] * cdiag["dist_out"] + FLOPS["cand_orb"] *
              cdiag["cand_orb"] + FLOPS["cand_box"] * cdiag["cand_box"] + FLOPS["inside"] * (cdiag["inside"] + cdiag["key_inside"])
-             + FLOPS["vox_nodes"] * cdiag["vox_nodes"])
+             + FLOPS["face_reloc"] * cdiag["face_reloc"] + FLOPS["vox_nodes"] * cdiag["vox_nodes"])
     t_launch = R["ms_launch_mean"] / 1e3
     paper = PAPER_SPHERES_MS[args.workload]
     line = {

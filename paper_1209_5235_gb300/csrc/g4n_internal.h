@@ -15,6 +15,7 @@
 //                their Inside test, as ordered integer keys of doubles
 //   skey[]       per slice of a world-aligned mother: the smallest world
 //                coordinate (as a key) that falls in that slice or above
+//   DFace[]      6 per kKeyBox volume: relocation results across its faces
 // All tables are small (a few MB at most) and stay L2-resident.
 #pragma once
 
@@ -40,7 +41,8 @@ struct alignas(128) DVol {
   int32_t kind, flags, mother, mat;
   int32_t vox;              // root voxel header of this volume's daughters (-1: no daughters)
   int32_t depth;            // 1 for the world
-  int32_t n_dau, pad;
+  int32_t n_dau;
+  int32_t face;             // first of the volume's 6 DFace records (-1: none)
 };
 static_assert(sizeof(DVol) == 128, "DVol must be 128 bytes");
 
@@ -74,6 +76,20 @@ struct alignas(16) DVol32 {
   float pad;
 };
 
+// Relocation across one face of a kKeyBox volume, decided on the host for a whole
+// region: the face's rectangle shrunk in-plane by a margin and thickened by tol/8
+// along the normal, as world-coordinate key intervals [lo, hi] per axis.  For
+// every point of the region moving outward through the face (normal direction
+// component of that sign, not subnormal), the relocation after leaving the volume
+// (up through the mothers, down through the daughters in id order, the Inside tests
+// on their keys) ends in `leaf` (-1: left the world).  ok = 0: not decided.
+// Faces are numbered 2 axis + (outward direction component > 0).
+struct alignas(64) DFace {
+  int64_t k[3][2];
+  int32_t leaf, ok;
+  int32_t pad[2];
+};
+
 struct DVoxHdr {
   double lo, width, inv_width;
   int32_t axis, nslices, slice_base;
@@ -104,6 +120,7 @@ struct DGeom {
   const int32_t *mat_off, *mat_n;
   const DKeyBox *kbox;
   const int64_t *skey;
+  const DFace *face;
   int32_t n_vol, n_mat;
   int32_t shared_grid;  // all materials tabulated on one energy grid
   int32_t pad;
@@ -140,6 +157,7 @@ struct HGeom {
   std::vector<int32_t> mat_off, mat_n;
   std::vector<DKeyBox> kbox;
   std::vector<int64_t> skey;
+  std::vector<DFace> face;
   int32_t max_depth = 0;
   // device blob
   void *blob = nullptr;

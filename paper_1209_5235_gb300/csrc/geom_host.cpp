@@ -332,6 +332,112 @@ void key_headers(HGeom &g, int32_t h0, const double *wt) {
   }
 }
 
+// ---------------------------------------------------------------- face relocation records
+// Inside test of volume V for a whole region R (key intervals per axis) and every
+// direction whose component on axis a has sign s (tangential components free):
+// 1 / 0 when the device's test gives that answer at every point, -1 when it is not
+// decided (the region straddles a threshold, a tangential band, or V is not a kKeyBox).
+int region_inside(const HGeom &g, int V, const int64_t R[3][2], int a, int s) {
+  if (!(g.vol[V].flags & kKeyBox)) return -1;
+  const DKeyBox &K = g.kbox[V];
+  for (int b = 0; b < 3; ++b)
+    if (R[b][1] <= K.k[b][0] || R[b][0] >= K.k[b][3]) return 0;   // outside by more than the band on axis b
+  int near = 0, high = 0;
+  for (int b = 0; b < 3; ++b) {
+    const int64_t lo = R[b][0], hi = R[b][1];
+    if (lo > K.k[b][1] && hi < K.k[b][2]) continue;                 // inside by more than the band
+    if (lo > K.k[b][0] && hi <= K.k[b][1]) { near |= 1 << b; continue; }
+    if (lo >= K.k[b][2] && hi < K.k[b][3]) { near |= 1 << b; high |= 1 << b; continue; }
+    return -1;
+  }
+  if (!near) return 1;
+  for (int b = 0; b < 3; ++b) {
+    if (!(near & (1 << b))) continue;
+    if (b != a) return -1;                                           // depends on a free direction component
+    if (((high >> b) & 1) == (s > 0)) return 0;                      // p_a v_a > 0: leaving V
+  }
+  return 1;
+}
+
+// Candidate lists of the voxel nodes of the tree at header h that overlap [lo, hi] (mother frame).
+void vox_collect(const HGeom &g, int32_t h, const double *lo, const double *hi, std::vector<int32_t> &lists) {
+  const DVoxHdr &H = g.hdr[h];
+  const int n = H.nslices;
+  long k0 = (long)std::floor((lo[H.axis] - H.lo) * H.inv_width) - 1;
+  long k1 = (long)std::floor((hi[H.axis] - H.lo) * H.inv_width) + 1;
+  k0 = std::max(0L, std::min((long)n - 1, k0));
+  k1 = std::max(0L, std::min((long)n - 1, k1));
+  for (long k = k0; k <= k1; ++k) {
+    const int32_t c = g.slice[H.slice_base + k].child;
+    if (c >= 0) lists.push_back(c);
+    else vox_collect(g, -c - 1, lo, hi, lists);
+  }
+}
+
+// The relocation after leaving kKeyBox volume L outward through face (a, s) for every point of
+// region R, evaluated as the device does it (up through the mothers from L's, the left volume
+// blocked; down through the daughters in id order); false if some test is not decided.
+bool eval_face(const HGeom &g, const std::vector<Box3> &ext, int L, int a, int s, const int64_t R[3][2], int &out) {
+  int blocked = L, V = g.vol[L].mother;
+  while (V >= 0) {
+    const int r = region_inside(g, V, R, a, s);
+    if (r < 0) return false;
+    if (r == 1) break;
+    blocked = V;
+    V = g.vol[V].mother;
+  }
+  if (V < 0) {
+    out = -1;
+    return true;
+  }
+  double rlo[3], rhi[3];
+  for (int b = 0; b < 3; ++b) {
+    rlo[b] = dunkey(R[b][0]);
+    rhi[b] = dunkey(R[b][1]);
+  }
+  int cur = V;
+  for (int lev = 0; lev < kDMax; ++lev) {
+    const DVol &C = g.vol[cur];
+    if (C.vox < 0) break;
+    if (!(C.flags & kWorldAligned)) return false;
+    const DWorld &w = g.wxf[cur];
+    const double wt[3] = {w.tx, w.ty, w.tz};
+    double lo[3], hi[3];
+    for (int b = 0; b < 3; ++b) {
+      const double sl = 1e-9 * (1.0 + std::fabs(rlo[b]) + std::fabs(wt[b]));
+      lo[b] = rlo[b] - wt[b] - sl;
+      hi[b] = rhi[b] - wt[b] + sl;
+    }
+    std::vector<int32_t> lists, cands;
+    vox_collect(g, C.vox, lo, hi, lists);
+    for (int32_t l : lists) {
+      const DCandList &cl = g.clist[l];
+      for (int32_t q = 0; q < cl.count; ++q) {
+        const int32_t d = g.cand[cl.offset + q];
+        bool hit = d != blocked;
+        for (int b = 0; b < 3 && hit; ++b) hit = ext[d].hi[b] >= lo[b] && ext[d].lo[b] <= hi[b];
+        if (hit) cands.push_back(d);
+      }
+    }
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    int found = -1;
+    for (int32_t d : cands) {
+      const int r = region_inside(g, d, R, a, s);
+      if (r < 0) return false;
+      if (r == 1) {
+        found = d;
+        break;
+      }
+    }
+    if (found < 0) break;
+    cur = found;
+    blocked = -1;
+  }
+  out = cur;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -672,19 +778,55 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
     }
     if (v.vox >= 0) key_headers(*g, v.vox, wt);
   }
+  // --- face relocation records of kKeyBox volumes
+  for (int i = 0; i < n; ++i) g->vol[i].face = -1;
+  for (int i = 0; i < n; ++i) {
+    DVol &v = g->vol[i];
+    if (!(v.flags & kKeyBox) || v.mother < 0) continue;
+    const DWorld &w = g->wxf[i];
+    const double wt[3] = {w.tx, w.ty, w.tz};
+    v.face = (int32_t)g->face.size();
+    for (int f = 0; f < 6; ++f) {
+      const int a = f >> 1, s = (f & 1) ? 1 : -1;
+      DFace F;
+      std::memset(&F, 0, sizeof(F));
+      F.leaf = -1;
+      bool ok = true;
+      for (int b = 0; b < 3; ++b) {
+        if (b == a) {
+          const double plane = wt[a] + s * v.p[a], d = 0.125 * tol;
+          F.k[b][0] = dkey(plane - d);
+          F.k[b][1] = dkey(plane + d);
+        } else {
+          const double m = 1e-6 + 1e-12 * (std::fabs(wt[b]) + v.p[b]);
+          const double lo = wt[b] - v.p[b] + m, hi = wt[b] + v.p[b] - m;
+          if (!(lo < hi)) ok = false;
+          F.k[b][0] = dkey(lo);
+          F.k[b][1] = dkey(hi);
+        }
+      }
+      int leaf = -1;
+      if (ok && eval_face(*g, ext, i, a, s, F.k, leaf)) {
+        F.leaf = leaf;
+        F.ok = 1;
+      }
+      g->face.push_back(F);
+    }
+  }
+  if (g->face.empty()) g->face.push_back(DFace{});
   // --- upload as one blob
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  constexpr int kTables = 15;
+  constexpr int kTables = 16;
   size_t off[kTables], sz[kTables] = {g->vol.size() * sizeof(DVol), g->wxf.size() * sizeof(DWorld), g->box.size() * sizeof(DBox32),
                             g->hdr.size() * sizeof(DVoxHdr), g->slice.size() * sizeof(DVoxSlice),
                             g->clist.size() * sizeof(DCandList), g->cand.size() * sizeof(int32_t),
                             g->matE.size() * sizeof(double), g->matC.size() * sizeof(double), g->matP.size() * sizeof(double),
                             g->mat_off.size() * sizeof(int32_t), g->mat_n.size() * sizeof(int32_t),
                             g->v32.size() * sizeof(DVol32), g->kbox.size() * sizeof(DKeyBox),
-                            g->skey.size() * sizeof(int64_t)};
+                            g->skey.size() * sizeof(int64_t), g->face.size() * sizeof(DFace)};
   const void *src[kTables] = {g->vol.data(), g->wxf.data(), g->box.data(), g->hdr.data(), g->slice.data(), g->clist.data(),
                          g->cand.data(), g->matE.data(), g->matC.data(), g->matP.data(), g->mat_off.data(), g->mat_n.data(),
-                         g->v32.data(), g->kbox.data(), g->skey.data()};
+                         g->v32.data(), g->kbox.data(), g->skey.data(), g->face.data()};
   size_t total = 0;
   for (int k = 0; k < kTables; ++k) { off[k] = total; total += al(std::max<size_t>(sz[k], 8)); }
   if (ctx->device < 0) {  // host-only context: keep the host tables
@@ -728,6 +870,7 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
   d.v32 = (const DVol32 *)(base + off[12]);
   d.kbox = (const DKeyBox *)(base + off[13]);
   d.skey = (const int64_t *)(base + off[14]);
+  d.face = (const DFace *)(base + off[15]);
   d.n_vol = n;
   d.n_mat = (int32_t)B.mats.size();
   d.shared_grid = 1;

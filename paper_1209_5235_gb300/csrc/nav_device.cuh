@@ -133,12 +133,24 @@ __device__ __forceinline__ double box_dist_in(const double *h, const V3 &p, cons
   return fmax(tin, 0.0);
 }
 
-// DistanceToOut with the reciprocal direction of the same frame.
-__device__ __forceinline__ double box_dist_out(const double *h, const V3 &p, const V3 &v, const Inv3 &iv) {
+// DistanceToOut with the reciprocal direction of the same frame; *face = the exit face
+// (2 axis + (v_axis > 0)) of the first axis attaining the minimum.
+__device__ __forceinline__ double box_dist_out(const double *h, const V3 &p, const V3 &v, const Inv3 &iv, int *face) {
   double t = kInf;
-  if (v.x != 0.0) t = fmin(t, (copysign(h[0], v.x) - p.x) * iv.x);
-  if (v.y != 0.0) t = fmin(t, (copysign(h[1], v.y) - p.y) * iv.y);
-  if (v.z != 0.0) t = fmin(t, (copysign(h[2], v.z) - p.z) * iv.z);
+  int f = -1;
+  if (v.x != 0.0) {
+    const double tx = (copysign(h[0], v.x) - p.x) * iv.x;
+    if (tx < t) t = tx, f = v.x > 0.0 ? 1 : 0;
+  }
+  if (v.y != 0.0) {
+    const double ty = (copysign(h[1], v.y) - p.y) * iv.y;
+    if (ty < t) t = ty, f = v.y > 0.0 ? 3 : 2;
+  }
+  if (v.z != 0.0) {
+    const double tz = (copysign(h[2], v.z) - p.z) * iv.z;
+    if (tz < t) t = tz, f = v.z > 0.0 ? 5 : 4;
+  }
+  *face = f;
   return fmax(t, 0.0);
 }
 
@@ -346,8 +358,10 @@ __device__ __forceinline__ double vol_dist_in(const DVol &d, const V3 &p, const 
   return tube_cross(d.p, d.flags, p, v, half, true);
 }
 
-__device__ __forceinline__ double vol_dist_out(const DVol &d, const V3 &p, const V3 &v, const Inv3 &iv, double half) {
-  if (d.kind == kBox) return box_dist_out(d.p, p, v, iv);
+__device__ __forceinline__ double vol_dist_out(const DVol &d, const V3 &p, const V3 &v, const Inv3 &iv, double half,
+                                               int *face) {
+  *face = -1;
+  if (d.kind == kBox) return box_dist_out(d.p, p, v, iv, face);
   if (d.kind == kOrb) return orb_dist_out(d.p[0], p, v);
   const double t = tube_cross(d.p, d.flags, p, v, half, false);
   return t == kInf ? 0.0 : fmax(t, 0.0);
@@ -863,6 +877,23 @@ __device__ __forceinline__ int relocate_warp(const DGeom &G, bool active, int le
   return in ? out : -1;
 }
 
+// Relocation after a step that left kKeyBox volume `leaf` through `face` (limiter mother,
+// positive length), from the volume's precomputed face record: true, and the new leaf
+// (-1: left the world) in *out, when x lies in the record's region and the direction's
+// normal component is not subnormal; the answer is then the one relocate_warp gives.
+__device__ __forceinline__ bool face_relocate(const DGeom &G, int leaf, int face, const V3 &x, const V3 &u, int *out) {
+  const int base = G.vol[leaf].face;
+  if (base < 0 || face < 0) return false;
+  const DFace &F = G.face[base + face];
+  if (!F.ok) return false;
+  if ((__double_as_longlong(comp(u, face >> 1)) & 0x7FF0000000000000ll) == 0) return false;
+  const long long kx = dkey(x.x), ky = dkey(x.y), kz = dkey(x.z);
+  if (kx < F.k[0][0] || kx > F.k[0][1] || ky < F.k[1][0] || ky > F.k[1][1] || kz < F.k[2][0] || kz > F.k[2][1])
+    return false;
+  *out = F.leaf;
+  return true;
+}
+
 // Voxel walk state: per level the header, the merged node's slice range.
 struct Chain {
   int h[kMaxLevels];
@@ -947,6 +978,7 @@ struct StepResult {
   double step;    // geometric step (exact when it is <= the limit)
   double safety;  // isotropic lower bound
   int lim;        // daughter id or G4N_LIM_MOTHER
+  int face;       // limiter mother and a box leaf: the exit face (2 axis + (v_axis > 0)), else -1
   bool physics;   // FP32 mode: proven that the limit comes first (no FP64 geometry done)
 };
 
@@ -962,8 +994,9 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
                                                      const Inv3 &iv, double limit, bool want_safety, Counters &cnt,
                                                      bool *timeout, const MlpCtx &mc) {
   const double half = G.half;
-  StepResult R{kInf, 0.0, G4N_LIM_MOTHER, false};
+  StepResult R{kInf, 0.0, G4N_LIM_MOTHER, -1, false};
   double best = kInf, stop = 0.0, tout = kInf;
+  int oface = -1;
   float out_lo = 0.f;
   Ray32 r;
   Chain ch;
@@ -983,7 +1016,7 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       stop = fmin(limit, (double)out_hi);
     } else {
       diag<COUNT>(cnt, G4N_C_DIST_OUT);
-      tout = vol_dist_out(V, p, v, iv, half);
+      tout = vol_dist_out(V, p, v, iv, half, &oface);
       R.safety = want_safety ? vol_safety_out(V, p) : 0.0;
       stop = fmin(limit, tout);
     }
@@ -1143,7 +1176,7 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       return R;
     }
     diag<COUNT>(cnt, G4N_C_DIST_OUT);
-    tout = vol_dist_out(G.vol[leaf], p, v, iv, half);
+    tout = vol_dist_out(G.vol[leaf], p, v, iv, half, &oface);
   }
   // a daughter wins a tie with the mother; `best` already holds the lowest id among tied daughters
   if (bl >= 0 && best <= tout) {
@@ -1152,6 +1185,7 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
   } else {
     R.step = tout;
     R.lim = G4N_LIM_MOTHER;
+    R.face = oface;
   }
   return R;
 }

@@ -476,8 +476,13 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
       t.safety = 0.0;
     }
   }
-  int leaf = relocate_warp<MODE, COUNT>(G, geo, geo ? t.leaf : 0, t.x, t.u, geo && lim == G4N_LIM_MOTHER && s > 0.0,
-                                        cnt);
+  // leaving a box through a face whose relocation is tabulated needs no search
+  int leaf = -1;
+  const bool left = geo && lim == G4N_LIM_MOTHER && s > 0.0;
+  const bool fast = left && face_relocate(G, t.leaf, R.face, t.x, t.u, &leaf);
+  if (fast) diag<COUNT>(cnt, G4N_C_FACE_RELOC);
+  const int searched = relocate_warp<MODE, COUNT>(G, geo && !fast, geo && !fast ? t.leaf : 0, t.x, t.u, left, cnt);
+  if (!fast) leaf = searched;
   bool pushing = false;
   if (geo) {
     t.nzero = (s <= G.half) ? t.nzero + 1 : 0;
@@ -752,8 +757,12 @@ __global__ void __launch_bounds__(128, 3) k_free_path(const FParams P) {
         cross = true;
       }
     }
-    const int nl = relocate_warp<MODE, COUNT>(G, cross, cross ? leaf : 0, x, u,
-                                              cross && R.lim == G4N_LIM_MOTHER && s > 0.0, cnt);
+    const bool left = cross && R.lim == G4N_LIM_MOTHER && s > 0.0;
+    int nl = -1;
+    const bool fast = left && face_relocate(G, leaf, R.face, x, u, &nl);
+    if (fast) diag<COUNT>(cnt, G4N_C_FACE_RELOC);
+    const int searched = relocate_warp<MODE, COUNT>(G, cross && !fast, cross && !fast ? leaf : 0, x, u, left, cnt);
+    if (!fast) nl = searched;
     if (cross) {
       if (nl < 0) {
         P.out_T[ray] = kInf;
