@@ -57,6 +57,13 @@ __device__ __forceinline__ void diag_kind(Counters &c, int kind) {
   }
 }
 
+// key(x): a double's bits as a signed integer with the negative half reflected, so that
+// x < y <=> key(x) < key(y) for all non-NaN doubles (-0 < +0).
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+
 // ---------------------------------------------------------------- frames
 
 __device__ __forceinline__ void to_local(const DVol &v, const V3 &pm, const V3 &vm, V3 &pl, V3 &vl) {
@@ -134,24 +141,30 @@ __device__ __forceinline__ double box_dist_in(const double *h, const V3 &p, cons
 }
 
 // DistanceToOut with the reciprocal direction of the same frame; *face = the exit face
-// (2 axis + (v_axis > 0)) of the first axis attaining the minimum.
+// (2 axis + (v_axis > 0)) of the first axis attaining the minimum.  The zero tests of
+// v, the minimum and the clamp at 0 are integer operations on the bit patterns (the
+// order-preserving keys of doubles), which give the same value as fmin/fmax.
+__device__ __forceinline__ bool nonzero_bits(double x) { return (__double_as_longlong(x) << 1) != 0; }
+
 __device__ __forceinline__ double box_dist_out(const double *h, const V3 &p, const V3 &v, const Inv3 &iv, int *face) {
+  constexpr long long kKeyInf = 0x7FF0000000000000ll;  // key of +inf; NaN keys lie outside [key(-inf), key(+inf)]
   double t = kInf;
+  long long kt = kKeyInf;
   int f = -1;
-  if (v.x != 0.0) {
-    const double tx = (copysign(h[0], v.x) - p.x) * iv.x;
-    if (tx < t) t = tx, f = v.x > 0.0 ? 1 : 0;
-  }
-  if (v.y != 0.0) {
-    const double ty = (copysign(h[1], v.y) - p.y) * iv.y;
-    if (ty < t) t = ty, f = v.y > 0.0 ? 3 : 2;
-  }
-  if (v.z != 0.0) {
-    const double tz = (copysign(h[2], v.z) - p.z) * iv.z;
-    if (tz < t) t = tz, f = v.z > 0.0 ? 5 : 4;
+  const double pp[3] = {p.x, p.y, p.z}, vv[3] = {v.x, v.y, v.z}, ii[3] = {iv.x, iv.y, iv.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!nonzero_bits(vv[a])) continue;
+    const double ta = (copysign(h[a], vv[a]) - pp[a]) * ii[a];
+    const long long k = dkey(ta);
+    if (k < kt && k >= -kKeyInf - 1) {
+      kt = k;
+      t = ta;
+      f = 2 * a + (vv[a] > 0.0 ? 1 : 0);
+    }
   }
   *face = f;
-  return fmax(t, 0.0);
+  return kt < 0 ? 0.0 : t;
 }
 
 __device__ __forceinline__ double box_safety_in(const double *h, const V3 &p) {
@@ -612,10 +625,6 @@ __device__ __forceinline__ int vox_lookup(const DGeom &G, int h, const V3 &p) {
 // FP64 predicates (Inside bands, slice index) change value; comparing keys then
 // gives the FP64 answer with integer instructions only.
 
-__device__ __forceinline__ long long dkey(double x) {
-  const long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
-}
 
 // A float near x built from the high word of its bits (truncated; no FP64 instruction).
 __device__ __forceinline__ float approx_float(double x) {
@@ -1203,10 +1212,11 @@ __device__ __forceinline__ void energy_bin(const double *Eg, int n, double E, in
     f = 1.0;
   } else {
     int lo = 0, hi = n - 1;
+    const long long eb = __double_as_longlong(E);  // E and the grid are positive: bit order = value order
 #pragma unroll 1
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
-      if (Eg[mid] <= E) lo = mid;
+      if (__double_as_longlong(Eg[mid]) <= eb) lo = mid;
       else hi = mid;
     }
     k = lo;
@@ -1220,10 +1230,11 @@ __device__ __forceinline__ void mu_at(const DGeom &G, int mat, int k, double f, 
   const int off = G.mat_off[mat];
   const double *C = G.matC + off, *P = G.matP + off;
   double mc, mp;
-  if (f == 0.0) {
+  const long long fb = __double_as_longlong(f);
+  if (fb == 0) {                                   // f == +0 (f is never -0 or negative)
     mc = C[k];
     mp = P[k];
-  } else if (f == 1.0) {
+  } else if (fb == 0x3FF0000000000000ll) {         // f == 1
     mc = C[k + 1];
     mp = P[k + 1];
   } else {
@@ -1259,12 +1270,29 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// Uniform in (0, 1] from one Philox block: counter (draw, id lo, id hi, stream).
-__device__ __forceinline__ double philox_uniform(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw) {
+// The 53-bit integer m of one Philox block (counter (draw, id lo, id hi, stream)): the
+// uniform in (0, 1] is m 2^-53.
+__device__ __forceinline__ uint64_t philox_m53(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw) {
   const uint4 x = philox4x32_10(make_uint4(draw++, (uint32_t)(uint64_t)tid, (uint32_t)((uint64_t)tid >> 32), stream),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
   const uint64_t w = ((uint64_t)x.y << 32) | x.x;
-  return (double)((w >> 11) + 1) * 0x1.0p-53;
+  return (w >> 11) + 1;
+}
+
+__device__ __forceinline__ double m53_double(uint64_t m) { return (double)m * 0x1.0p-53; }
+
+// m 2^-53 as a float, truncated to 24 bits (relative error < 2^-23), with integer
+// instructions only (m in [1, 2^53]).
+__device__ __forceinline__ float m53_float(uint64_t m) {
+  const int lz = __clzll((long long)m);                 // 11 .. 63
+  const int sh = 40 - lz;                               // keep the leading one and 23 bits below it
+  const uint32_t mant = sh >= 0 ? (uint32_t)(m >> sh) : (uint32_t)(m << (-sh));
+  return __uint_as_float(((uint32_t)(63 - lz - 53 + 127) << 23) | (mant & 0x7FFFFFu));
+}
+
+// Uniform in (0, 1] from one Philox block.
+__device__ __forceinline__ double philox_uniform(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw) {
+  return m53_double(philox_m53(seed, tid, stream, draw));
 }
 
 __device__ __forceinline__ uint64_t fnv_word(uint64_t h, uint32_t w) {

@@ -206,13 +206,20 @@ __device__ __forceinline__ int find_item(const DItem *items, int n_items, int64_
   return lo;
 }
 
-// Unit-disc rejection: (cos, sin) of a uniform azimuth.
+// Unit-disc rejection: (cos, sin) of a uniform azimuth.  Points with a^2 + b^2 > 1 + 1e-5 in
+// FP32 (from the Philox integers; error < 2e-6) are rejected without FP64 work; the others
+// take the FP64 test and, if accepted, the FP64 evaluation.
 __device__ __forceinline__ bool disc_azimuth(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw, double &c,
                                              double &s) {
 #pragma unroll 1
   for (int t = 0; t < 1000; ++t) {
-    const double a = 2.0 * philox_uniform(seed, tid, stream, draw) - 1.0;
-    const double b = 2.0 * philox_uniform(seed, tid, stream, draw) - 1.0;
+    const uint64_t ma = philox_m53(seed, tid, stream, draw);
+    const uint64_t mb = philox_m53(seed, tid, stream, draw);
+    const float af = 2.0f * m53_float(ma) - 1.0f, bf = 2.0f * m53_float(mb) - 1.0f;
+    const float r2f = af * af + bf * bf;
+    if (r2f > 1.0f + 1e-5f) continue;
+    const double a = 2.0 * m53_double(ma) - 1.0;
+    const double b = 2.0 * m53_double(mb) - 1.0;
     const double r2 = a * a + b * b;
     if (r2 > 0.0 && r2 <= 1.0) {
       const double inv = 1.0 / r2;
@@ -335,9 +342,10 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
 
 // Kahn's rejection method for the Klein-Nishina law of eta = E / E' (three uniforms per
 // trial).  Each comparison of a uniform with its threshold is first made in FP32 and kept
-// when they differ by more than 1e-5.  All three thresholds lie in [0, 1] and their FP32
+// when they differ by more than 1e-5.  All three thresholds lie in [0, 1]; their FP32
 // values (written without cancellation: 1 - (eta - 1) / alpha = 1 - 2 (1 - r2) / (1 + 2
-// alpha r2)) are within 2e-6 of the exact ones, so such a decision is the exact one; the
+// alpha r2)) and the uniforms' FP32 copies (built from the Philox integers, relative error
+// < 2^-23) are within 2e-6 of the exact ones, so such a decision is the exact one; the
 // others are taken on the FP64 thresholds of the plain formulas.  The accepted trial's eta
 // and cos theta are computed in FP64.  FP64 work is left for the accepted trial and the
 // rare close calls.
@@ -348,29 +356,26 @@ __device__ __forceinline__ bool kahn(double E, uint64_t seed, int64_t tid, uint3
   const float p1f = (1.0f + 2.0f * alf) / (9.0f + 2.0f * alf);
 #pragma unroll 1
   for (int t = 0; t < 1000; ++t) {
-    const double r1 = philox_uniform(seed, tid, 1, draw);
-    const double r2 = philox_uniform(seed, tid, 1, draw);
-    const double r3 = philox_uniform(seed, tid, 1, draw);
-    const float d1 = (float)r1 - p1f;
-    const bool first = fabsf(d1) > kMargin ? d1 <= 0.f : r1 <= (1.0 + 2.0 * al) / (9.0 + 2.0 * al);
-    const float r2f = (float)r2;
+    const uint64_t m1 = philox_m53(seed, tid, 1, draw);
+    const uint64_t m2 = philox_m53(seed, tid, 1, draw);
+    const uint64_t m3 = philox_m53(seed, tid, 1, draw);
+    const float d1 = m53_float(m1) - p1f;
+    const bool first = fabsf(d1) > kMargin ? d1 <= 0.f : m53_double(m1) <= (1.0 + 2.0 * al) / (9.0 + 2.0 * al);
+    const float r2f = m53_float(m2), r3f = m53_float(m3);
     const float a2 = 2.0f * alf * r2f, den = 1.0f + a2;
     if (first) {
-      const float d = (float)r3 - 4.0f * a2 / (den * den);
-      eta = 1.0 + 2.0 * al * r2;
-      if (fabsf(d) > kMargin) {
-        if (d > 0.f) continue;
-      } else if (!(r3 <= 4.0 * (1.0 / eta - 1.0 / (eta * eta)))) {
-        continue;
-      }
+      const float d = r3f - 4.0f * a2 / (den * den);
+      if (fabsf(d) > kMargin && d > 0.f) continue;
+      eta = 1.0 + 2.0 * al * m53_double(m2);
+      if (!(fabsf(d) > kMargin) && !(m53_double(m3) <= 4.0 * (1.0 / eta - 1.0 / (eta * eta)))) continue;
       cost = 1.0 - (eta - 1.0) / al;
     } else {
       const float cf = 1.0f - 2.0f * (1.0f - r2f) / den;
-      const float d = (float)r3 - 0.5f * (cf * cf + den / (1.0f + 2.0f * alf));
+      const float d = r3f - 0.5f * (cf * cf + den / (1.0f + 2.0f * alf));
       if (fabsf(d) > kMargin && d > 0.f) continue;
-      eta = (1.0 + 2.0 * al) / (1.0 + 2.0 * al * r2);
+      eta = (1.0 + 2.0 * al) / (1.0 + 2.0 * al * m53_double(m2));
       cost = 1.0 - (eta - 1.0) / al;
-      if (!(fabsf(d) > kMargin) && !(r3 <= 0.5 * (cost * cost + 1.0 / eta))) continue;
+      if (!(fabsf(d) > kMargin) && !(m53_double(m3) <= 0.5 * (cost * cost + 1.0 / eta))) continue;
     }
     return true;
   }
@@ -419,12 +424,16 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   V3 p{0, 0, 0}, v{0, 0, 1};
   Inv3 iv{0, 0, 0};
   bool lazy = false;       // FP64 mode: sphys not computed, s * mu is compared with Y instead
+  bool want_saf = true;    // FP64 mode, leaf without daughters: the safety is taken in the interaction phase
   double lim_geo = kInf;  // limit handed to the geometric step (an upper bound of sphys)
   if (act) {
     const DVol &L = G.vol[t.leaf];
-    lazy = MODE == kFP64 && t.mu > 0.0 && !mc.log;
-    if (!lazy) sphys = t.mu > 0.0 ? t.Y / t.mu : kInf;
-    need_geo = lazy ? !(t.Y < t.safety * t.mu) : !(sphys < t.safety);
+    const bool mu_pos = nonzero_bits(t.mu);  // mu >= 0
+    lazy = MODE == kFP64 && mu_pos && !mc.log;
+    if (!lazy) sphys = mu_pos ? t.Y / t.mu : kInf;
+    // a zero safety (after every boundary crossing) always needs the boundary search
+    need_geo = !nonzero_bits(t.safety) || (lazy ? !(t.Y < t.safety * t.mu) : !(sphys < t.safety));
+    want_saf = !(MODE == kFP64 && L.vox < 0);
     if (!need_geo) {
       diag<COUNT>(cnt, G4N_C_SAFETY_SKIPS);
       if (lazy) sphys = t.Y / t.mu;
@@ -441,8 +450,8 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   }
   bool timeout = false;
   if (MODE == kLearned || mc.log) mc.loge = act ? (logf((float)t.E) + 4.6f) * 0.1f : 0.f;
-  const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, lim_geo, true, cnt,
-                                                   &timeout, mc);
+  const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, lim_geo, want_saf,
+                                                   cnt, &timeout, mc);
   bool geo = false;
   double s = sphys;
   int lim = G4N_LIM_PHYSICS;
@@ -471,7 +480,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
       cnt.c[G4N_C_PHYS_STEPS]++;
       next = kInteract;
     } else {
-      if (t.mu > 0.0) t.Y = fmax(t.Y - s * t.mu, 0.0);
+      if (nonzero_bits(t.mu)) t.Y = fmax(t.Y - s * t.mu, 0.0);
       cnt.c[G4N_C_GEOM_STEPS]++;
       t.safety = 0.0;
     }
@@ -485,7 +494,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   if (!fast) leaf = searched;
   bool pushing = false;
   if (geo) {
-    t.nzero = (s <= G.half) ? t.nzero + 1 : 0;
+    t.nzero = (dkey(s) <= dkey(G.half)) ? t.nzero + 1 : 0;
     if (leaf >= 0 && t.nzero >= 10) {
       const double push = 100.0 * G.tol;
       t.x.x += push * t.u.x;
@@ -551,6 +560,15 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
   t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCompton);
   update_mu(G, t);
+  // the isotropic safety of a leaf without daughters, at the interaction point (the step
+  // phase does not compute it there; a safety only lets the next step skip a boundary
+  // search whose answer could not win)
+  const DVol &L = G.vol[t.leaf];
+  if (L.vox < 0) {
+    V3 p, v;
+    world_to_local(G.wxf[t.leaf], L.flags & kWorldAligned, t.x, t.u, p, v);
+    t.safety = fmax(t.safety, vol_safety_out(L, p));
+  }
   return kStep;
 }
 
