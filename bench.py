@@ -122,6 +122,9 @@ WORKLOADS = {
               "voxels; 10^7 gamma log-uniform 0.02-20 MeV isotropic from points on the axis",
     "barrel_learned": "barrel scene with the learned candidate proposal (MLP trained on steps logged by the plain "
                       "navigator); 10^7 gamma",
+    "barrel_nested": "barrel with deep nesting: 30 full tubes each inside the previous (the shells' annuli tiled by "
+                     "64 phi segments inside each), 2000 lead-like orbs in the segments, hierarchy depth 32, smart "
+                     "voxels; 10^7 gamma log-uniform 0.02-20 MeV isotropic from points on the axis",
     "spheres_regular": "Spheres (Sec. 3.4): 8000 aluminium balls r 100 mm on a 250 mm grid in a 5 m vacuum cube, smart "
                        "voxels, mu = rho x 0.06146 cm^2/g; 10^5 rays from the centre towards a 400 x 250 grid on the +z "
                        "face, Y = 1; free path T of Algorithm 1 per ray (the raytraced image)",
@@ -276,11 +279,11 @@ def setup_workload(g4, ctx, args, rank):
             tid += nt
         return g4.make_items(entries), off, synth.scenes.CONFIG_SEEDS[2][1], tid, WORKLOADS["batched"], \
             ["fp64", "fp32_recheck"]
-    sc = synth.scenes.barrel_scene()
+    sc = synth.scenes.nested_barrel_scene() if w == "barrel_nested" else synth.scenes.barrel_scene()
     gid = g4.build_scene(ctx, sc)
     n = 10_000_000
     items = g4.make_items([(gid, n, rank * n, synth.scenes.barrel_source(), 0)])
-    seed = synth.scenes.CONFIG_SEEDS[3 if w == "barrel" else 4][1]
+    seed = synth.scenes.CONFIG_SEEDS[4 if w == "barrel_learned" else 3][1]
     modes = ["fp64", "fp32_recheck"]
     if w == "barrel_learned":
         # the proposal network: 10^7 steps logged by the plain navigator, trained by the library's kernels
@@ -591,8 +594,8 @@ def main():
     ap.add_argument("--mode", default="auto", choices=["auto", "fp64", "fp32_recheck"])
     ap.add_argument("--voxel", default="smart")
     ap.add_argument("--workload", default="calorimeter",
-                    choices=["calorimeter", "tiny", "batched", "barrel", "barrel_learned", "spheres_regular",
-                             "spheres_random"])
+                    choices=["calorimeter", "tiny", "batched", "barrel", "barrel_learned", "barrel_nested",
+                             "spheres_regular", "spheres_random"])
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tune-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

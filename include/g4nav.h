@@ -65,7 +65,7 @@ enum {
 /* Limiter codes returned by g4n_compute_step. */
 enum { G4N_LIM_PHYSICS = -2, G4N_LIM_MOTHER = -1 };
 
-#define G4N_DMAX 8        /* maximum hierarchy depth, world included */
+#define G4N_DMAX 32       /* maximum hierarchy depth, world included */
 #define G4N_N_COUNTERS 32 /* length of the transport counter array */
 
 /* Transport counters (indices into out_counters). */

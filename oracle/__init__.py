@@ -40,7 +40,7 @@ _lib = None
 N_COUNTERS = 16
 COUNTER_NAMES = ["tracks", "steps", "geom_steps", "phys_steps", "photo", "compton", "escaped", "cutoff",
                  "pushes", "step_limit", "dist_in_evals", "inside_tests"]
-DMAX = 8
+DMAX = 32
 LIM_PHYS, LIM_MOTHER = -2, -1
 
 

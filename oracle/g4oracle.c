@@ -38,7 +38,7 @@
 #include <omp.h>
 #endif
 
-#define O_DMAX 8
+#define O_DMAX 32
 #define O_MAXG 4096
 #define O_INF INFINITY
 

@@ -23,7 +23,7 @@ G4N_ERR_STEP_LIMIT, G4N_ERR_TIMEOUT, G4N_ERR_QUEUE, G4N_ERR_STATE = -5, -6, -7, 
 G4N_BOX, G4N_TUBE, G4N_ORB = 0, 1, 2
 G4N_MODE_FP64, G4N_MODE_FP32_RECHECK, G4N_MODE_LEARNED = 0, 1, 2
 G4N_LIM_PHYSICS, G4N_LIM_MOTHER = -2, -1
-G4N_DMAX = 8
+G4N_DMAX = 32
 G4N_N_COUNTERS = 32
 G4N_FLAG_DIAGNOSTICS = 1
 G4N_NOALLOC_MAX_ITEMS = 256

@@ -1271,8 +1271,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // The 53-bit integer m of one Philox block (counter (draw, id lo, id hi, stream)): the
-// uniform in (0, 1] is m 2^-53.
-__device__ __forceinline__ uint64_t philox_m53(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw) {
+// uniform in (0, 1] is m 2^-53.  Out of line: its ~100 instructions would otherwise be
+// repeated at each of the ~15 draw sites of the transport kernel (measured: 1.5 % faster).
+__device__ __noinline__ uint64_t philox_m53(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw) {
   const uint4 x = philox4x32_10(make_uint4(draw++, (uint32_t)(uint64_t)tid, (uint32_t)((uint64_t)tid >> 32), stream),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
   const uint64_t w = ((uint64_t)x.y << 32) | x.x;

@@ -530,6 +530,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
 
 // The interaction at the end of a free path: photoabsorption if U mu_tot < mu_photo,
 // else a Compton scatter (Kahn), the cutoff, and a new Y = -log W.
+template <int MODE>
 __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   const DItem &it = P.items[t.item];
   const DGeom &G = P.geoms[it.geom];
@@ -560,11 +561,11 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
   t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCompton);
   update_mu(G, t);
-  // the isotropic safety of a leaf without daughters, at the interaction point (the step
-  // phase does not compute it there; a safety only lets the next step skip a boundary
-  // search whose answer could not win)
+  // FP64 mode: the isotropic safety of a leaf without daughters, at the interaction point
+  // (the step phase does not compute it there; a safety only lets the next step skip a
+  // boundary search whose answer could not win).  The FP32 modes keep their FP32 bound.
   const DVol &L = G.vol[t.leaf];
-  if (L.vox < 0) {
+  if (MODE == kFP64 && L.vox < 0) {
     V3 p, v;
     world_to_local(G.wxf[t.leaf], L.flags & kWorldAligned, t.x, t.u, p, v);
     t.safety = fmax(t.safety, vol_safety_out(L, p));
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
     const unsigned stepping = __ballot_sync(0xffffffffu, phase == kStep);
     const long long c1 = COUNT ? clock64() : 0;
     if (waiting && (__popc(waiting) >= P.interact_min || stepping == 0)) {
-      if (phase == kInteract) phase = interact(P, t, cnt);
+      if (phase == kInteract) phase = interact<MODE>(P, t, cnt);
     }
     __syncwarp();
     const long long c2 = COUNT ? clock64() : 0;

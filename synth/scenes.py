@@ -310,6 +310,62 @@ def barrel_scene(seed: int = CONFIG_SEEDS[3][0], n_shells: int = 30, n_phi: int 
     return Scene("barrel", mats, solids, places, VoxelSpec(mode="smart"))
 
 
+def nested_barrel_scene(seed: int = CONFIG_SEEDS[3][0], n_shells: int = 30, n_phi: int = 64, n_orbs: int = 2000,
+                        r_in: float = 50.0, r_out: float = 1500.0, half_len: float = 1500.0) -> Scene:
+    """The barrel with deep nesting: full tube k (radius R_k = r_out - k dr, half-length half_len - k mm) is placed
+    inside full tube k - 1; inside tube k the annulus [R_{k+1}, R_k] is tiled by n_phi φ segments (the innermost
+    annulus down to r_in), and orbs sit in the segments of all but the innermost shell.  Depth: world, 30 tubes,
+    a segment, an orb = 33 levels at most, 32 used (no orbs in the innermost shell)."""
+    rng = np.random.default_rng(seed)
+    mats, mi = _std_materials()
+    solids = [Solid(BOX, (2000.0, 2000.0, 2000.0))]
+    places = [Placement(-1, 0, mi["vacuum"], (0.0, 0.0, 0.0))]
+    dr = (r_out - r_in) / n_shells
+    dphi = TWO_PI / n_phi
+    seg_index = []   # (segment volume, rmin, rmax, hz, shell)
+    mother = 0
+    for k in range(n_shells):
+        R, Rin, hz = r_out - k * dr, r_out - (k + 1) * dr, half_len - k
+        solids.append(Solid(TUBE, (0.0, R, hz, 0.0, TWO_PI)))
+        places.append(Placement(mother, len(solids) - 1, mi["vacuum"], (0.0, 0.0, 0.0)))
+        tube = len(places) - 1
+        mat = mi["scint"] if k % 2 == 0 else mi["al"]
+        solids.append(Solid(TUBE, (Rin, R, hz, 0.0, dphi)))
+        seg_solid = len(solids) - 1
+        for j in range(n_phi):
+            th = j * dphi
+            places.append(Placement(tube, seg_solid, mat, (0.0, 0.0, 0.0), (math.cos(th), math.sin(th))))
+            if k < n_shells - 1:
+                seg_index.append((len(places) - 1, Rin, R, hz))
+        mother = tube
+    orbs_in = {}
+    margin = 0.5
+    placed, tries = 0, 0
+    while placed < n_orbs:
+        tries += 1
+        if tries > 100 * n_orbs:
+            raise RuntimeError("could not place orbs")
+        vol, rmin, rmax, hz = seg_index[int(rng.integers(len(seg_index)))]
+        r = float(rng.uniform(5.0, 20.0))
+        lo, hi = rmin + r + margin, rmax - r - margin
+        if lo >= hi:
+            continue
+        rc = float(rng.uniform(lo, hi))
+        half_ang = math.asin(min(1.0, (r + margin) / rc))
+        if 2.0 * half_ang >= dphi:
+            continue
+        ph = float(rng.uniform(half_ang, dphi - half_ang))
+        zc = float(rng.uniform(-hz + r + margin, hz - r - margin))
+        c = np.array([rc * math.cos(ph), rc * math.sin(ph), zc])
+        if any(np.sum((c - c2) ** 2) < (r + r2 + margin) ** 2 for c2, r2 in orbs_in.get(vol, [])):
+            continue
+        orbs_in.setdefault(vol, []).append((c, r))
+        solids.append(Solid(ORB, (r,)))
+        places.append(Placement(vol, len(solids) - 1, mi["lead"], tuple(float(x) for x in c)))
+        placed += 1
+    return Scene("nested_barrel", mats, solids, places, VoxelSpec(mode="smart"))
+
+
 def barrel_source() -> Source:
     return Source(pos=(0.0, 0.0, 0.0), z_range=(-1500.0, 1500.0), isotropic=True, e_kind="loguniform",
                   e0=0.02, e1=20.0)

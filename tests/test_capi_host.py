@@ -85,8 +85,9 @@ def test_host_only_validation(g4, case, code):
             elif case == "sticks_out":
                 g4.build_scene(ctx, _scene([Solid(ORB, (10,))], [Placement(0, 1, 0, (95, 0, 0))]))
             elif case == "too_deep":
-                sols = [Solid(BOX, (90.0 - 10 * k, 90.0 - 10 * k, 90.0 - 10 * k)) for k in range(8)]
-                g4.build_scene(ctx, _scene(sols, [Placement(k, k + 1, 0, (0, 0, 0)) for k in range(8)]))
+                D = g4.G4N_DMAX
+                sols = [Solid(BOX, (95.0 - 2.5 * k,) * 3) for k in range(D)]
+                g4.build_scene(ctx, _scene(sols, [Placement(k, k + 1, 0, (0, 0, 0)) for k in range(D)]))
             elif case == "bad_rotation":
                 g4.build_scene(ctx, _scene([Solid(BOX, (1, 1, 1))], [Placement(0, 1, 0, (0, 0, 0), (1.0, 0.1))]))
             elif case == "bad_box":
@@ -110,8 +111,9 @@ def test_host_only_accepts_touching_and_max_depth(g4):
     """Exactly touching siblings and a hierarchy of exactly G4N_DMAX levels are valid."""
     ctx = g4.g4n_create(-1)
     try:
-        sols = [Solid(BOX, (90.0 - 10 * k, 90.0 - 10 * k, 90.0 - 10 * k)) for k in range(7)]
-        g4.build_scene(ctx, _scene(sols, [Placement(k, k + 1, 0, (0, 0, 0)) for k in range(7)]))
+        D = g4.G4N_DMAX
+        sols = [Solid(BOX, (95.0 - 2.5 * k,) * 3) for k in range(D - 1)]
+        g4.build_scene(ctx, _scene(sols, [Placement(k, k + 1, 0, (0, 0, 0)) for k in range(D - 1)]))
         g4.build_scene(ctx, _scene([Solid(BOX, (10, 10, 10))],
                                    [Placement(0, 1, 0, (-10, 0, 0)), Placement(0, 1, 0, (10, 0, 0))]))
         seg = Solid(TUBE, (10.0, 20.0, 5.0, 0.0, math.pi / 2))

@@ -42,8 +42,9 @@ SCENES = {
     "nested_core": lambda: nested_scene(),
     "spheres": lambda: synth.scenes.spheres_scene(),
     "segments": lambda: segments_scene(),
+    "nested_barrel": lambda: synth.scenes.nested_barrel_scene(),
 }
-BOX_HALF = {"barrel": (1600.0, 1600.0, 1600.0), "calorimeter": (600.0, 600.0, 400.0), "nested_core": (12.0, 12.0, 12.0),
+BOX_HALF = {"barrel": (1600.0, 1600.0, 1600.0), "nested_barrel": (1600.0, 1600.0, 1600.0), "calorimeter": (600.0, 600.0, 400.0), "nested_core": (12.0, 12.0, 12.0),
             "segments": (360.0, 360.0, 90.0)}
 AIM = {"segments": 0.8, "mixed_smart": 0.3, "mixed_fixed": 0.3, "mixed_none": 0.3}
 
@@ -68,6 +69,8 @@ def test_locate_parity(env, name):
     bad = np.nonzero((d != d_ref) | np.any(path != path_ref, axis=1))[0]
     assert bad.size == 0, f"{bad.size} mismatches, first: {p[bad[0]]} {v[bad[0]]} gpu {path[bad[0]]} ref {path_ref[bad[0]]}"
     assert (d_ref >= 2).sum() > 0  # the cases do reach daughters
+    if name == "nested_barrel":
+        assert d_ref.max() == g4.G4N_DMAX  # the deepest level is reached
 
 
 def _band_edge_points(sc, n, seed, half=0.5e-9):
@@ -202,12 +205,14 @@ def _compare_transport(g4, r, edep, cnt, h, ln, nv, exact_tally_rel=1e-9):
 
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name,n", [("tiny", 10000), ("calorimeter", 20000), ("mixed_smart", 20000),
-                                    ("barrel", 20000), ("nested", 20000), ("spheres", 5000), ("segments", 20000)])
+                                    ("barrel", 20000), ("nested", 20000), ("spheres", 5000), ("segments", 20000),
+                                    ("nested_barrel", 20000)])
 def test_transport_parity(env, name, n, mode):
     g4, torch, ctx = env
     sc, og, gid = _build(env, name)
     src = {"tiny": synth.scenes.tiny_source(), "calorimeter": synth.scenes.calorimeter_source(),
-           "barrel": synth.scenes.barrel_source()}.get(name, Source(pos=(1.0, 2.0, 3.0), isotropic=True,
+           "barrel": synth.scenes.barrel_source(),
+           "nested_barrel": synth.scenes.barrel_source()}.get(name, Source(pos=(1.0, 2.0, 3.0), isotropic=True,
                                                                    e_kind="loguniform", e0=0.05, e1=5.0))
     seed = 0x7A0C0000
     r = og.transport(src, seed, n, threads=0)
