@@ -235,8 +235,11 @@ typedef struct {
  * cap (0 = 10^6).  Launch shape (0 = defaults): block_size (multiple of 32, <= 128),
  * blocks_per_sm, refill_min (a warp refills its idle lanes once at least this many are idle,
  * 1..32, default 8), interact_min (a warp runs its interaction phase once at least this many
- * lanes wait for it, 1..32, default 8).  flags: G4N_FLAG_DIAGNOSTICS also fills the diagnostic
- * counters (G4N_C_FACE_RELOC and above).  Results never depend on the launch shape. */
+ * lanes wait for it, 1..32, default 8), walk_budget (voxel nodes a boundary search walks in one
+ * round of its warp before it yields and continues in a later round, so that lanes with short
+ * searches take their next steps meanwhile; default 8, values >= 65536 never yield).  flags:
+ * G4N_FLAG_DIAGNOSTICS also fills the diagnostic counters (G4N_C_FACE_RELOC and above).  Results
+ * never depend on the launch shape. */
 #define G4N_FLAG_DIAGNOSTICS 1
 typedef struct {
   int32_t n_items;
@@ -252,6 +255,7 @@ typedef struct {
   int32_t refill_min;
   int32_t interact_min;
   int32_t flags;
+  int32_t walk_budget;
 } g4n_batch_desc;
 
 /* Transport every track of the batch (Algorithm 2, phase 5).  out_edep: n_tally_batches x

@@ -7,6 +7,7 @@
 //   DBox32[n]    32 B: FP32 bounding box of each volume in its mother's frame,
 //                rounded outward and padded (conservative prefilter for Inside)
 //   DVoxHdr[]    smart-voxel headers (one per slicing level and node)
+//   DVoxHdr32[]  their FP32 enclosures (the FP32 voxel walk)
 //   DVoxSlice[]  per slice: child (candidate list or sub-header) and the
 //                slice range [k0, k1] of the merged node it belongs to
 //   DCandList[]  (offset, count) into cand[]: daughter ids in increasing id
@@ -97,6 +98,15 @@ struct DVoxHdr {
   float lo_wf, inv_wf;      // FP32 slice origin in world coordinates and 1/width (for a first guess)
 };
 
+// FP32 copy of a voxel header for the FP32 voxel walk: enclosures of lo, width and
+// inv_width (the floats nearest below and above each), with which every FP64 slab
+// boundary and slice index of the header is bounded.
+struct alignas(32) DVoxHdr32 {
+  float lo_dn, lo_up, w_dn, w_up, iw_dn, iw_up;
+  int32_t slice_base;
+  int32_t n_axis;           // nslices << 2 | axis
+};
+
 struct DVoxSlice {
   int32_t child;            // >= 0: candidate list id; < 0: -(sub header + 1)
   int16_t k0, k1;           // slice range of the merged node
@@ -113,6 +123,7 @@ struct DGeom {
   const DBox32 *box;
   const DVol32 *v32;
   const DVoxHdr *hdr;
+  const DVoxHdr32 *hdr32;
   const DVoxSlice *slice;
   const DCandList *clist;
   const int32_t *cand;
@@ -150,6 +161,7 @@ struct HGeom {
   std::vector<DBox32> box;
   std::vector<DVol32> v32;
   std::vector<DVoxHdr> hdr;
+  std::vector<DVoxHdr32> hdr32;
   std::vector<DVoxSlice> slice;
   std::vector<DCandList> clist;
   std::vector<int32_t> cand;

@@ -163,6 +163,13 @@ void to_local(const HPlace &pl, const double *m, double *l) {
   l[2] = m[2] - pl.t[2];
 }
 
+// The floats nearest below and above x (both x when x is a float).
+void float_enclose(double x, float &lo, float &hi) {
+  const float f = (float)x;
+  lo = (double)f > x ? std::nextafter(f, -HUGE_VALF) : f;
+  hi = (double)f < x ? std::nextafter(f, HUGE_VALF) : f;
+}
+
 int smart_levels(const g4n_voxel_params &P) { return P.n_levels > 0 ? std::min(P.n_levels, kMaxLevels) : kMaxLevels; }
 
 struct VoxBuilder {
@@ -814,19 +821,31 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
     }
   }
   if (g->face.empty()) g->face.push_back(DFace{});
+  // --- FP32 copies of the voxel headers
+  g->hdr32.resize(g->hdr.size());
+  for (size_t h = 0; h < g->hdr.size(); ++h) {
+    const DVoxHdr &H = g->hdr[h];
+    DVoxHdr32 &F = g->hdr32[h];
+    float_enclose(H.lo, F.lo_dn, F.lo_up);
+    float_enclose(H.width, F.w_dn, F.w_up);
+    float_enclose(H.inv_width, F.iw_dn, F.iw_up);
+    F.slice_base = H.slice_base;
+    F.n_axis = (H.nslices << 2) | H.axis;
+  }
   // --- upload as one blob
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  constexpr int kTables = 16;
+  constexpr int kTables = 17;
   size_t off[kTables], sz[kTables] = {g->vol.size() * sizeof(DVol), g->wxf.size() * sizeof(DWorld), g->box.size() * sizeof(DBox32),
                             g->hdr.size() * sizeof(DVoxHdr), g->slice.size() * sizeof(DVoxSlice),
                             g->clist.size() * sizeof(DCandList), g->cand.size() * sizeof(int32_t),
                             g->matE.size() * sizeof(double), g->matC.size() * sizeof(double), g->matP.size() * sizeof(double),
                             g->mat_off.size() * sizeof(int32_t), g->mat_n.size() * sizeof(int32_t),
                             g->v32.size() * sizeof(DVol32), g->kbox.size() * sizeof(DKeyBox),
-                            g->skey.size() * sizeof(int64_t), g->face.size() * sizeof(DFace)};
+                            g->skey.size() * sizeof(int64_t), g->face.size() * sizeof(DFace),
+                            g->hdr32.size() * sizeof(DVoxHdr32)};
   const void *src[kTables] = {g->vol.data(), g->wxf.data(), g->box.data(), g->hdr.data(), g->slice.data(), g->clist.data(),
                          g->cand.data(), g->matE.data(), g->matC.data(), g->matP.data(), g->mat_off.data(), g->mat_n.data(),
-                         g->v32.data(), g->kbox.data(), g->skey.data(), g->face.data()};
+                         g->v32.data(), g->kbox.data(), g->skey.data(), g->face.data(), g->hdr32.data()};
   size_t total = 0;
   for (int k = 0; k < kTables; ++k) { off[k] = total; total += al(std::max<size_t>(sz[k], 8)); }
   if (ctx->device < 0) {  // host-only context: keep the host tables
@@ -859,6 +878,7 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
   d.wxf = (const DWorld *)(base + off[1]);
   d.box = (const DBox32 *)(base + off[2]);
   d.hdr = (const DVoxHdr *)(base + off[3]);
+  d.hdr32 = (const DVoxHdr32 *)(base + off[16]);
   d.slice = (const DVoxSlice *)(base + off[4]);
   d.clist = (const DCandList *)(base + off[5]);
   d.cand = (const int32_t *)(base + off[6]);

@@ -606,6 +606,63 @@ __device__ __forceinline__ int slice_of(const DVoxHdr &H, double coord) {
   return (int)f;
 }
 
+// ---------------------------------------------------------------- FP32 voxel walk
+// The FP32 modes walk the voxel nodes with interval arithmetic on the headers' outward
+// rounded FP32 copies (lo_dn/lo_up, w_dn/w_up, iw_dn/iw_up) and on the ray's enclosure
+// (Ray32).  Every interval encloses the value the FP64 walk computes (each FP64 result
+// is a double between two directed-rounded floats of the same operation), so a
+// decision taken where the intervals do not overlap is the FP64 walk's decision; an
+// overlapping case returns "undecided" and the FP64 code takes that node step.
+
+__device__ __forceinline__ float sel3(float a, float b, float c, int i) { return i == 0 ? a : (i == 1 ? b : c); }
+__device__ __forceinline__ int sel3i(int a, int b, int c, int i) { return i == 0 ? a : (i == 1 ? b : c); }
+
+// Slice index of every FP64 coordinate in [qlo, qhi] under slice_of, or -1 if they differ.
+__device__ __forceinline__ int slice_of32(const DVoxHdr32 &H, float qlo, float qhi) {
+  const float dlo = __fsub_rd(qlo, H.lo_up), dhi = __fsub_ru(qhi, H.lo_dn);
+  const float slo = dlo >= 0.f ? __fmul_rd(dlo, H.iw_dn) : __fmul_rd(dlo, H.iw_up);
+  const float shi = dhi >= 0.f ? __fmul_ru(dhi, H.iw_up) : __fmul_ru(dhi, H.iw_dn);
+  const float top = (float)((H.n_axis >> 2) - 1);
+  const float klo = fminf(fmaxf(floorf(slo), 0.f), top), khi = fminf(fmaxf(floorf(shi), 0.f), top);
+  return klo == khi ? (int)klo : -1;
+}
+
+// Enclosure of the FP64 slab boundaries lo + k0 w and lo + (k1 + 1) w of a merged node.
+__device__ __forceinline__ void slab32(const DVoxHdr32 &H, int k0, int k1, float &blo_dn, float &blo_up, float &bhi_dn,
+                                       float &bhi_up) {
+  const float a = (float)k0, b = (float)(k1 + 1);
+  blo_dn = __fadd_rd(H.lo_dn, __fmul_rd(a, H.w_dn));
+  blo_up = __fadd_ru(H.lo_up, __fmul_ru(a, H.w_up));
+  bhi_dn = __fadd_rd(H.lo_dn, __fmul_rd(b, H.w_dn));
+  bhi_up = __fadd_ru(H.lo_up, __fmul_ru(b, H.w_up));
+}
+
+// Enclosure [qlo, qhi] of the FP64 coordinate p_a + t v_a for t in [tl, th] (axis a of the ray).
+// False when v_a is tiny but not zero (the FP32 enclosure does not hold it).
+__device__ __forceinline__ bool advance32(const Ray32 &r, const V3 &v, int a, float tl, float th, float &qlo,
+                                          float &qhi) {
+  const float plo = sel3(r.plo[0], r.plo[1], r.plo[2], a), phi = sel3(r.phi[0], r.phi[1], r.phi[2], a);
+  const int sg = sel3i(r.sgn[0], r.sgn[1], r.sgn[2], a);
+  if (sg == 0) {
+    qlo = plo;
+    qhi = phi;
+    return !nonzero_bits(comp(v, a));
+  }
+  // |v_a| lies in [1 / ihi, 1 / ilo]
+  const float ilo = sel3(r.ilo[0], r.ilo[1], r.ilo[2], a), ihi = sel3(r.ihi[0], r.ihi[1], r.ihi[2], a);
+  const float vlo = __frcp_rd(ihi), vhi = __frcp_ru(ilo);
+  const float mlo = tl >= 0.f ? __fmul_rd(tl, vlo) : __fmul_rd(tl, vhi);
+  const float mhi = th >= 0.f ? __fmul_ru(th, vhi) : __fmul_ru(th, vlo);
+  if (sg > 0) {
+    qlo = __fadd_rd(plo, mlo);
+    qhi = __fadd_ru(phi, mhi);
+  } else {
+    qlo = __fsub_rd(plo, mhi);
+    qhi = __fsub_ru(phi, mlo);
+  }
+  return true;
+}
+
 // Candidate list of the voxel node holding p (mother frame).
 __device__ __forceinline__ int vox_lookup(const DGeom &G, int h, const V3 &p) {
 #pragma unroll 1
@@ -727,7 +784,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // daughter of m already known not to contain the point (the volume just left).
 // Returns the deepest volume.
 template <bool COUNT>
-__device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, V3 p, V3 v, bool have_p,
+__device__ __forceinline__ int descend_body(const DGeom &G, bool active, int m, V3 p, V3 v, bool have_p,
                                             const WPos &W, int blocked, Counters &cnt) {
 #pragma unroll 1
   for (int lev = 0; lev < kDMax; ++lev) {
@@ -815,8 +872,27 @@ __device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, 
   return m;
 }
 
-// Locate from the world (warp-collective): the leaf, or -1 outside the world.
+// The descent out of line: one copy of its code serves every call site of a kernel.  The
+// FP32 modes use it (their kernels are larger and stall on instruction fetch, which the
+// shared copy relieves: measured 8 % on the barrel scene); the FP64 navigator inlines it
+// (measured 2 % faster on the calorimeter, whose relocations are mostly face records).
+// Counters are passed by pointer (null without diagnostics) so that they stay in registers.
 template <bool COUNT>
+__device__ __noinline__ int descend_ool(const DGeom &G, bool active, int m, V3 p, V3 v, bool have_p, const WPos &W,
+                                        int blocked, Counters *cntp) {
+  Counters none;
+  return descend_body<COUNT>(G, active, m, p, v, have_p, W, blocked, COUNT ? *cntp : none);
+}
+
+template <bool COUNT, bool OOL>
+__device__ __forceinline__ int descend_warp(const DGeom &G, bool active, int m, V3 p, V3 v, bool have_p,
+                                            const WPos &W, int blocked, Counters &cnt) {
+  if (OOL) return descend_ool<COUNT>(G, active, m, p, v, have_p, W, blocked, COUNT ? &cnt : nullptr);
+  return descend_body<COUNT>(G, active, m, p, v, have_p, W, blocked, cnt);
+}
+
+// Locate from the world (warp-collective): the leaf, or -1 outside the world.
+template <bool COUNT, bool OOL = false>
 __device__ __forceinline__ int locate_world_warp(const DGeom &G, bool active, const V3 &x, const V3 &u, Counters &cnt) {
   V3 p{0, 0, 0}, v{0, 0, 1};
   bool in = false, have_p = false;
@@ -832,7 +908,7 @@ __device__ __forceinline__ int locate_world_warp(const DGeom &G, bool active, co
       in = vol_inside(G.vol[0], p, v, G.half);
     }
   }
-  const int leaf = descend_warp<COUNT>(G, in, 0, p, v, have_p, W, -1, cnt);
+  const int leaf = descend_warp<COUNT, OOL>(G, in, 0, p, v, have_p, W, -1, cnt);
   return in ? leaf : -1;
 }
 
@@ -882,7 +958,7 @@ __device__ __forceinline__ int relocate_warp(const DGeom &G, bool active, int le
       }
     }
   }
-  const int out = descend_warp<COUNT>(G, in, in ? leaf : 0, p, v, have_p, W, blocked, cnt);
+  const int out = descend_warp<COUNT, MODE != kFP64>(G, in, in ? leaf : 0, p, v, have_p, W, blocked, cnt);
   return in ? out : -1;
 }
 
@@ -928,6 +1004,191 @@ __device__ __forceinline__ void chain_fill(const DGeom &G, Chain &ch, int lev, i
   }
   ch.nlev = kMaxLevels;
   ch.list = 0;
+}
+
+// One node step of the plain FP64 voxel walk: the exit texit of the current node along the
+// ray (the first level whose slab the ray leaves), the end test texit >= bound, the
+// neighbouring node across that face and the lookup of its deeper levels at p + texit v.
+// Returns 0: the walk ends; 1: ch holds the next node.  With `saf` the distances from the
+// point to the node's slab faces lower *saf.
+__device__ __forceinline__ int walk_step64(const DGeom &G, Chain &ch, const V3 &p, const V3 &v, const Inv3 &iv,
+                                           double bound, bool saf, double *saf64, int *it, bool *timeout,
+                                           double *t_exit) {
+  double texit = kInf;
+  int lstar = -1;
+#pragma unroll 1
+  for (int l = 0; l < ch.nlev; ++l) {
+    const DVoxHdr H = G.hdr[ch.h[l]];
+    const double pa = comp(p, H.axis), va = comp(v, H.axis);
+    const double blo = H.lo + ch.k0[l] * H.width, bhi = H.lo + (ch.k1[l] + 1) * H.width;
+    if (saf) *saf64 = fmin(*saf64, fmax(fmin(pa - blo, bhi - pa), 0.0));
+    double t = kInf;
+    if (va > 0.0) t = (bhi - pa) * icomp(iv, H.axis);
+    else if (va < 0.0) t = (blo - pa) * icomp(iv, H.axis);
+    if (t < texit) {
+      texit = t;
+      lstar = l;
+    }
+  }
+  if (!(texit < bound)) return 0;
+  *t_exit = texit;
+  const DVoxHdr H = G.hdr[ch.h[lstar]];
+  const int nk = comp(v, H.axis) > 0.0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
+  if (nk < 0 || nk >= H.nslices || ++*it >= (1 << 16)) {
+    if (*it >= (1 << 16)) *timeout = true;
+    return 0;
+  }
+  const DVoxSlice S = G.slice[H.slice_base + nk];
+  ch.k0[lstar] = S.k0;
+  ch.k1[lstar] = S.k1;
+  if (S.child >= 0) {
+    ch.nlev = lstar + 1;
+    ch.list = S.child;
+  } else {
+    const V3 qpt{p.x + texit * v.x, p.y + texit * v.y, p.z + texit * v.z};
+    chain_fill(G, ch, lstar + 1, -S.child - 1, qpt);
+  }
+  return 1;
+}
+
+// The same, out of line: the FP32 modes take it only when their intervals do not decide.
+__device__ __noinline__ int walk_step64_ool(const DGeom &G, Chain &ch, const V3 &p, const V3 &v, const Inv3 &iv,
+                                            double bound, bool saf, double *saf64, int *it, bool *timeout,
+                                            double *t_exit) {
+  return walk_step64(G, ch, p, v, iv, bound, saf, saf64, it, timeout, t_exit);
+}
+
+// chain_fill from the root header h0 for every FP64 point in the ray's enclosure (FP32
+// modes); false if a level's slice index is undecided (the caller then fills in FP64).
+__device__ __forceinline__ bool chain_fill32(const DGeom &G, Chain &ch, int h, const Ray32 &r) {
+#pragma unroll 1
+  for (int lev = 0; lev < kMaxLevels; ++lev) {
+    const DVoxHdr32 H = G.hdr32[h];
+    const int a = H.n_axis & 3;
+    const int k = slice_of32(H, sel3(r.plo[0], r.plo[1], r.plo[2], a), sel3(r.phi[0], r.phi[1], r.phi[2], a));
+    if (k < 0) return false;
+    const DVoxSlice S = G.slice[H.slice_base + k];
+    ch.h[lev] = h;
+    ch.k0[lev] = S.k0;
+    ch.k1[lev] = S.k1;
+    if (S.child >= 0) {
+      ch.nlev = lev + 1;
+      ch.list = S.child;
+      return true;
+    }
+    h = -S.child - 1;
+  }
+  ch.nlev = kMaxLevels;
+  ch.list = 0;
+  return true;
+}
+
+// Lower / upper bound of num / |v_a| for a runtime axis a.
+__device__ __forceinline__ float div_lo_a(float n, const Ray32 &r, int a) {
+  return n >= 0.f ? __fmul_rd(n, sel3(r.ilo[0], r.ilo[1], r.ilo[2], a)) : __fmul_rd(n, sel3(r.ihi[0], r.ihi[1], r.ihi[2], a));
+}
+__device__ __forceinline__ float div_hi_a(float n, const Ray32 &r, int a) {
+  return n >= 0.f ? __fmul_ru(n, sel3(r.ihi[0], r.ihi[1], r.ihi[2], a)) : __fmul_ru(n, sel3(r.ilo[0], r.ilo[1], r.ilo[2], a));
+}
+
+// One node step of the voxel walk in FP32 interval arithmetic (FP32 modes): the exit of
+// the current node along the ray (the level whose slab the ray leaves first), the end
+// test against bound_f (an upper bound of the FP64 walk's bound min(best, stop)), the
+// neighbouring node and the lookup of its deeper levels at the entry point.  Returns 0:
+// the walk ends; 1: ch holds the next node; 2: undecided (ch unchanged), the FP64 code
+// takes this node step.  With `saf` the distances from the point to the node's slab
+// faces lower the isotropic safety *saf_f.
+__device__ __forceinline__ int walk_step32(const DGeom &G, Chain &ch, const Ray32 &r, const V3 &v, float bound_f,
+                                           bool saf, float *saf_f, int *it, bool *timeout, float *t_exit_lo) {
+  float tl[kMaxLevels], th[kMaxLevels];
+  const int nlev = ch.nlev;
+  int lstar = -1;
+  float ts_lo = kInfF, ts_hi = kInfF;
+  bool tiny = false;
+#pragma unroll
+  for (int l = 0; l < kMaxLevels; ++l) {
+    tl[l] = th[l] = kInfF;
+    if (l < nlev) {
+      const DVoxHdr32 H = G.hdr32[ch.h[l]];
+      const int a = H.n_axis & 3;
+      float blo_dn, blo_up, bhi_dn, bhi_up;
+      slab32(H, ch.k0[l], ch.k1[l], blo_dn, blo_up, bhi_dn, bhi_up);
+      const float plo = sel3(r.plo[0], r.plo[1], r.plo[2], a), phi = sel3(r.phi[0], r.phi[1], r.phi[2], a);
+      if (saf) *saf_f = fminf(*saf_f, fmaxf(fminf(__fsub_rd(plo, blo_up), __fsub_rd(bhi_dn, phi)), 0.f));
+      const int sg = sel3i(r.sgn[0], r.sgn[1], r.sgn[2], a);
+      if (sg > 0) {
+        tl[l] = div_lo_a(__fsub_rd(bhi_dn, phi), r, a);
+        th[l] = div_hi_a(__fsub_ru(bhi_up, plo), r, a);
+      } else if (sg < 0) {
+        tl[l] = div_lo_a(__fsub_rd(plo, blo_up), r, a);
+        th[l] = div_hi_a(__fsub_ru(phi, blo_dn), r, a);
+      } else {
+        tiny |= nonzero_bits(comp(v, a));  // a direction component too small for the enclosure
+      }
+      if (th[l] < ts_hi) {
+        ts_hi = th[l];
+        ts_lo = tl[l];
+        lstar = l;
+      }
+    }
+  }
+  if (tiny) return 2;
+  if (lstar < 0) return 0;  // the ray leaves no slab: the FP64 exit is +inf
+  // the FP64 minimum is taken by lstar alone (the first level attaining it wins ties)
+#pragma unroll
+  for (int l = 0; l < kMaxLevels; ++l)
+    if (l != lstar && !(tl[l] > ts_hi)) return 2;
+  if (ts_lo >= bound_f) return 0;  // texit >= bound_f >= min(best, stop)
+  *t_exit_lo = ts_lo;
+  const DVoxHdr32 H = G.hdr32[ch.h[lstar]];
+  const int nk = sel3i(r.sgn[0], r.sgn[1], r.sgn[2], H.n_axis & 3) > 0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
+  if (nk < 0 || nk >= (H.n_axis >> 2) || ++*it >= (1 << 16)) {
+    if (*it >= (1 << 16)) *timeout = true;
+    return 0;
+  }
+  const DVoxSlice S = G.slice[H.slice_base + nk];
+  int list = S.child;
+  int dh[kMaxLevels - 1], dk0[kMaxLevels - 1], dk1[kMaxLevels - 1];
+  int nd = 0;
+  if (list < 0) {
+    // deeper levels: slices of the entry point p + texit v, texit in [ts_lo, ts_hi]
+    int hh = -S.child - 1;
+#pragma unroll
+    for (int j = 0; j < kMaxLevels - 1; ++j) {
+      if (list < 0 && lstar + 1 + j < kMaxLevels) {
+        const DVoxHdr32 D = G.hdr32[hh];
+        float qlo, qhi;
+        if (!advance32(r, v, D.n_axis & 3, ts_lo, ts_hi, qlo, qhi)) return 2;
+        const int k = slice_of32(D, qlo, qhi);
+        if (k < 0) return 2;
+        const DVoxSlice Sd = G.slice[D.slice_base + k];
+        dh[j] = hh;
+        dk0[j] = Sd.k0;
+        dk1[j] = Sd.k1;
+        nd = j + 1;
+        if (Sd.child >= 0) list = Sd.child;
+        else hh = -Sd.child - 1;
+      }
+    }
+  }
+  ch.k0[lstar] = S.k0;
+  ch.k1[lstar] = S.k1;
+#pragma unroll
+  for (int j = 0; j < kMaxLevels - 1; ++j) {
+    if (j < nd) {
+      ch.h[lstar + 1 + j] = dh[j];
+      ch.k0[lstar + 1 + j] = dk0[j];
+      ch.k1[lstar + 1 + j] = dk1[j];
+    }
+  }
+  if (list >= 0) {
+    ch.nlev = lstar + 1 + nd;
+    ch.list = list;
+  } else {
+    ch.nlev = kMaxLevels;
+    ch.list = 0;
+  }
+  return 1;
 }
 
 // Training-sample log written by the plain navigator (features, label = list slot of the
@@ -983,12 +1244,26 @@ __device__ __forceinline__ void node_features(const DGeom &G, const DVol &V, con
   f[8] = 1.0f;
 }
 
+// A boundary search that yields after walking its budget of voxel nodes is continued in a
+// later round: from ray parameter t (at or before the entry of the first node not yet
+// searched) with the best daughter found so far and the safety bound of its first round.
+// Searching a node twice changes nothing (the minimum and its tie rule are idempotent).
+struct WalkResume {
+  double t;       // restart parameter along the ray
+  double best;    // best DistanceToIn found so far (+inf: none)
+  double safety;  // isotropic safety bound of the first round
+  int bl;         // the daughter of `best` (G4N_LIM_MOTHER: none)
+  int it;         // voxel nodes walked so far (the walk's iteration cap)
+};
+
 struct StepResult {
   double step;    // geometric step (exact when it is <= the limit)
   double safety;  // isotropic lower bound
   int lim;        // daughter id or G4N_LIM_MOTHER
   int face;       // limiter mother and a box leaf: the exit face (2 axis + (v_axis > 0)), else -1
   bool physics;   // FP32 mode: proven that the limit comes first (no FP64 geometry done)
+  bool yielded;   // the search used its node budget: continue it from `resume`
+  WalkResume resume;
 };
 
 // Geometric step inside `leaf` from local point p along v (Sec. 3.2, problem 2),
@@ -998,15 +1273,25 @@ struct StepResult {
 // mode: a candidate is evaluated in FP64 only if its FP32 entry bound does not
 // exceed the best exact distance so far, and no FP64 geometry at all is done when
 // the bounds prove that `limit` comes first.  Both return the FP64 result.
+//
+// Budget (budget > 0): after `budget` node steps a lane's search yields (R.yielded, with the
+// state to continue from in R.resume); `resume` continues such a search.  The result of a
+// search is the same whether or not it yields.
 template <int MODE, bool COUNT>
 __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active, int leaf, const V3 &p, const V3 &v,
                                                      const Inv3 &iv, double limit, bool want_safety, Counters &cnt,
-                                                     bool *timeout, const MlpCtx &mc) {
+                                                     bool *timeout, const MlpCtx &mc, bool resume = false,
+                                                     const WalkResume &from = WalkResume{0.0, kInf, 0.0, -1, 0},
+                                                     int budget = 0) {
   const double half = G.half;
-  StepResult R{kInf, 0.0, G4N_LIM_MOTHER, -1, false};
+  StepResult R{kInf, 0.0, G4N_LIM_MOTHER, -1, false, false, WalkResume{0.0, kInf, 0.0, -1, 0}};
+  int nodes = 0;          // node steps taken in this call (the budget)
+  double t_yield = 0.0;   // restart parameter when the search yields
   double best = kInf, stop = 0.0, tout = kInf;
   int oface = -1;
   float out_lo = 0.f;
+  float bound_f = kInfF;  // FP32 modes: float >= min(best, stop), the FP32 walk's bound
+  float saf_f = 0.f;      // FP32 modes: the isotropic safety bound
   Ray32 r;
   Chain ch;
   bool walking = false, first = true;
@@ -1021,21 +1306,33 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       r = make_ray32(p, v);
       float out_hi, saf32;
       exit_bounds32(V, r, p, &out_lo, &out_hi, &saf32);
-      R.safety = saf32;
+      saf_f = resume ? (float)from.safety : saf32;
       stop = fmin(limit, (double)out_hi);
     } else {
       diag<COUNT>(cnt, G4N_C_DIST_OUT);
       tout = vol_dist_out(V, p, v, iv, half, &oface);
-      R.safety = want_safety ? vol_safety_out(V, p) : 0.0;
+      R.safety = resume ? from.safety : (want_safety ? vol_safety_out(V, p) : 0.0);
       stop = fmin(limit, tout);
     }
+    if (resume) {
+      best = from.best;
+      bl = from.bl;
+      it = from.it;
+      first = false;
+    }
+    if (MODE != kFP64) bound_f = __double2float_ru(fmin(best, stop));
     if (V.vox >= 0) {
-      chain_fill(G, ch, 0, V.vox, p);
+      if (resume) {
+        const V3 q{p.x + from.t * v.x, p.y + from.t * v.y, p.z + from.t * v.z};
+        chain_fill(G, ch, 0, V.vox, q);
+      } else if (MODE == kFP64 || !chain_fill32(G, ch, V.vox, r)) {
+        chain_fill(G, ch, 0, V.vox, p);
+      }
       L = G.clist[ch.list];
       L0 = L;
       walking = true;
       diag<COUNT>(cnt, G4N_C_VOX_NODES);
-      if ((MODE == kLearned || mc.log) && L.count >= 2 && L.count <= mlp::kOut) {
+      if (!resume && (MODE == kLearned || mc.log) && L.count >= 2 && L.count <= mlp::kOut) {
         node_features(G, V, ch, p, v, mc.loge, L.count, feat);
         have_feat = true;
       }
@@ -1070,7 +1367,7 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
           const DBox32 B = G.box[c];
           const float iso = iso_lb32(G.v32[c], r.plo[0], r.plo[1], r.plo[2]) - (float)(2.0 * G.half);
           const float lb = fmaxf(box_entry_lb(B.lo, B.hi, r, nullptr), iso);
-          if ((double)lb <= fmin(best, stop)) {
+          if (lb <= bound_f) {
             d = c;
             from_first = true;
             break;
@@ -1083,10 +1380,10 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
           if (MODE != kFP64) {
             const DBox32 B = G.box[c];
             const float iso = iso_lb32(G.v32[c], r.plo[0], r.plo[1], r.plo[2]) - (float)(2.0 * G.half);
-            if (first && want_safety) R.safety = fmin(R.safety, (double)fmaxf(box_gap_lb(B.lo, B.hi, r), iso));
+            if (first && want_safety) saf_f = fminf(saf_f, fmaxf(box_gap_lb(B.lo, B.hi, r), iso));
             if (MODE == kLearned && first && i - 1 == prop_done) continue;  // already evaluated exactly
             const float lb = fmaxf(box_entry_lb(B.lo, B.hi, r, nullptr), iso);
-            if (!((double)lb <= fmin(best, stop))) {
+            if (!(lb <= bound_f)) {
               if (MODE == kLearned) diag<COUNT>(cnt, G4N_C_PRUNED);
               continue;
             }
@@ -1097,44 +1394,34 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
           break;
         }
         // list done: exit of the current node along the ray; its slab boundaries bound the safety
-        double texit = kInf;
-        int lstar = -1;
-#pragma unroll 1
-        for (int l = 0; l < ch.nlev; ++l) {
-          const DVoxHdr H = G.hdr[ch.h[l]];
-          const double pa = comp(p, H.axis), va = comp(v, H.axis);
-          const double blo = H.lo + ch.k0[l] * H.width, bhi = H.lo + (ch.k1[l] + 1) * H.width;
-          if (first && want_safety) R.safety = fmin(R.safety, fmax(fmin(pa - blo, bhi - pa), 0.0));
-          double t = kInf;
-          if (va > 0.0) t = (bhi - pa) * icomp(iv, H.axis);
-          else if (va < 0.0) t = (blo - pa) * icomp(iv, H.axis);
-          if (t < texit) {
-            texit = t;
-            lstar = l;
+        int w = 2;
+        double t_next = 0.0;  // at or before the entry of the node stepped into
+        if (MODE != kFP64) {
+          float tl32 = 0.f;
+          w = walk_step32(G, ch, r, v, bound_f, first && want_safety, &saf_f, &it, timeout, &tl32);
+          t_next = (double)tl32;
+        }
+        if (w == 2) {
+          // FP64 node step (the FP32 modes come here only when the intervals do not decide)
+          if (MODE == kFP64) {
+            w = walk_step64(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &R.safety, &it, timeout, &t_next);
+          } else {
+            double s64 = kInf;
+            w = walk_step64_ool(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &s64, &it, timeout, &t_next);
+            saf_f = fminf(saf_f, __double2float_rd(s64));
           }
         }
         first = false;
-        if (!(texit < fmin(best, stop))) {
+        if (w == 0) {
           walking = false;
           break;
         }
-        // step into the neighbouring node at level lstar; deeper levels are looked up again
-        const DVoxHdr H = G.hdr[ch.h[lstar]];
-        const int nk = comp(v, H.axis) > 0.0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
-        if (nk < 0 || nk >= H.nslices || ++it >= (1 << 16)) {
-          if (it >= (1 << 16)) *timeout = true;
+        if (budget > 0 && ++nodes >= budget) {
+          // yield: the search continues in a later round from t_next
           walking = false;
+          R.yielded = true;
+          t_yield = t_next;
           break;
-        }
-        const DVoxSlice S = G.slice[H.slice_base + nk];
-        ch.k0[lstar] = S.k0;
-        ch.k1[lstar] = S.k1;
-        if (S.child >= 0) {
-          ch.nlev = lstar + 1;
-          ch.list = S.child;
-        } else {
-          const V3 qpt{p.x + texit * v.x, p.y + texit * v.y, p.z + texit * v.z};
-          chain_fill(G, ch, lstar + 1, -S.child - 1, qpt);
         }
         L = G.clist[ch.list];
         i = 0;
@@ -1156,11 +1443,17 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       if (t < kInf && (t < best || (t == best && (bl < 0 || d < bl)))) {
         best = t;
         bl = d;
+        if (MODE != kFP64) bound_f = __double2float_ru(fmin(best, stop));
       }
       if (MODE == kFP64 && from_first && want_safety) R.safety = fmin(R.safety, vol_safety_in(D, dp));
     }
   }
+  if (MODE != kFP64) R.safety = saf_f;
   if (!active) return R;
+  if (R.yielded) {
+    R.resume = WalkResume{t_yield, best, R.safety, bl, it};
+    return R;
+  }
   if (MODE == kFP64 && mc.log && have_feat && bl >= 0 && best <= tout) {
     // training sample: the daughter entered, if it is listed in the first node
     int slot = -1;

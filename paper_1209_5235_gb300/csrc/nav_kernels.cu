@@ -162,7 +162,10 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
 
 // ---------------------------------------------------------------- transport
 
-enum Phase : int { kEmpty = 0, kStep = 1, kInteract = 2 };
+enum Phase : int { kEmpty = 0, kStep = 1, kInteract = 2, kWalk = 3 };  // kWalk: a yielded boundary search
+
+// Voxel nodes a boundary search walks per round before it yields (walk_budget = 0).
+constexpr int kDefaultWalkBudget = 8;
 
 struct Track {
   V3 x, u;
@@ -172,6 +175,7 @@ struct Track {
   int64_t tid, gidx;
   int leaf, item, steps, nzero, ebin;
   uint32_t draw;
+  WalkResume w;      // phase kWalk: the yielded boundary search of the current step
 };
 
 struct TParams {
@@ -192,6 +196,7 @@ struct TParams {
   double *out_len;
   int refill_min;    // refill a warp's idle lanes once at least this many are idle
   int interact_min;  // run the interaction phase once at least this many lanes wait for it
+  int walk_budget;   // voxel nodes a boundary search walks per round before it yields
   const mlp::SmemWeights *mlp_w;  // learned mode: weights (device image)
   const MlpLog *log;              // plain mode: training-sample log (null: none)
 };
@@ -299,7 +304,7 @@ __device__ __forceinline__ void set_direction(Track &t, const V3 &u) {
 // Start track number g of the concatenated items on the lanes with `active` set
 // (warp-collective: locate runs across the warp).  Returns the new phase of the
 // lane: kStep, or kEmpty if the track ended at once (or the lane was not active).
-template <bool COUNT>
+template <int MODE, bool COUNT>
 __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Counters &cnt) {
   const DGeom *Gp = &P.geoms[P.items[0].geom];
   if (active) {
@@ -322,7 +327,7 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
     t.E = E;
   }
   const DGeom &G = *Gp;
-  const int leaf = locate_world_warp<COUNT>(G, active, t.x, t.u, cnt);
+  const int leaf = locate_world_warp<COUNT, MODE != kFP64>(G, active, t.x, t.u, cnt);
   if (!active) return kEmpty;
   t.leaf = leaf;
   if (leaf < 0) {
@@ -406,10 +411,11 @@ __device__ __forceinline__ V3 deflect(const V3 &u, double ct, double cph, double
 // Returns the lane's next phase.
 template <int MODE, bool COUNT>
 __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, MlpCtx mc) {
-  bool act = phase == kStep;
+  const bool resume = phase == kWalk;  // continue the step's yielded boundary search
+  bool act = phase == kStep || resume;
   const DGeom &G = P.geoms[P.items[act ? t.item : 0].geom];
   int next = phase;
-  if (act && t.steps >= P.max_steps) {
+  if (act && !resume && t.steps >= P.max_steps) {
     cnt.c[G4N_C_STEP_LIMIT]++;
     flag(P.status, kStStepLimit);
     t.h = hash_step(t.h, t.leaf, kLimStepLimit, kEvStepLimit);
@@ -432,7 +438,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     lazy = MODE == kFP64 && mu_pos && !mc.log;
     if (!lazy) sphys = mu_pos ? t.Y / t.mu : kInf;
     // a zero safety (after every boundary crossing) always needs the boundary search
-    need_geo = !nonzero_bits(t.safety) || (lazy ? !(t.Y < t.safety * t.mu) : !(sphys < t.safety));
+    need_geo = resume || !nonzero_bits(t.safety) || (lazy ? !(t.Y < t.safety * t.mu) : !(sphys < t.safety));
     want_saf = !(MODE == kFP64 && L.vox < 0);
     if (!need_geo) {
       diag<COUNT>(cnt, G4N_C_SAFETY_SKIPS);
@@ -450,8 +456,16 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   }
   bool timeout = false;
   if (MODE == kLearned || mc.log) mc.loge = act ? (logf((float)t.E) + 4.6f) * 0.1f : 0.f;
+  // the learned proposal and the sample log look at the first node only: no yielding there
+  const int budget = (MODE == kLearned || mc.log) ? 0 : P.walk_budget;
   const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, lim_geo, want_saf,
-                                                   cnt, &timeout, mc);
+                                                   cnt, &timeout, mc, resume, t.w, budget);
+  if (act && R.yielded) {
+    // the search used its node budget: the step continues in a later round
+    t.w = R.resume;
+    next = kWalk;
+    act = false;
+  }
   bool geo = false;
   double s = sphys;
   int lim = G4N_LIM_PHYSICS;
@@ -490,27 +504,33 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   const bool left = geo && lim == G4N_LIM_MOTHER && s > 0.0;
   const bool fast = left && face_relocate(G, t.leaf, R.face, t.x, t.u, &leaf);
   if (fast) diag<COUNT>(cnt, G4N_C_FACE_RELOC);
-  const int searched = relocate_warp<MODE, COUNT>(G, geo && !fast, geo && !fast ? t.leaf : 0, t.x, t.u, left, cnt);
-  if (!fast) leaf = searched;
-  bool pushing = false;
-  if (geo) {
-    t.nzero = (dkey(s) <= dkey(G.half)) ? t.nzero + 1 : 0;
-    if (leaf >= 0 && t.nzero >= 10) {
-      const double push = 100.0 * G.tol;
-      t.x.x += push * t.u.x;
-      t.x.y += push * t.u.y;
-      t.x.z += push * t.u.z;
-      t.len += push;
-      cnt.c[G4N_C_PUSHES]++;
-      t.nzero = 0;
-      pushing = true;
+  // relocation search, then (after 10 zero steps) the push and its relocation: one copy of
+  // the relocation code serves both passes
+  bool need = geo && !fast, from_left = left, pushing = false;
+  int from = t.leaf;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int found = relocate_warp<MODE, COUNT>(G, need, need ? from : 0, t.x, t.u, from_left, cnt);
+    if (need) leaf = found;
+    need = false;
+    if (pass == 0 && geo) {
+      t.nzero = (dkey(s) <= dkey(G.half)) ? t.nzero + 1 : 0;
+      if (leaf >= 0 && t.nzero >= 10) {
+        const double push = 100.0 * G.tol;
+        t.x.x += push * t.u.x;
+        t.x.y += push * t.u.y;
+        t.x.z += push * t.u.z;
+        t.len += push;
+        cnt.c[G4N_C_PUSHES]++;
+        t.nzero = 0;
+        pushing = need = true;
+        from = leaf;
+        from_left = false;
+      }
     }
+    if (!__any_sync(kFull, need)) break;
   }
-  const int pushed = relocate_warp<MODE, COUNT>(G, pushing, pushing ? leaf : 0, t.x, t.u, false, cnt);
-  if (pushing) {
-    leaf = pushed;
-    t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
-  }
+  if (pushing) t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
   if (geo) {
     if (leaf < 0) {
       cnt.c[G4N_C_ESCAPED]++;
@@ -612,18 +632,18 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
       if (base + __popc(idle) >= (unsigned long long)P.total) drained = true;
       const int64_t g = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
       const bool take = phase == kEmpty && g < P.total;
-      const int started = start_warp<COUNT>(P, take, g, t, cnt);
+      const int started = start_warp<MODE, COUNT>(P, take, g, t, cnt);
       if (take) phase = started;
     }
     const unsigned waiting = __ballot_sync(0xffffffffu, phase == kInteract);
-    const unsigned stepping = __ballot_sync(0xffffffffu, phase == kStep);
+    const unsigned stepping = __ballot_sync(0xffffffffu, phase == kStep || phase == kWalk);
     const long long c1 = COUNT ? clock64() : 0;
     if (waiting && (__popc(waiting) >= P.interact_min || stepping == 0)) {
       if (phase == kInteract) phase = interact<MODE>(P, t, cnt);
     }
     __syncwarp();
     const long long c2 = COUNT ? clock64() : 0;
-    const unsigned stepping2 = __ballot_sync(0xffffffffu, phase == kStep);
+    const unsigned stepping2 = __ballot_sync(0xffffffffu, phase == kStep || phase == kWalk);
     phase = step_warp<MODE, COUNT>(P, t, phase, cnt, mc);
     if (COUNT) {
       __syncwarp();
@@ -858,8 +878,10 @@ int launch_error(g4n_ctx *ctx, const char *what) {
 }
 
 // Launch shape of a transport batch (validated); 0 fields take the defaults.
-int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refill, int *inter) {
+int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refill, int *inter, int *budget) {
   *block = b->block_size > 0 ? b->block_size : 128;
+  if (b->walk_budget < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: walk_budget must be >= 0");
+  *budget = b->walk_budget > 0 ? std::min(b->walk_budget, 1 << 20) : kDefaultWalkBudget;
   if (*block % 32 || *block > 128) return g4n_fail(ctx, G4N_ERR_ARG, "transport: block_size must be a multiple of 32, <= 128");
   *refill = b->refill_min > 0 ? b->refill_min : 8;
   *inter = b->interact_min > 0 ? b->interact_min : 8;
@@ -988,8 +1010,8 @@ static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_ede
   if (!ctx || !b) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null argument");
   if (b->n_items < 1 || !b->items) return g4n_fail(ctx, G4N_ERR_ARG, "transport: no work items");
   if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null output");
-  int block, refill, inter;
-  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter)) return rc0;
+  int block, refill, inter, budget;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget)) return rc0;
   if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport: n_tally_batches < 1");
   if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: cutoff must be >= 0");
   std::vector<DItem> items;
@@ -1023,6 +1045,7 @@ static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_ede
   P.out_len = out_track_len;
   P.refill_min = refill;
   P.interact_min = inter;
+  P.walk_budget = budget;
   P.log = logging ? &ws->log : nullptr;
   return launch_transport(ctx, b, P, block, st);
 }
@@ -1224,8 +1247,8 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: more than G4N_NOALLOC_MAX_ITEMS (" +
                                           std::to_string(G4N_NOALLOC_MAX_ITEMS) + ") work items; use g4n_transport_batch");
   if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: null output");
-  int block, refill, inter;
-  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter)) return rc0;
+  int block, refill, inter, budget;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget)) return rc0;
   if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: n_tally_batches < 1");
   if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: cutoff must be >= 0");
   DItem items[G4N_NOALLOC_MAX_ITEMS];  // host staging on the stack: no heap either
@@ -1289,6 +1312,7 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     P.out_len = out_track_len;
     P.refill_min = refill;
     P.interact_min = inter;
+    P.walk_budget = budget;
     P.log = nullptr;
     rc = launch_transport(ctx, b, P, block, st);
     if (rc) return rc;
@@ -1326,8 +1350,8 @@ int g4n_graph_create(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, ui
   *out = nullptr;
   if (ctx->device < 0) return g4n_fail(ctx, G4N_ERR_STATE, "host-only context: no device queries");
   if (b->n_items < 1 || !b->items || !out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "graph_create: no items or outputs");
-  int block, refill, inter;
-  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter)) return rc0;
+  int block, refill, inter, budget;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget)) return rc0;
   if (b->n_tally_batches < 1 || !(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "graph_create: bad tallies or cutoff");
   std::vector<DItem> items;
   int64_t total = 0;
@@ -1367,6 +1391,7 @@ int g4n_graph_create(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, ui
   P.out_len = out_track_len;
   P.refill_min = refill;
   P.interact_min = inter;
+  P.walk_budget = budget;
   P.log = nullptr;
   P.mlp_w = g4n_mlp_image(ctx);
   const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
