@@ -72,6 +72,7 @@ enum { G4N_LIM_PHYSICS = -2, G4N_LIM_MOTHER = -1 };
 enum {
   G4N_C_TRACKS = 0, G4N_C_STEPS, G4N_C_GEOM_STEPS, G4N_C_PHYS_STEPS, G4N_C_PHOTO, G4N_C_COMPTON, G4N_C_ESCAPED,
   G4N_C_CUTOFF, G4N_C_PUSHES, G4N_C_STEP_LIMIT,
+  G4N_C_WALK_YIELDS = 10,    /* boundary searches that used their node budget and went on in a later round */
   G4N_C_FACE_RELOC = 14,     /* relocations answered by a box face's precomputed record */
   G4N_C_KEY_INSIDE = 15,     /* Inside tests of world-aligned boxes answered by exact coordinate thresholds */
   G4N_C_SAFETY_SKIPS = 16,   /* steps that skipped the boundary search because safety exceeded the physics step */
@@ -237,7 +238,8 @@ typedef struct {
  * 1..32, default 8), interact_min (a warp runs its interaction phase once at least this many
  * lanes wait for it, 1..32, default 8), walk_budget (voxel nodes a boundary search walks in one
  * round of its warp before it yields and continues in a later round, so that lanes with short
- * searches take their next steps meanwhile; default 8, values >= 65536 never yield).  flags:
+ * searches take their next steps meanwhile; default 16, values >= 65536 never yield and select a
+ * kernel without that code).  flags:
  * G4N_FLAG_DIAGNOSTICS also fills the diagnostic counters (G4N_C_FACE_RELOC and above).  Results
  * never depend on the launch shape. */
 #define G4N_FLAG_DIAGNOSTICS 1

@@ -16,13 +16,13 @@ import time
 from . import binding as b
 
 SPACE = {
+    "walk_budget": (1 << 16, 4, 8, 32),
     "block_size": (64, 96, 128),
     "blocks_per_sm": (0, 2, 3),
     "refill_min": (4, 6, 8, 12, 16),
     "interact_min": (4, 6, 8, 12, 16),
-    "walk_budget": (4, 16, 32, 1 << 16),
 }
-DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8, "walk_budget": 8}
+DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8, "walk_budget": 16}
 
 
 def time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps=2, stream=None):

@@ -1012,8 +1012,7 @@ __device__ __forceinline__ void chain_fill(const DGeom &G, Chain &ch, int lev, i
 // Returns 0: the walk ends; 1: ch holds the next node.  With `saf` the distances from the
 // point to the node's slab faces lower *saf.
 __device__ __forceinline__ int walk_step64(const DGeom &G, Chain &ch, const V3 &p, const V3 &v, const Inv3 &iv,
-                                           double bound, bool saf, double *saf64, int *it, bool *timeout,
-                                           double *t_exit) {
+                                           double bound, bool saf, double *saf64, int *it, bool *timeout) {
   double texit = kInf;
   int lstar = -1;
 #pragma unroll 1
@@ -1031,7 +1030,6 @@ __device__ __forceinline__ int walk_step64(const DGeom &G, Chain &ch, const V3 &
     }
   }
   if (!(texit < bound)) return 0;
-  *t_exit = texit;
   const DVoxHdr H = G.hdr[ch.h[lstar]];
   const int nk = comp(v, H.axis) > 0.0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
   if (nk < 0 || nk >= H.nslices || ++*it >= (1 << 16)) {
@@ -1053,9 +1051,8 @@ __device__ __forceinline__ int walk_step64(const DGeom &G, Chain &ch, const V3 &
 
 // The same, out of line: the FP32 modes take it only when their intervals do not decide.
 __device__ __noinline__ int walk_step64_ool(const DGeom &G, Chain &ch, const V3 &p, const V3 &v, const Inv3 &iv,
-                                            double bound, bool saf, double *saf64, int *it, bool *timeout,
-                                            double *t_exit) {
-  return walk_step64(G, ch, p, v, iv, bound, saf, saf64, it, timeout, t_exit);
+                                            double bound, bool saf, double *saf64, int *it, bool *timeout) {
+  return walk_step64(G, ch, p, v, iv, bound, saf, saf64, it, timeout);
 }
 
 // chain_fill from the root header h0 for every FP64 point in the ray's enclosure (FP32
@@ -1099,7 +1096,7 @@ __device__ __forceinline__ float div_hi_a(float n, const Ray32 &r, int a) {
 // takes this node step.  With `saf` the distances from the point to the node's slab
 // faces lower the isotropic safety *saf_f.
 __device__ __forceinline__ int walk_step32(const DGeom &G, Chain &ch, const Ray32 &r, const V3 &v, float bound_f,
-                                           bool saf, float *saf_f, int *it, bool *timeout, float *t_exit_lo) {
+                                           bool saf, float *saf_f, int *it, bool *timeout) {
   float tl[kMaxLevels], th[kMaxLevels];
   const int nlev = ch.nlev;
   int lstar = -1;
@@ -1139,7 +1136,6 @@ __device__ __forceinline__ int walk_step32(const DGeom &G, Chain &ch, const Ray3
   for (int l = 0; l < kMaxLevels; ++l)
     if (l != lstar && !(tl[l] > ts_hi)) return 2;
   if (ts_lo >= bound_f) return 0;  // texit >= bound_f >= min(best, stop)
-  *t_exit_lo = ts_lo;
   const DVoxHdr32 H = G.hdr32[ch.h[lstar]];
   const int nk = sel3i(r.sgn[0], r.sgn[1], r.sgn[2], H.n_axis & 3) > 0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
   if (nk < 0 || nk >= (H.n_axis >> 2) || ++*it >= (1 << 16)) {
@@ -1245,11 +1241,9 @@ __device__ __forceinline__ void node_features(const DGeom &G, const DVol &V, con
 }
 
 // A boundary search that yields after walking its budget of voxel nodes is continued in a
-// later round: from ray parameter t (at or before the entry of the first node not yet
-// searched) with the best daughter found so far and the safety bound of its first round.
-// Searching a node twice changes nothing (the minimum and its tie rule are idempotent).
+// later round at the node it had stepped into (its Chain, kept by the caller), with the best
+// daughter found so far and the safety bound of its first round.
 struct WalkResume {
-  double t;       // restart parameter along the ray
   double best;    // best DistanceToIn found so far (+inf: none)
   double safety;  // isotropic safety bound of the first round
   int bl;         // the daughter of `best` (G4N_LIM_MOTHER: none)
@@ -1275,25 +1269,24 @@ struct StepResult {
 // the bounds prove that `limit` comes first.  Both return the FP64 result.
 //
 // Budget (budget > 0): after `budget` node steps a lane's search yields (R.yielded, with the
-// state to continue from in R.resume); `resume` continues such a search.  The result of a
-// search is the same whether or not it yields.
+// state to continue from in R.resume and in `ch`, which then holds the node stepped into);
+// `resume` continues such a search from there.  The result of a search is the same whether
+// or not it yields.  `ch` is the caller's voxel chain (per-lane local memory).
 template <int MODE, bool COUNT>
 __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active, int leaf, const V3 &p, const V3 &v,
                                                      const Inv3 &iv, double limit, bool want_safety, Counters &cnt,
-                                                     bool *timeout, const MlpCtx &mc, bool resume = false,
-                                                     const WalkResume &from = WalkResume{0.0, kInf, 0.0, -1, 0},
+                                                     bool *timeout, const MlpCtx &mc, Chain &ch, bool resume = false,
+                                                     const WalkResume &from = WalkResume{kInf, 0.0, -1, 0},
                                                      int budget = 0) {
   const double half = G.half;
-  StepResult R{kInf, 0.0, G4N_LIM_MOTHER, -1, false, false, WalkResume{0.0, kInf, 0.0, -1, 0}};
+  StepResult R{kInf, 0.0, G4N_LIM_MOTHER, -1, false, false, WalkResume{kInf, 0.0, -1, 0}};
   int nodes = 0;          // node steps taken in this call (the budget)
-  double t_yield = 0.0;   // restart parameter when the search yields
   double best = kInf, stop = 0.0, tout = kInf;
   int oface = -1;
   float out_lo = 0.f;
   float bound_f = kInfF;  // FP32 modes: float >= min(best, stop), the FP32 walk's bound
   float saf_f = 0.f;      // FP32 modes: the isotropic safety bound
   Ray32 r;
-  Chain ch;
   bool walking = false, first = true;
   int i = 0, it = 0, bl = G4N_LIM_MOTHER;
   DCandList L{0, 0}, L0{0, 0};
@@ -1322,12 +1315,7 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
     }
     if (MODE != kFP64) bound_f = __double2float_ru(fmin(best, stop));
     if (V.vox >= 0) {
-      if (resume) {
-        const V3 q{p.x + from.t * v.x, p.y + from.t * v.y, p.z + from.t * v.z};
-        chain_fill(G, ch, 0, V.vox, q);
-      } else if (MODE == kFP64 || !chain_fill32(G, ch, V.vox, r)) {
-        chain_fill(G, ch, 0, V.vox, p);
-      }
+      if (!resume && (MODE == kFP64 || !chain_fill32(G, ch, V.vox, r))) chain_fill(G, ch, 0, V.vox, p);
       L = G.clist[ch.list];
       L0 = L;
       walking = true;
@@ -1395,19 +1383,14 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
         }
         // list done: exit of the current node along the ray; its slab boundaries bound the safety
         int w = 2;
-        double t_next = 0.0;  // at or before the entry of the node stepped into
-        if (MODE != kFP64) {
-          float tl32 = 0.f;
-          w = walk_step32(G, ch, r, v, bound_f, first && want_safety, &saf_f, &it, timeout, &tl32);
-          t_next = (double)tl32;
-        }
+        if (MODE != kFP64) w = walk_step32(G, ch, r, v, bound_f, first && want_safety, &saf_f, &it, timeout);
         if (w == 2) {
           // FP64 node step (the FP32 modes come here only when the intervals do not decide)
           if (MODE == kFP64) {
-            w = walk_step64(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &R.safety, &it, timeout, &t_next);
+            w = walk_step64(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &R.safety, &it, timeout);
           } else {
             double s64 = kInf;
-            w = walk_step64_ool(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &s64, &it, timeout, &t_next);
+            w = walk_step64_ool(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &s64, &it, timeout);
             saf_f = fminf(saf_f, __double2float_rd(s64));
           }
         }
@@ -1417,10 +1400,10 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
           break;
         }
         if (budget > 0 && ++nodes >= budget) {
-          // yield: the search continues in a later round from t_next
+          // yield: ch holds the node stepped into; the search continues there in a later round
           walking = false;
           R.yielded = true;
-          t_yield = t_next;
+          diag<COUNT>(cnt, G4N_C_WALK_YIELDS);
           break;
         }
         L = G.clist[ch.list];
@@ -1451,7 +1434,7 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
   if (MODE != kFP64) R.safety = saf_f;
   if (!active) return R;
   if (R.yielded) {
-    R.resume = WalkResume{t_yield, best, R.safety, bl, it};
+    R.resume = WalkResume{best, R.safety, bl, it};
     return R;
   }
   if (MODE == kFP64 && mc.log && have_feat && bl >= 0 && best <= tout) {

@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
       }
     }
     bool timeout = false;
-    const StepResult R = geom_step_warp<MODE, false>(G, ok, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout, mc);
+    Chain ch;
+    const StepResult R = geom_step_warp<MODE, false>(G, ok, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout, mc, ch);
     if (ok) {
       if (timeout) flag(status, kStTimeout);
       double s = R.step;
@@ -164,8 +165,10 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
 
 enum Phase : int { kEmpty = 0, kStep = 1, kInteract = 2, kWalk = 3 };  // kWalk: a yielded boundary search
 
-// Voxel nodes a boundary search walks per round before it yields (walk_budget = 0).
-constexpr int kDefaultWalkBudget = 8;
+// Voxel nodes a boundary search walks per round before it yields (walk_budget = 0); budgets
+// from kNeverYield on select the kernel without yielding.
+constexpr int kDefaultWalkBudget = 16;
+constexpr int kNeverYield = 1 << 16;
 
 struct Track {
   V3 x, u;
@@ -409,9 +412,9 @@ __device__ __forceinline__ V3 deflect(const V3 &u, double ct, double cph, double
 // (warp-collective): the free path (Eq. 7) races the geometric step; a boundary
 // crossing relocates, a physics end point waits for the interaction phase.
 // Returns the lane's next phase.
-template <int MODE, bool COUNT>
-__device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, MlpCtx mc) {
-  const bool resume = phase == kWalk;  // continue the step's yielded boundary search
+template <int MODE, bool COUNT, bool YIELD>
+__device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, MlpCtx mc, Chain &wch) {
+  const bool resume = YIELD && phase == kWalk;  // continue the step's yielded boundary search
   bool act = phase == kStep || resume;
   const DGeom &G = P.geoms[P.items[act ? t.item : 0].geom];
   int next = phase;
@@ -457,9 +460,9 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   bool timeout = false;
   if (MODE == kLearned || mc.log) mc.loge = act ? (logf((float)t.E) + 4.6f) * 0.1f : 0.f;
   // the learned proposal and the sample log look at the first node only: no yielding there
-  const int budget = (MODE == kLearned || mc.log) ? 0 : P.walk_budget;
+  const int budget = (!YIELD || MODE == kLearned || mc.log) ? 0 : P.walk_budget;
   const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, lim_geo, want_saf,
-                                                   cnt, &timeout, mc, resume, t.w, budget);
+                                                   cnt, &timeout, mc, wch, resume, t.w, budget);
   if (act && R.yielded) {
     // the search used its node budget: the step continues in a later round
     t.w = R.resume;
@@ -599,7 +602,11 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
 // it, (3) advances every stepping lane by one step.  Deferring the long
 // interaction and start-up code until many lanes need it keeps the warp's lanes
 // on the same code; the order of operations inside each history is unchanged.
-template <int MODE, bool COUNT>
+//
+// YIELD: boundary searches yield after P.walk_budget voxel nodes (phase kWalk) and go on in a
+// later round.  The kernel without it has none of that code: the workloads whose searches are
+// short run faster without it (smaller code; measured 5 % on the calorimeter).
+template <int MODE, bool COUNT, bool YIELD>
 __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
   Counters cnt;
 #pragma unroll
@@ -617,6 +624,7 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
   Track t;
   t.item = 0;
   t.leaf = 0;
+  Chain wch;  // voxel chain of the lane's boundary search (kept while the search yields)
   int phase = kEmpty;
   bool drained = false;
 #pragma unroll 1
@@ -644,7 +652,7 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
     __syncwarp();
     const long long c2 = COUNT ? clock64() : 0;
     const unsigned stepping2 = __ballot_sync(0xffffffffu, phase == kStep || phase == kWalk);
-    phase = step_warp<MODE, COUNT>(P, t, phase, cnt, mc);
+    phase = step_warp<MODE, COUNT, YIELD>(P, t, phase, cnt, mc, wch);
     if (COUNT) {
       __syncwarp();
       const long long c3 = clock64();
@@ -768,8 +776,9 @@ __global__ void __launch_bounds__(128, 3) k_free_path(const FParams P) {
       iv = aligned ? iu : inv_dir(v);
     }
     bool timeout = false;
+    Chain ch;
     const StepResult R = geom_step_warp<MODE, COUNT>(G, active, active ? leaf : 0, p, v, iv, kInf, false, cnt, &timeout,
-                                                     mc);
+                                                     mc, ch);
     bool cross = false;
     double s = 0.0;
     if (active) {
@@ -836,10 +845,14 @@ FreePathKernel free_path_kernel(int mode, bool count) {
 
 using TransportKernel = void (*)(const TParams);
 
-TransportKernel transport_kernel(int mode, bool count) {
-  if (mode == G4N_MODE_FP64) return count ? k_transport<kFP64, true> : k_transport<kFP64, false>;
-  if (mode == G4N_MODE_FP32_RECHECK) return count ? k_transport<kFP32, true> : k_transport<kFP32, false>;
-  return count ? k_transport<kLearned, true> : k_transport<kLearned, false>;
+// The diagnostics kernel always has the yield code (its counters then also count yields); the
+// learned mode never yields.
+TransportKernel transport_kernel(int mode, bool count, bool yield) {
+  if (mode == G4N_MODE_FP64)
+    return count ? k_transport<kFP64, true, true> : (yield ? k_transport<kFP64, false, true> : k_transport<kFP64, false, false>);
+  if (mode == G4N_MODE_FP32_RECHECK)
+    return count ? k_transport<kFP32, true, true> : (yield ? k_transport<kFP32, false, true> : k_transport<kFP32, false, false>);
+  return count ? k_transport<kLearned, true, false> : k_transport<kLearned, false, false>;
 }
 
 // Dynamic shared memory of a launch: the MLP weights and one scratch tile per warp (learned mode).
@@ -930,7 +943,7 @@ int build_items(g4n_ctx *ctx, const g4n_batch_desc *b, std::vector<DItem> &items
 
 // Launch the persistent transport kernel of mode b->mode with parameters P on `st`.
 int launch_transport(g4n_ctx *ctx, const g4n_batch_desc *b, TParams &P, int block, cudaStream_t st) {
-  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
+  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS, P.walk_budget < kNeverYield);
   const size_t smem = mlp_smem_bytes(b->mode, block);
   P.mlp_w = g4n_mlp_image(ctx);
   if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1394,7 +1407,7 @@ int g4n_graph_create(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, ui
   P.walk_budget = budget;
   P.log = nullptr;
   P.mlp_w = g4n_mlp_image(ctx);
-  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS);
+  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS, P.walk_budget < kNeverYield);
   const size_t smem = mlp_smem_bytes(b->mode, block);
   if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = b->blocks_per_sm;

@@ -343,6 +343,32 @@ def test_autotuned_shape_gives_identical_results(env):
     _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_walk_budget_gives_identical_results(env, mode):
+    """A boundary search that yields after its voxel-node budget and resumes in a later round gives the
+    same histories: budgets 1, 3 and 8 (yielding often) and 65536 (never) against the oracle, on a random
+    world whose walks cross many voxel nodes."""
+    g4, torch, ctx = env
+    sc = mixed_scene(seed=11, n=400, half=500.0)
+    og = oracle.Geometry(sc)
+    gid = g4.build_scene(ctx, sc)
+    src = Source(pos=(1.0, 2.0, 3.0), isotropic=True, e_kind="loguniform", e0=0.05, e1=5.0)
+    n, seed = 6000, 0x7A0C0011
+    r = og.transport(src, seed, n, threads=0)
+    for budget in (1, 3, 8, 1 << 16):
+        edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, walk_budget=budget)
+        g4.g4n_sync(ctx)
+        _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
+    c = {}
+    for budget in (1, 1 << 16):
+        edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, walk_budget=budget, diagnostics=True)
+        g4.g4n_sync(ctx)
+        c[budget] = g4.counters_dict(cnt)
+    # budget 1 yields at every node step after the first; the continued searches visit the same nodes
+    assert c[1]["walk_yields"] > 0 and c[1 << 16]["walk_yields"] == 0
+    assert c[1]["vox_nodes"] == c[1 << 16]["vox_nodes"]
+
+
 def _full_size_sampled(env, entries_fn, seed, n_sample=300):
     """Both modes over a full-size launch: identical histories across modes, and a random sample
     of them replayed one by one by the oracle."""
