@@ -239,7 +239,9 @@ typedef struct {
  * lanes wait for it, 1..32, default 8), walk_budget (voxel nodes a boundary search walks in one
  * round of its warp before it yields and continues in a later round, so that lanes with short
  * searches take their next steps meanwhile; default 16, values >= 65536 never yield and select a
- * kernel without that code).  flags:
+ * kernel without that code), regroup_period (0 = off: every that many rounds each thread block
+ * sorts its tracks by phase and solid kind of the leaf and deals them out again, so that each
+ * warp runs one kind of work; FP64 and FP32_RECHECK modes without diagnostics).  flags:
  * G4N_FLAG_DIAGNOSTICS also fills the diagnostic counters (G4N_C_FACE_RELOC and above).  Results
  * never depend on the launch shape. */
 #define G4N_FLAG_DIAGNOSTICS 1
@@ -258,6 +260,7 @@ typedef struct {
   int32_t interact_min;
   int32_t flags;
   int32_t walk_budget;
+  int32_t regroup_period;
 } g4n_batch_desc;
 
 /* Transport every track of the batch (Algorithm 2, phase 5).  out_edep: n_tally_batches x

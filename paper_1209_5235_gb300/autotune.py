@@ -1,8 +1,8 @@
 """Launch-shape autotuner of the persistent transport kernel.
 
 Results never depend on the launch shape (block size, blocks per SM, the warp
-refill and interaction thresholds, the voxel-walk budget per round) or on the
-precision mode, only speed does.
+refill and interaction thresholds, the voxel-walk budget per round, the period of
+block-wide regrouping) or on the precision mode, only speed does.
 The tuner times trial launches of the caller's batch with CUDA events and walks
 one parameter at a time from the defaults, keeping any value that is faster
 (coordinate descent), within a time budget.  It only calls the C ABI through the
@@ -17,12 +17,14 @@ from . import binding as b
 
 SPACE = {
     "walk_budget": (1 << 16, 4, 8, 32),
+    "regroup_period": (1, 2, 4),
     "block_size": (64, 96, 128),
     "blocks_per_sm": (0, 2, 3),
     "refill_min": (4, 6, 8, 12, 16),
     "interact_min": (4, 6, 8, 12, 16),
 }
-DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8, "walk_budget": 16}
+DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8, "walk_budget": 16,
+           "regroup_period": 0}
 
 
 def time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps=2, stream=None):

@@ -80,7 +80,7 @@ class g4n_batch_desc(ctypes.Structure):
                 ("cutoff", ctypes.c_double), ("mode", ctypes.c_int32), ("n_tally_batches", ctypes.c_int32),
                 ("tally_stride", ctypes.c_int64), ("max_steps", ctypes.c_int64), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("refill_min", ctypes.c_int32), ("interact_min", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("walk_budget", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("walk_budget", ctypes.c_int32), ("regroup_period", ctypes.c_int32)]
 
 
 _lib = None
@@ -342,7 +342,7 @@ def make_items(entries) -> "ctypes.Array":
 
 
 def _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, refill_min=0,
-          interact_min=0, diagnostics=False, walk_budget=0):
+          interact_min=0, diagnostics=False, walk_budget=0, regroup_period=0):
     d = g4n_batch_desc()
     d.n_items = len(items)
     d.items = ctypes.cast(items, ctypes.POINTER(g4n_work_item))
@@ -356,17 +356,18 @@ def _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, b
     d.refill_min, d.interact_min = int(refill_min), int(interact_min)
     d.flags = G4N_FLAG_DIAGNOSTICS if diagnostics else 0
     d.walk_budget = int(walk_budget)
+    d.regroup_period = int(regroup_period)
     return d
 
 
 def g4n_transport_batch(ctx, items, seed: int, edep, counters, track_hash=None, track_len=None, cutoff: float = 0.01,
                         mode: int = G4N_MODE_FP64, n_batches: int = 100, max_steps: int = 0, block_size: int = 0,
                         blocks_per_sm: int = 0, refill_min: int = 0, interact_min: int = 0,
-                        diagnostics: bool = False, stream=None, walk_budget: int = 0) -> None:
+                        diagnostics: bool = False, stream=None, walk_budget: int = 0, regroup_period: int = 0) -> None:
     """Device outputs (accumulated): edep (n_batches, stride) f64, counters (32,) int64 (as uint64 bits)."""
     import torch
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
-              interact_min, diagnostics, walk_budget)
+              interact_min, diagnostics, walk_budget, regroup_period)
     if edep.shape[0] != n_batches:
         raise ValueError("edep rows must equal n_batches")
     _check(ctx, load().g4n_transport_batch(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
@@ -379,7 +380,7 @@ def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_has
                                 cutoff: float = 0.01, mode: int = G4N_MODE_FP64, n_batches: int = 100,
                                 max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0, refill_min: int = 0,
                                 interact_min: int = 0, diagnostics: bool = False, stream=None,
-                                walk_budget: int = 0) -> None:
+                                walk_budget: int = 0, regroup_period: int = 0) -> None:
     """The allocation-free variant of g4n_transport_batch (at most G4N_NOALLOC_MAX_ITEMS items).
 
     For callers that must not allocate device memory while running: the library keeps this call's
@@ -388,7 +389,7 @@ def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_has
     """
     import torch
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
-              interact_min, diagnostics, walk_budget)
+              interact_min, diagnostics, walk_budget, regroup_period)
     if edep.shape[0] != n_batches:
         raise ValueError("edep rows must equal n_batches")
     _check(ctx, load().g4n_transport_batch_noalloc(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
@@ -401,10 +402,10 @@ def g4n_transport_batch_host(ctx, items, seed: int, stride: int, n_tracks: int =
                              want_len: bool = False, cutoff: float = 0.01, mode: int = G4N_MODE_FP64,
                              n_batches: int = 100, max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0,
                              refill_min: int = 0, interact_min: int = 0, diagnostics: bool = False, stream=None,
-                             out=None, walk_budget: int = 0):
+                             out=None, walk_budget: int = 0, regroup_period: int = 0):
     """Host-buffer variant: returns dict of numpy arrays (edep, counters, hashes, lengths)."""
     d = _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, refill_min,
-              interact_min, diagnostics, walk_budget)
+              interact_min, diagnostics, walk_budget, regroup_period)
     if out is None:
         out = {"edep": np.zeros((n_batches, stride)), "counters": np.zeros(G4N_N_COUNTERS, dtype=np.uint64),
                "hashes": np.zeros(n_tracks, dtype=np.uint64) if want_hash else None,
@@ -493,11 +494,11 @@ def g4n_mlp_predict(ctx, feat, stream=None):
 def g4n_graph_create(ctx, items, seed: int, edep, counters, track_hash=None, track_len=None, cutoff: float = 0.01,
                      mode: int = G4N_MODE_FP64, n_batches: int = 100, max_steps: int = 0, block_size: int = 0,
                      blocks_per_sm: int = 0, refill_min: int = 0, interact_min: int = 0, diagnostics: bool = False,
-                     walk_budget: int = 0):
+                     walk_budget: int = 0, regroup_period: int = 0):
     """Record the batch as a CUDA graph writing into the given device outputs; returns the handle."""
     import torch
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
-              interact_min, diagnostics, walk_budget)
+              interact_min, diagnostics, walk_budget, regroup_period)
     h = ctypes.c_void_p()
     _check(ctx, load().g4n_graph_create(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
                                         _dptr(counters, torch.int64, "counters"),

@@ -200,6 +200,7 @@ struct TParams {
   int refill_min;    // refill a warp's idle lanes once at least this many are idle
   int interact_min;  // run the interaction phase once at least this many lanes wait for it
   int walk_budget;   // voxel nodes a boundary search walks per round before it yields
+  int regroup;       // regrouping kernel: rounds between block-wide regroups of the tracks
   const mlp::SmemWeights *mlp_w;  // learned mode: weights (device image)
   const MlpLog *log;              // plain mode: training-sample log (null: none)
 };
@@ -596,6 +597,114 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   return kStep;
 }
 
+// ---------------------------------------------------------------- regrouping between rounds
+// The alternative divergence cure: every P.regroup rounds the block's tracks are sorted by
+// (phase, solid kind of the leaf) and dealt out again, so that each warp holds tracks that
+// run the same code (the interaction phase, boxes, tubes, orbs, yielded searches; idle lanes
+// together, which then refill a whole warp at once).  A track's state moves through shared
+// memory as 32-bit words, one array per word (consecutive slots: no bank conflicts on the
+// way back).  Histories do not depend on which lane carries them.
+
+constexpr int kTrackWords = 62;  // Track (50 words), phase (1), voxel chain (11)
+
+__device__ __forceinline__ int regroup_key(const TParams &P, const Track &t, int phase) {
+  if (phase == kEmpty) return 0;
+  const int kind = P.geoms[P.items[t.item].geom].vol[t.leaf].kind;  // box, tube, orb
+  return phase == kStep ? 1 + kind : (phase == kWalk ? 4 + kind : 7 + kind);
+}
+constexpr int kRegroupKeys = 10;
+
+struct WordIO {
+  uint32_t *S;
+  int stride, slot, k;
+  __device__ __forceinline__ void put(uint32_t w) { S[(k++) * stride + slot] = w; }
+  __device__ __forceinline__ uint32_t get() { return S[(k++) * stride + slot]; }
+  __device__ __forceinline__ void putd(double d) {
+    put((uint32_t)__double2loint(d));
+    put((uint32_t)__double2hiint(d));
+  }
+  __device__ __forceinline__ double getd() {
+    const uint32_t lo = get(), hi = get();
+    return __hiloint2double((int)hi, (int)lo);
+  }
+  __device__ __forceinline__ void putl(uint64_t l) {
+    put((uint32_t)l);
+    put((uint32_t)(l >> 32));
+  }
+  __device__ __forceinline__ uint64_t getl() {
+    const uint64_t lo = get(), hi = get();
+    return lo | (hi << 32);
+  }
+};
+
+__device__ __forceinline__ void put_track(WordIO &io, const Track &t, int phase, const Chain &ch) {
+  io.putd(t.x.x); io.putd(t.x.y); io.putd(t.x.z);
+  io.putd(t.u.x); io.putd(t.u.y); io.putd(t.u.z);
+  io.putd(t.iu.x); io.putd(t.iu.y); io.putd(t.iu.z);
+  io.putd(t.E); io.putd(t.Y); io.putd(t.len); io.putd(t.safety); io.putd(t.mu); io.putd(t.mupe); io.putd(t.efrac);
+  io.putd(t.w.best); io.putd(t.w.safety);
+  io.putl(t.h); io.putl((uint64_t)t.tid); io.putl((uint64_t)t.gidx);
+  io.put(t.leaf); io.put(t.item); io.put(t.steps); io.put(t.nzero); io.put(t.ebin); io.put(t.draw);
+  io.put(t.w.bl); io.put(t.w.it);
+  io.put(phase);
+#pragma unroll
+  for (int l = 0; l < kMaxLevels; ++l) {
+    io.put(ch.h[l]);
+    io.put(ch.k0[l]);
+    io.put(ch.k1[l]);
+  }
+  io.put(ch.nlev);
+  io.put(ch.list);
+}
+
+__device__ __forceinline__ void get_track(WordIO &io, Track &t, int &phase, Chain &ch) {
+  t.x.x = io.getd(); t.x.y = io.getd(); t.x.z = io.getd();
+  t.u.x = io.getd(); t.u.y = io.getd(); t.u.z = io.getd();
+  t.iu.x = io.getd(); t.iu.y = io.getd(); t.iu.z = io.getd();
+  t.E = io.getd(); t.Y = io.getd(); t.len = io.getd(); t.safety = io.getd(); t.mu = io.getd(); t.mupe = io.getd();
+  t.efrac = io.getd();
+  t.w.best = io.getd(); t.w.safety = io.getd();
+  t.h = io.getl(); t.tid = (int64_t)io.getl(); t.gidx = (int64_t)io.getl();
+  t.leaf = (int)io.get(); t.item = (int)io.get(); t.steps = (int)io.get(); t.nzero = (int)io.get();
+  t.ebin = (int)io.get(); t.draw = io.get();
+  t.w.bl = (int)io.get(); t.w.it = (int)io.get();
+  phase = (int)io.get();
+#pragma unroll
+  for (int l = 0; l < kMaxLevels; ++l) {
+    ch.h[l] = (int)io.get();
+    ch.k0[l] = (int)io.get();
+    ch.k1[l] = (int)io.get();
+  }
+  ch.nlev = (int)io.get();
+  ch.list = (int)io.get();
+}
+
+// Block-wide regroup (every thread of the block calls it).  S: kTrackWords x blockDim.x words.
+__device__ __forceinline__ void regroup_block(const TParams &P, Track &t, int &phase, Chain &ch, uint32_t *S) {
+  __shared__ int count[kRegroupKeys], base[kRegroupKeys];
+  const int tid = threadIdx.x;
+  if (tid < kRegroupKeys) count[tid] = 0;
+  __syncthreads();
+  const int key = regroup_key(P, t, phase);
+  const int rank = atomicAdd(&count[key], 1);
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+#pragma unroll
+    for (int k = 0; k < kRegroupKeys; ++k) {
+      base[k] = acc;
+      acc += count[k];
+    }
+  }
+  __syncthreads();
+  WordIO out{S, (int)blockDim.x, base[key] + rank, 0};
+  put_track(out, t, phase, ch);
+  __syncthreads();
+  WordIO in{S, (int)blockDim.x, tid, 0};
+  get_track(in, t, phase, ch);
+  __syncthreads();
+}
+
 // Persistent transport: every lane carries one track in registers.  Each round a
 // warp (1) refills its idle lanes from the device queue when enough are idle (one
 // atomic per refill), (2) runs the interaction phase when enough lanes wait for
@@ -606,7 +715,10 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
 // YIELD: boundary searches yield after P.walk_budget voxel nodes (phase kWalk) and go on in a
 // later round.  The kernel without it has none of that code: the workloads whose searches are
 // short run faster without it (smaller code; measured 5 % on the calorimeter).
-template <int MODE, bool COUNT, bool YIELD>
+//
+// REGROUP: every P.regroup rounds the block's tracks are regrouped (regroup_block); the rounds
+// are then block-synchronous and the block ends when none of its lanes has work left.
+template <int MODE, bool COUNT, bool YIELD, bool REGROUP>
 __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
   Counters cnt;
 #pragma unroll
@@ -627,8 +739,17 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
   Chain wch;  // voxel chain of the lane's boundary search (kept while the search yields)
   int phase = kEmpty;
   bool drained = false;
+  int round = 0;
 #pragma unroll 1
   for (;;) {
+    if (REGROUP) {
+      if (round > 0 && round % P.regroup == 0) {
+        if (!__syncthreads_or(phase != kEmpty || !drained)) break;
+        extern __shared__ __align__(16) unsigned char smem_rg[];
+        regroup_block(P, t, phase, wch, reinterpret_cast<uint32_t *>(smem_rg));
+      }
+      ++round;
+    }
     const unsigned idle = __ballot_sync(0xffffffffu, phase == kEmpty);
     const unsigned busy = ~idle;
     const long long c0 = COUNT ? clock64() : 0;
@@ -652,7 +773,7 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
     __syncwarp();
     const long long c2 = COUNT ? clock64() : 0;
     const unsigned stepping2 = __ballot_sync(0xffffffffu, phase == kStep || phase == kWalk);
-    phase = step_warp<MODE, COUNT, YIELD>(P, t, phase, cnt, mc, wch);
+    if (!REGROUP || stepping2) phase = step_warp<MODE, COUNT, YIELD>(P, t, phase, cnt, mc, wch);
     if (COUNT) {
       __syncwarp();
       const long long c3 = clock64();
@@ -666,7 +787,7 @@ __global__ void __launch_bounds__(128, 3) k_transport(const TParams P) {
         }
       }
     }
-    if (drained && __ballot_sync(0xffffffffu, phase != kEmpty) == 0) break;
+    if (!REGROUP && drained && __ballot_sync(0xffffffffu, phase != kEmpty) == 0) break;
   }
   // flush counters: warp reduction, one atomic per counter per warp
 #pragma unroll
@@ -847,17 +968,32 @@ using TransportKernel = void (*)(const TParams);
 
 // The diagnostics kernel always has the yield code (its counters then also count yields); the
 // learned mode never yields.
-TransportKernel transport_kernel(int mode, bool count, bool yield) {
-  if (mode == G4N_MODE_FP64)
-    return count ? k_transport<kFP64, true, true> : (yield ? k_transport<kFP64, false, true> : k_transport<kFP64, false, false>);
+// The regrouping variants exist for the FP64 and FP32 modes without diagnostics.
+template <int MODE>
+TransportKernel plain_kernel(bool yield, bool regroup) {
+  if (regroup) return yield ? k_transport<MODE, false, true, true> : k_transport<MODE, false, false, true>;
+  return yield ? k_transport<MODE, false, true, false> : k_transport<MODE, false, false, false>;
+}
+
+TransportKernel transport_kernel(int mode, bool count, bool yield, bool regroup) {
+  if (mode == G4N_MODE_FP64) return count ? k_transport<kFP64, true, true, false> : plain_kernel<kFP64>(yield, regroup);
   if (mode == G4N_MODE_FP32_RECHECK)
-    return count ? k_transport<kFP32, true, true> : (yield ? k_transport<kFP32, false, true> : k_transport<kFP32, false, false>);
-  return count ? k_transport<kLearned, true, false> : k_transport<kLearned, false, false>;
+    return count ? k_transport<kFP32, true, true, false> : plain_kernel<kFP32>(yield, regroup);
+  return count ? k_transport<kLearned, true, false, false> : k_transport<kLearned, false, false, false>;
 }
 
 // Dynamic shared memory of a launch: the MLP weights and one scratch tile per warp (learned mode).
+// Dynamic shared memory of a transport launch: the MLP weights (learned mode) or the
+// regroup buffer (regrouping kernels).
+size_t transport_smem_bytes(int mode, int block, int regroup);
+
 size_t mlp_smem_bytes(int mode, int block) {
   return mode == G4N_MODE_LEARNED ? sizeof(mlp::SmemWeights) + (size_t)(block / 32) * sizeof(mlp::SmemWarp) : 0;
+}
+
+size_t transport_smem_bytes(int mode, int block, int regroup) {
+  if (mode == G4N_MODE_LEARNED) return mlp_smem_bytes(mode, block);
+  return regroup > 0 ? (size_t)kTrackWords * block * sizeof(uint32_t) : 0;
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -891,8 +1027,11 @@ int launch_error(g4n_ctx *ctx, const char *what) {
 }
 
 // Launch shape of a transport batch (validated); 0 fields take the defaults.
-int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refill, int *inter, int *budget) {
+int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refill, int *inter, int *budget,
+                    int *regroup) {
   *block = b->block_size > 0 ? b->block_size : 128;
+  if (b->regroup_period < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: regroup_period must be >= 0");
+  *regroup = b->mode == G4N_MODE_LEARNED ? 0 : std::min(b->regroup_period, 1 << 20);
   if (b->walk_budget < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: walk_budget must be >= 0");
   *budget = b->walk_budget > 0 ? std::min(b->walk_budget, 1 << 20) : kDefaultWalkBudget;
   if (*block % 32 || *block > 128) return g4n_fail(ctx, G4N_ERR_ARG, "transport: block_size must be a multiple of 32, <= 128");
@@ -943,8 +1082,8 @@ int build_items(g4n_ctx *ctx, const g4n_batch_desc *b, std::vector<DItem> &items
 
 // Launch the persistent transport kernel of mode b->mode with parameters P on `st`.
 int launch_transport(g4n_ctx *ctx, const g4n_batch_desc *b, TParams &P, int block, cudaStream_t st) {
-  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS, P.walk_budget < kNeverYield);
-  const size_t smem = mlp_smem_bytes(b->mode, block);
+  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS, P.walk_budget < kNeverYield, P.regroup > 0);
+  const size_t smem = transport_smem_bytes(b->mode, block, (b->flags & G4N_FLAG_DIAGNOSTICS) ? 0 : P.regroup);
   P.mlp_w = g4n_mlp_image(ctx);
   if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = b->blocks_per_sm;
@@ -1023,8 +1162,8 @@ static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_ede
   if (!ctx || !b) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null argument");
   if (b->n_items < 1 || !b->items) return g4n_fail(ctx, G4N_ERR_ARG, "transport: no work items");
   if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport: null output");
-  int block, refill, inter, budget;
-  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget)) return rc0;
+  int block, refill, inter, budget, regroup;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget, &regroup)) return rc0;
   if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport: n_tally_batches < 1");
   if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport: cutoff must be >= 0");
   std::vector<DItem> items;
@@ -1059,6 +1198,7 @@ static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_ede
   P.refill_min = refill;
   P.interact_min = inter;
   P.walk_budget = budget;
+  P.regroup = regroup;
   P.log = logging ? &ws->log : nullptr;
   return launch_transport(ctx, b, P, block, st);
 }
@@ -1260,8 +1400,8 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: more than G4N_NOALLOC_MAX_ITEMS (" +
                                           std::to_string(G4N_NOALLOC_MAX_ITEMS) + ") work items; use g4n_transport_batch");
   if (!out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: null output");
-  int block, refill, inter, budget;
-  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget)) return rc0;
+  int block, refill, inter, budget, regroup;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget, &regroup)) return rc0;
   if (b->n_tally_batches < 1) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: n_tally_batches < 1");
   if (!(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "transport_noalloc: cutoff must be >= 0");
   DItem items[G4N_NOALLOC_MAX_ITEMS];  // host staging on the stack: no heap either
@@ -1326,6 +1466,7 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     P.refill_min = refill;
     P.interact_min = inter;
     P.walk_budget = budget;
+    P.regroup = regroup;
     P.log = nullptr;
     rc = launch_transport(ctx, b, P, block, st);
     if (rc) return rc;
@@ -1363,8 +1504,8 @@ int g4n_graph_create(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, ui
   *out = nullptr;
   if (ctx->device < 0) return g4n_fail(ctx, G4N_ERR_STATE, "host-only context: no device queries");
   if (b->n_items < 1 || !b->items || !out_edep || !out_counters) return g4n_fail(ctx, G4N_ERR_ARG, "graph_create: no items or outputs");
-  int block, refill, inter, budget;
-  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget)) return rc0;
+  int block, refill, inter, budget, regroup;
+  if (int rc0 = transport_shape(ctx, b, &block, &refill, &inter, &budget, &regroup)) return rc0;
   if (b->n_tally_batches < 1 || !(b->cutoff >= 0.0)) return g4n_fail(ctx, G4N_ERR_ARG, "graph_create: bad tallies or cutoff");
   std::vector<DItem> items;
   int64_t total = 0;
@@ -1405,10 +1546,11 @@ int g4n_graph_create(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, ui
   P.refill_min = refill;
   P.interact_min = inter;
   P.walk_budget = budget;
+  P.regroup = regroup;
   P.log = nullptr;
   P.mlp_w = g4n_mlp_image(ctx);
-  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS, P.walk_budget < kNeverYield);
-  const size_t smem = mlp_smem_bytes(b->mode, block);
+  const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS, P.walk_budget < kNeverYield, P.regroup > 0);
+  const size_t smem = transport_smem_bytes(b->mode, block, (b->flags & G4N_FLAG_DIAGNOSTICS) ? 0 : P.regroup);
   if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = b->blocks_per_sm;
   if (per_sm <= 0) {

@@ -369,6 +369,24 @@ def test_walk_budget_gives_identical_results(env, mode):
     assert c[1]["vox_nodes"] == c[1 << 16]["vox_nodes"]
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", ["barrel", "mixed_smart"])
+def test_regroup_gives_identical_results(env, name, mode):
+    """Block-wide regrouping of the tracks between rounds (periods 1 and 3, with and without yielding
+    searches) moves histories between lanes and warps without changing them: compared with the oracle."""
+    g4, torch, ctx = env
+    sc, og, gid = _build(env, name)
+    src = synth.scenes.barrel_source() if name == "barrel" else Source(pos=(1.0, 2.0, 3.0), isotropic=True,
+                                                                      e_kind="loguniform", e0=0.05, e1=5.0)
+    n, seed = 8000, 0x7A0C0012
+    r = og.transport(src, seed, n, threads=0)
+    for period, budget in ((1, 1 << 16), (3, 2), (1, 8)):
+        edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, regroup_period=period,
+                                          walk_budget=budget)
+        g4.g4n_sync(ctx)
+        _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
+
+
 def _full_size_sampled(env, entries_fn, seed, n_sample=300):
     """Both modes over a full-size launch: identical histories across modes, and a random sample
     of them replayed one by one by the oracle."""
