@@ -9,9 +9,10 @@ The arithmetic lives in ``g4oracle.c`` (plain C, IEEE double, contraction
 off); this module compiles it with gcc and wraps it with ctypes.
 
 Parity status of each function (how it is pinned, see ``tests/test_oracle_*``):
-  * solids (box, orb, tube segment): closed-form ray/solid distances, a
-    bisection march on Inside() for segments and rotated solids, safety checked
-    against sampled distances;
+  * solids (box, orb, tube segment, cone): closed-form ray/solid distances, a
+    bisection march on Inside() for segments, cones and rotated solids, a cone
+    with equal end radii against the tube, safety checked against sampled
+    distances;
   * locate / compute_step / relocate: brute force is the definition itself;
     checked by invariants (locate/step consistency, jitter stability, hand
     built scenes with known answers);

@@ -42,7 +42,7 @@
 #define O_MAXG 4096
 #define O_INF INFINITY
 
-enum { O_BOX = 0, O_TUBE = 1, O_ORB = 2 };
+enum { O_BOX = 0, O_TUBE = 1, O_ORB = 2, O_CONE = 3 };
 enum { EV_NONE = 0, EV_PHOTO = 1, EV_COMPTON = 2, EV_CUTOFF = 3, EV_ESCAPE = 4, EV_PUSH = 5, EV_STEPLIMIT = 6 };
 enum { LIM_PHYS = -2, LIM_MOTHER = -1, LIM_PUSH = -3, LIM_STEPLIMIT = -4 };
 enum {
@@ -50,7 +50,8 @@ enum {
   C_DIST_IN, C_INSIDE, O_NCOUNT = 16
 };
 
-/* Tolerance: kTol = 1e-9 mm x scale; surface band = +-kHalf. */
+/* Solids: box, orb, tube segment and (full) cone, each in its own frame.
+ * Tolerance: kTol = 1e-9 mm x scale; surface band = +-kHalf. */
 static double kTol = 1e-9, kHalf = 0.5e-9;
 
 typedef struct {
@@ -59,6 +60,10 @@ typedef struct {
   double sphi, dphi;         /* tube */
   int seg, wide;             /* tube: phi segment? segment wider than pi? */
   double cs, ss, ce, se;     /* tube: cos/sin of start and end angle */
+  /* cone: radii R(z) = k z + c of the outer (o) and inner (i) surfaces, c = hz above,
+   * cos of their half-opening angles (ca = 1 / sqrt(1 + k^2)), inner surface present */
+  double ko, co, ki, ci, cao, cai;
+  int has_in;
 } OSolid;
 
 typedef struct {
@@ -144,6 +149,19 @@ int o_add_solid(int gi, int kind, const double *p) {
     s.wide = s.seg && s.dphi > M_PI;
     s.cs = cos(s.sphi); s.ss = sin(s.sphi);
     s.ce = cos(s.sphi + s.dphi); s.se = sin(s.sphi + s.dphi);
+  } else if (kind == O_CONE) {
+    /* p = rmin1, rmax1 (at z = -hz), rmin2, rmax2 (at z = +hz), hz; full in phi */
+    const double rmin1 = p[0], rmax1 = p[1], rmin2 = p[2], rmax2 = p[3], hz = p[4];
+    if (!(hz > kTol && rmax1 > rmin1 + kTol && rmax2 > rmin2 + kTol)) return -1;
+    if (!((rmin1 == 0.0 && rmin2 == 0.0) || (rmin1 > kTol && rmin2 > kTol))) return -1;
+    s.c = hz;
+    s.ko = (rmax2 - rmax1) / (2.0 * hz);
+    s.co = 0.5 * (rmax1 + rmax2);
+    s.ki = (rmin2 - rmin1) / (2.0 * hz);
+    s.ci = 0.5 * (rmin1 + rmin2);
+    s.cao = 1.0 / sqrt(1.0 + s.ko * s.ko);
+    s.cai = 1.0 / sqrt(1.0 + s.ki * s.ki);
+    s.has_in = rmin1 > 0.0;
   } else {
     return -1;
   }
@@ -480,11 +498,132 @@ static double tube_safety_out(const OSolid *s, const double *p) {
   return m > 0.0 ? m : 0.0;
 }
 
+/* Cone, full in phi.  Between z = -hz and +hz the solid is Rin(z) <= r <= Rout(z) with
+ * Rout(z) = ko z + co and Rin(z) = ki z + ci (Rin = 0: no inner surface).  The band of a
+ * conical surface is measured along r at the point's z.  Outward normal of the outer surface
+ * along (x / r, y / r, -ko); of the inner surface (the solid lies outside it) along
+ * (-x / r, -y / r, ki).  The end faces' radii are R(+-hz) evaluated the same way. */
+static double cone_r(double k, double c, double z) { return k * z + c; }
+
+static int cone_inside(const OSolid *s, const double *p, const double *v) {
+  const double x = p[0], y = p[1], z = p[2], hz = s->c;
+  double sz = fabs(z) - hz;
+  if (sz > kHalf) return 0;
+  double r2 = x * x + y * y;
+  double ro = cone_r(s->ko, s->co, z);
+  double rop = ro + kHalf, rom = ro - kHalf;
+  if (r2 > rop * rop) return 0;
+  int nz = sz >= -kHalf;
+  int nrmax = r2 >= rom * rom;
+  int nrmin = 0;
+  if (s->has_in) {
+    double ri = cone_r(s->ki, s->ci, z);
+    double rim = ri - kHalf, rip = ri + kHalf;
+    if (r2 < rim * rim) return 0;
+    nrmin = r2 <= rip * rip;
+  }
+  if (!(nz || nrmax || nrmin)) return 1;
+  double r = sqrt(r2);
+  double vr = x * v[0] + y * v[1];
+  if (nz && !(z * v[2] < 0.0)) return 0;
+  if (nrmax && !(vr - s->ko * r * v[2] < 0.0)) return 0;
+  if (nrmin && !(vr - s->ki * r * v[2] > 0.0)) return 0;
+  return 1;
+}
+
+/* mode = +1: entering crossings with t > kHalf; mode = -1: exiting crossings with t > -kHalf. */
+static double cone_cross(const OSolid *s, const double *p, const double *v, int mode) {
+  const double x = p[0], y = p[1], z = p[2], hz = s->c;
+  const double tmin = mode > 0 ? kHalf : -kHalf;
+  double best = O_INF;
+  /* end faces: the hit radius between the inner and outer radius of that end */
+  if (v[2] != 0.0) {
+    for (int k = 0; k < 2; ++k) {
+      double sg = k == 0 ? 1.0 : -1.0;
+      int entering = sg * v[2] < 0.0;
+      if ((mode > 0) != entering) continue;
+      double t = (sg * hz - z) / v[2];
+      if (!(t > tmin && t < best)) continue;
+      double qx = x + t * v[0], qy = y + t * v[1];
+      double r2 = qx * qx + qy * qy;
+      double ro = cone_r(s->ko, s->co, sg * hz) + kHalf;
+      if (r2 > ro * ro) continue;
+      if (s->has_in) {
+        double ri = cone_r(s->ki, s->ci, sg * hz) - kHalf;
+        if (r2 < ri * ri) continue;
+      }
+      best = t;
+    }
+  }
+  /* conical surfaces: (x + t vx)^2 + (y + t vy)^2 = (k (z + t vz) + c)^2, i.e.
+   * a t^2 + 2 b t + cc = 0; d = a t + b is half the rate of change of r^2 - R^2 */
+  for (int w = 0; w < 1 + s->has_in; ++w) {
+    const double k = w == 0 ? s->ko : s->ki, c = w == 0 ? s->co : s->ci;
+    const double rz = cone_r(k, c, z);
+    const double a = v[0] * v[0] + v[1] * v[1] - k * k * v[2] * v[2];
+    const double b = x * v[0] + y * v[1] - k * v[2] * rz;
+    const double cc = x * x + y * y - rz * rz;
+    double roots[2];
+    int nr = 0;
+    if (a != 0.0) {
+      double disc = b * b - a * cc;
+      if (disc > 0.0) {
+        double sq = sqrt(disc);
+        double q = b >= 0.0 ? -(b + sq) : -(b - sq);
+        roots[nr++] = q / a;
+        roots[nr++] = cc / q;
+      }
+    } else if (b != 0.0) {
+      roots[nr++] = -cc / (2.0 * b);
+    }
+    for (int i = 0; i < nr; ++i) {
+      const double t = roots[i];
+      if (!(t > tmin && t < best)) continue;
+      const double d = a * t + b;
+      /* into the solid: through the outer surface r^2 - R^2 decreases, through the inner one it grows */
+      const int entering = w == 0 ? d < 0.0 : d > 0.0;
+      if ((mode > 0) != entering) continue;
+      const double qz = z + t * v[2];
+      if (fabs(qz) > hz + kHalf) continue;
+      if (!(cone_r(k, c, qz) >= 0.0)) continue;   /* the other half of the double cone */
+      best = t;
+    }
+  }
+  return best;
+}
+
+static double cone_dist_in(const OSolid *s, const double *p, const double *v) { return cone_cross(s, p, v, +1); }
+
+static double cone_dist_out(const OSolid *s, const double *p, const double *v) {
+  double t = cone_cross(s, p, v, -1);
+  if (t == O_INF) return 0.0;
+  return t > 0.0 ? t : 0.0;
+}
+
+/* Safety: perpendicular distances (in the meridian plane) to the lines of the conical surfaces,
+ * which bound the distances to the surfaces from below, and the distance to the end planes. */
+static double cone_safety_in(const OSolid *s, const double *p) {
+  double r = sqrt(p[0] * p[0] + p[1] * p[1]);
+  double m = fabs(p[2]) - s->c, d;
+  d = (r - cone_r(s->ko, s->co, p[2])) * s->cao; if (d > m) m = d;
+  if (s->has_in) { d = (cone_r(s->ki, s->ci, p[2]) - r) * s->cai; if (d > m) m = d; }
+  return m > 0.0 ? m : 0.0;
+}
+
+static double cone_safety_out(const OSolid *s, const double *p) {
+  double r = sqrt(p[0] * p[0] + p[1] * p[1]);
+  double m = s->c - fabs(p[2]), d;
+  d = (cone_r(s->ko, s->co, p[2]) - r) * s->cao; if (d < m) m = d;
+  if (s->has_in) { d = (r - cone_r(s->ki, s->ci, p[2])) * s->cai; if (d < m) m = d; }
+  return m > 0.0 ? m : 0.0;
+}
+
 /* "Fork" dispatch on the solid type (the paper's replacement for virtual calls, Sec. 3.3). */
 static int s_inside(const OSolid *s, const double *p, const double *v) {
   switch (s->kind) {
     case O_BOX: return box_inside(s, p, v);
     case O_TUBE: return tube_inside(s, p, v);
+    case O_CONE: return cone_inside(s, p, v);
     default: return orb_inside(s, p, v);
   }
 }
@@ -492,6 +631,7 @@ static double s_dist_in(const OSolid *s, const double *p, const double *v) {
   switch (s->kind) {
     case O_BOX: return box_dist_in(s, p, v);
     case O_TUBE: return tube_dist_in(s, p, v);
+    case O_CONE: return cone_dist_in(s, p, v);
     default: return orb_dist_in(s, p, v);
   }
 }
@@ -499,6 +639,7 @@ static double s_dist_out(const OSolid *s, const double *p, const double *v) {
   switch (s->kind) {
     case O_BOX: return box_dist_out(s, p, v);
     case O_TUBE: return tube_dist_out(s, p, v);
+    case O_CONE: return cone_dist_out(s, p, v);
     default: return orb_dist_out(s, p, v);
   }
 }
@@ -506,6 +647,7 @@ static double s_safety_in(const OSolid *s, const double *p) {
   switch (s->kind) {
     case O_BOX: return box_safety_in(s, p);
     case O_TUBE: return tube_safety_in(s, p);
+    case O_CONE: return cone_safety_in(s, p);
     default: return orb_safety_in(s, p);
   }
 }
@@ -513,6 +655,7 @@ static double s_safety_out(const OSolid *s, const double *p) {
   switch (s->kind) {
     case O_BOX: return box_safety_out(s, p);
     case O_TUBE: return tube_safety_out(s, p);
+    case O_CONE: return cone_safety_out(s, p);
     default: return orb_safety_out(s, p);
   }
 }

@@ -39,14 +39,14 @@ import numpy as np
 
 from .materials import Material, toy_materials, constant_material, vacuum, E_GRID_MEV
 
-BOX, TUBE, ORB = 0, 1, 2
+BOX, TUBE, ORB, CONE = 0, 1, 2, 3
 TWO_PI = 2.0 * math.pi
 CONFIG_SEEDS = {i: (0x6E4A0000 + i, 0x7A0C0000 + i) for i in range(5)}   # (geometry seed, track seed)
 
 
 @dataclasses.dataclass
 class Solid:
-    kind: int                 # BOX, TUBE or ORB
+    kind: int                 # BOX, TUBE, ORB or CONE (rmin1, rmax1, rmin2, rmax2, hz; full in phi)
     params: tuple             # box: (hx, hy, hz); tube: (rmin, rmax, hz, sphi, dphi); orb: (r,)
 
 

@@ -9,7 +9,7 @@ import math
 
 import numpy as np
 
-BOX, TUBE, ORB = 0, 1, 2
+BOX, TUBE, ORB, CONE = 0, 1, 2, 3
 
 
 def inside_strict(kind, par, p):
@@ -20,6 +20,12 @@ def inside_strict(kind, par, p):
         return (np.abs(x) < par[0]) & (np.abs(y) < par[1]) & (np.abs(z) < par[2])
     if kind == ORB:
         return x * x + y * y + z * z < par[0] ** 2
+    if kind == CONE:
+        # radii interpolated linearly from the -hz end (rmin1, rmax1) to the +hz end (rmin2, rmax2)
+        rmin1, rmax1, rmin2, rmax2, hz = par
+        f = (z + hz) / (2.0 * hz)
+        r = np.hypot(x, y)
+        return (np.abs(z) < hz) & (r < rmax1 + (rmax2 - rmax1) * f) & (r > rmin1 + (rmin2 - rmin1) * f)
     rmin, rmax, hz, sphi, dphi = par
     r = np.hypot(x, y)
     ok = (r < rmax) & (r > rmin) & (np.abs(z) < hz)

@@ -10,7 +10,7 @@ import oracle
 import synth
 from synth.scenes import Scene, Solid, Placement, VoxelSpec
 from synth.materials import vacuum
-from geomref import (BOX, TUBE, ORB, inside_strict, first_entry_closed_form, first_exit_closed_form,
+from geomref import (BOX, TUBE, ORB, CONE, inside_strict, first_entry_closed_form, first_exit_closed_form,
                      march_entry, march_exit, random_unit)
 
 TOL = 1e-9
@@ -139,8 +139,11 @@ def test_tube_segment_vs_march(oracle_lib, par):
     assert n_in > 50 and n_out > 20
 
 
+CONES = [(0.0, 1.0, 0.0, 3.0, 2.0), (0.5, 3.0, 0.3, 1.0, 1.5), (1.0, 2.0, 1.2, 2.5, 3.0), (0.0, 3.0, 0.0, 0.3, 0.5)]
+
+
 @pytest.mark.parametrize("kind,par", [(BOX, (2.0, 1.0, 0.5)), (ORB, (1.5,)), (TUBE, (0.5, 2.0, 1.0, 0.0, 2 * math.pi))]
-                         + [(TUBE, s) for s in SEGMENTS])
+                         + [(TUBE, s) for s in SEGMENTS] + [(CONE, c) for c in CONES])
 def test_safety_is_lower_bound(oracle_lib, kind, par):
     g = lab([Solid(kind, par)])
     pred = lambda q: inside_strict(kind, par, q)
@@ -189,3 +192,108 @@ def test_rejects_bad_solids(oracle_lib):
                       (TUBE, [0, 1, 1, 0, 7.0]), (TUBE, [0, 1, 0, 0, 1])]:
         a = np.array(par, dtype=np.float64)
         assert L.o_add_solid(g.gid, kind, a.ctypes.data) < 0
+
+
+@pytest.mark.parametrize("rmin,rmax,hz", [(0.0, 2.0, 1.5), (0.7, 2.0, 1.5)])
+def test_cone_with_equal_ends_is_the_tube(oracle_lib, rmin, rmax, hz):
+    """A cone whose end radii are equal is the (pinned) full tube: same answers on random points and rays."""
+    g = lab([Solid(CONE, (rmin, rmax, rmin, rmax, hz)), Solid(TUBE, (rmin, rmax, hz, 0.0, 2 * math.pi))])
+    rng = np.random.default_rng(8)
+    for _ in range(3000):
+        p = rng.uniform(-3, 3, 3)
+        v = random_unit(rng, 1)[0]
+        assert g.solid_inside(1, p, v) == g.solid_inside(2, p, v)
+        if g.solid_inside(1, p, v):
+            assert g.solid_dist_out(1, p, v) == pytest.approx(g.solid_dist_out(2, p, v), rel=1e-13, abs=1e-13)
+            assert g.solid_safety_out(1, p) == pytest.approx(g.solid_safety_out(2, p), rel=1e-13, abs=1e-13)
+        else:
+            a, b = g.solid_dist_in(1, p, v), g.solid_dist_in(2, p, v)
+            assert (a == INF and b == INF) or a == pytest.approx(b, rel=1e-13, abs=1e-13)
+            assert g.solid_safety_in(1, p) == pytest.approx(g.solid_safety_in(2, p), rel=1e-13, abs=1e-13)
+
+
+def test_cone_closed_forms(oracle_lib):
+    g = lab([Solid(CONE, (0.0, 1.0, 0.0, 3.0, 2.0)), Solid(CONE, (1.0, 2.0, 0.5, 3.0, 1.0))])
+    # along the axis: the end faces
+    assert g.solid_dist_in(1, [0, 0, -10], [0, 0, 1]) == 8.0
+    assert g.solid_dist_out(1, [0, 0, 0.5], [0, 0, 1]) == 1.5
+    # in the plane z = 0 the outer radius is the mean of the end radii
+    assert abs(g.solid_dist_out(1, [0, 0, 0], [1, 0, 0]) - 2.0) < 1e-15
+    assert abs(g.solid_dist_in(1, [-10, 0, 0], [1, 0, 0]) - 8.0) < 1e-14
+    # hollow cone at z = 0: inner radius 0.75, outer 2.5; from the axis the ray enters at the inner cone
+    assert abs(g.solid_dist_in(2, [0, 0, 0], [0, 1, 0]) - 0.75) < 1e-15
+    assert abs(g.solid_dist_out(2, [0, 1.0, 0], [0, 1, 0]) - 1.5) < 1e-15
+    assert abs(g.solid_dist_out(2, [0, 1.0, 0], [0, -1, 0]) - 0.25) < 1e-15
+    # the outer surface of solid 1 is r = z / 2 + 2; the ray r = z from the origin would meet it at z = 4,
+    # beyond the +z face, so it leaves through that face
+    v = np.array([1.0, 0.0, 1.0]) / math.sqrt(2)
+    t = g.solid_dist_out(1, [0, 0, 0], v)
+    q = np.array([0, 0, 0]) + t * v
+    assert abs(q[2] - 2.0) < 1e-14
+    # safety at the origin: the perpendicular distance to the line r = z / 2 + 2, 2 / sqrt(1.25)
+    assert abs(g.solid_safety_out(1, [0, 0, 0]) - 2.0 / math.sqrt(1.25)) < 1e-15
+
+
+@pytest.mark.parametrize("par", CONES)
+def test_cone_vs_march(oracle_lib, par):
+    """Cones (solid, hollow, widening, narrowing, flat): DistanceToIn/Out against a march + bisection on an
+    independent strict-inside predicate."""
+    g = lab([Solid(CONE, par)])
+    pred = lambda q: inside_strict(CONE, par, q)
+    rng = np.random.default_rng(4)
+    ext = max(par[1], par[3], par[4]) * 1.1
+    n_in = n_out = 0
+    tries = 0
+    while n_out < 60 and tries < 100000:
+        tries += 1
+        p = rng.uniform(-ext, ext, 3)
+        if not pred(p):
+            continue
+        v = random_unit(rng, 1)[0]
+        ref = march_exit(pred, p, v, 20.0, 0.01)
+        got = g.solid_dist_out(1, p, v)
+        assert abs(got - ref) < 1e-9, (p, v, got, ref)
+        n_out += 1
+    for _ in range(400):
+        p = rng.uniform(-2 * ext, 2 * ext, 3)
+        if pred(p):
+            continue
+        aim = rng.uniform(-0.8 * ext, 0.8 * ext, 3)
+        v = (aim - p) / np.linalg.norm(aim - p)
+        ref, chord = march_entry(pred, p, v, 30.0, 0.01)
+        got = g.solid_dist_in(1, p, v)
+        if ref == INF or got < ref - 1e-9:
+            # the oracle found an entry the march stepped over: a chord thinner than the march step
+            if got != INF:
+                assert g.solid_dist_out(1, p + got * v, v) < 0.02
+                assert pred(p + (got + 1e-7) * v) and not pred(p + (got - 1e-7) * v)
+        elif chord > 1e-3:
+            assert abs(got - ref) < 1e-9, (p, v, got, ref)
+            n_in += 1
+    assert n_in > 40 and n_out == 60
+
+
+def test_cone_surface_rule(oracle_lib):
+    g = lab([Solid(CONE, (0.5, 1.0, 1.5, 3.0, 2.0))])
+    # outer surface r = 0.5 z + 2, inner r = 0.25 z + 1; outward normal of the outer one along (1, 0, -0.5)
+    on_out = [2.0, 0.0, 0.0]
+    assert g.solid_inside(1, on_out, [-1, 0, 0])
+    assert not g.solid_inside(1, on_out, [1, 0, 0])
+    assert g.solid_inside(1, on_out, [0, 0, 1])          # up the widening cone: v . n = -0.5 < 0
+    assert not g.solid_inside(1, on_out, [0, 0, -1])
+    assert not g.solid_inside(1, on_out, [0.5, 0, 1.0])  # along the surface's generator: tangent
+    on_in = [1.0, 0.0, 0.0]
+    assert g.solid_inside(1, on_in, [1, 0, 0])           # into the solid across the inner cone
+    assert not g.solid_inside(1, on_in, [-1, 0, 0])
+    assert g.solid_inside(1, [1.5, 0.0, 2.0], [0, 0, -1])  # end face
+    assert not g.solid_inside(1, [1.5, 0.0, 2.0], [0, 0, 1])
+    assert g.solid_inside(1, [2.0 + 0.4 * TOL, 0, 0], [-1, 0, 0])
+    assert not g.solid_inside(1, [2.0 + 0.6 * TOL, 0, 0], [-1, 0, 0])
+
+
+def test_rejects_bad_cones(oracle_lib):
+    L = oracle.lib()
+    g = lab([])
+    for par in [(0, 1, 0, 1, 0), (1, 0.5, 0, 1, 1), (0, 1, 2, 1, 1), (0, 1, 0.5, 2, 1), (-1, 1, 0, 1, 1)]:
+        a = np.array(par, dtype=np.float64)
+        assert L.o_add_solid(g.gid, CONE, a.ctypes.data) < 0
