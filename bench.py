@@ -43,7 +43,7 @@ WORKLOAD = ("sampling calorimeter: 50 alternating 5 mm lead-like / 10 mm scintil
 # box test whose answer it gives, and a relocation answered by a face record (face_reloc) as the two Inside
 # tests (mother, entered volume) the method needs at least: the work the method defines, not the
 # instructions the kernel executes.
-FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube": 90, "inside": 24,
+FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube": 90, "cand_cone": 100, "inside": 24,
          "key_inside": 24, "face_reloc": 48, "vox_nodes": 14, "phys_steps": 60}
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
 

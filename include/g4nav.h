@@ -53,7 +53,7 @@ enum {
   G4N_ERR_STATE = -8       /* call out of order (e.g. placing after finalize, query before finalize) */
 };
 
-enum { G4N_BOX = 0, G4N_TUBE = 1, G4N_ORB = 2 };
+enum { G4N_BOX = 0, G4N_TUBE = 1, G4N_ORB = 2, G4N_CONE = 3 };
 
 /* Precision modes of compute_step / transport. */
 enum {
@@ -73,6 +73,7 @@ enum {
   G4N_C_TRACKS = 0, G4N_C_STEPS, G4N_C_GEOM_STEPS, G4N_C_PHYS_STEPS, G4N_C_PHOTO, G4N_C_COMPTON, G4N_C_ESCAPED,
   G4N_C_CUTOFF, G4N_C_PUSHES, G4N_C_STEP_LIMIT,
   G4N_C_WALK_YIELDS = 10,    /* boundary searches that used their node budget and went on in a later round */
+  G4N_C_CAND_CONE = 11,      /* DistanceToIn evaluations of cones */
   G4N_C_FACE_RELOC = 14,     /* relocations answered by a box face's precomputed record */
   G4N_C_KEY_INSIDE = 15,     /* Inside tests of world-aligned boxes answered by exact coordinate thresholds */
   G4N_C_SAFETY_SKIPS = 16,   /* steps that skipped the boundary search because safety exceeded the physics step */
@@ -114,12 +115,16 @@ int g4n_sync(g4n_ctx *ctx, g4n_stream stream);
 int g4n_material_add(g4n_ctx *ctx, double density, int32_t n_e, const double *E_MeV, const double *mu_compton,
                      const double *mu_photo, int32_t *out_mat);
 
-/* Solids (Sec. 3.5 uses boxes, tubes, cones and balls; this library has box, tube segment, orb).
- * Box: half-lengths.  Tube: rmin >= 0 (0 = solid), rmax > rmin, half-length hz, phi range
- * [sphi, sphi + dphi] with 0 < dphi <= 2 pi.  Orb: a full solid sphere. */
+/* Solids (Sec. 3.5 uses boxes, tubes, cones and balls; this library has box, tube segment, orb
+ * and full cone).  Box: half-lengths.  Tube: rmin >= 0 (0 = solid), rmax > rmin, half-length hz,
+ * phi range [sphi, sphi + dphi] with 0 < dphi <= 2 pi.  Orb: a full solid sphere.  Cone: full in
+ * phi, half-length hz, radii rmin1 < rmax1 at z = -hz and rmin2 < rmax2 at z = +hz varying
+ * linearly in between; rmin1 and rmin2 both 0 (no inner surface) or both above the tolerance.
+ * A cone's surface band is measured along r at the point's z. */
 int g4n_solid_box(g4n_ctx *ctx, double hx, double hy, double hz, int32_t *out_solid);
 int g4n_solid_tube(g4n_ctx *ctx, double rmin, double rmax, double hz, double sphi, double dphi, int32_t *out_solid);
 int g4n_solid_orb(g4n_ctx *ctx, double r, int32_t *out_solid);
+int g4n_solid_cone(g4n_ctx *ctx, double rmin1, double rmax1, double rmin2, double rmax2, double hz, int32_t *out_solid);
 
 /* Place `solid` of material `mat` inside volume `mother` (-1 for the world, which must be the
  * first placement of a geometry).  Every placement is a distinct volume; ids are consecutive from

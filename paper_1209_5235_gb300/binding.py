@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libg4nav.so")
 
 G4N_OK, G4N_ERR_ARG, G4N_ERR_GEOM, G4N_ERR_OOM, G4N_ERR_CUDA = 0, -1, -2, -3, -4
 G4N_ERR_STEP_LIMIT, G4N_ERR_TIMEOUT, G4N_ERR_QUEUE, G4N_ERR_STATE = -5, -6, -7, -8
-G4N_BOX, G4N_TUBE, G4N_ORB = 0, 1, 2
+G4N_BOX, G4N_TUBE, G4N_ORB, G4N_CONE = 0, 1, 2, 3
 G4N_MODE_FP64, G4N_MODE_FP32_RECHECK, G4N_MODE_LEARNED = 0, 1, 2
 G4N_LIM_PHYSICS, G4N_LIM_MOTHER = -2, -1
 G4N_DMAX = 32
@@ -30,7 +30,7 @@ G4N_NOALLOC_MAX_ITEMS = 256
 G4N_MLP_N_PARAMS = 6880
 G4N_NOALLOC_STATUS_SLOT = G4N_N_COUNTERS - 1
 COUNTER_NAMES = {0: "tracks", 1: "steps", 2: "geom_steps", 3: "phys_steps", 4: "photo", 5: "compton", 6: "escaped",
-                 7: "cutoff", 8: "pushes", 9: "step_limit", 10: "walk_yields", 14: "face_reloc", 15: "key_inside", 16: "safety_skips", 17: "cand_box", 18: "cand_tube",
+                 7: "cutoff", 8: "pushes", 9: "step_limit", 10: "walk_yields", 11: "cand_cone", 14: "face_reloc", 15: "key_inside", 16: "safety_skips", 17: "cand_box", 18: "cand_tube",
                  19: "cand_orb", 20: "dist_out", 21: "inside", 22: "vox_nodes", 23: "rechecks", 24: "proposals",
                  25: "pruned", 26: "cyc_refill", 27: "cyc_interact", 28: "cyc_step", 29: "step_lanes",
                  30: "step_phases"}
@@ -38,7 +38,7 @@ PARITY_COUNTERS = ["tracks", "steps", "geom_steps", "phys_steps", "photo", "comp
                    "step_limit"]
 
 EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_scale", "g4n_sync", "g4n_material_add",
-            "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_place", "g4n_voxelize", "g4n_geom_finalize",
+            "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_solid_cone", "g4n_place", "g4n_voxelize", "g4n_geom_finalize",
             "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_free_path", "g4n_transport_batch", "g4n_transport_batch_host",
             "g4n_transport_batch_noalloc", "g4n_mlp_load", "g4n_mlp_get", "g4n_mlp_log", "g4n_mlp_train",
             "g4n_mlp_grad", "g4n_mlp_predict", "g4n_graph_create", "g4n_graph_launch", "g4n_graph_destroy"]
@@ -104,6 +104,7 @@ def load():
         "g4n_destroy": [vp], "g4n_set_tolerance_scale": [vp, d], "g4n_sync": [vp, vp],
         "g4n_material_add": [vp, d, i32, vp, vp, vp, vp],
         "g4n_solid_box": [vp, d, d, d, vp], "g4n_solid_tube": [vp, d, d, d, d, d, vp], "g4n_solid_orb": [vp, d, vp],
+        "g4n_solid_cone": [vp, d, d, d, d, d, vp],
         "g4n_place": [vp, i32, i32, i32, vp, vp, vp], "g4n_voxelize": [vp, ctypes.POINTER(g4n_voxel_params)],
         "g4n_geom_finalize": [vp, vp], "g4n_geom_info": [vp, i32, vp],
         "g4n_locate": [vp, i32, i64, vp, vp, vp, vp, vp],
@@ -208,6 +209,13 @@ def g4n_solid_tube(ctx, rmin: float, rmax: float, hz: float, sphi: float, dphi: 
     return out.value
 
 
+def g4n_solid_cone(ctx, rmin1: float, rmax1: float, rmin2: float, rmax2: float, hz: float) -> int:
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_solid_cone(ctx, float(rmin1), float(rmax1), float(rmin2), float(rmax2), float(hz),
+                                      ctypes.byref(out)))
+    return out.value
+
+
 def g4n_solid_orb(ctx, r: float) -> int:
     out = ctypes.c_int32()
     _check(ctx, load().g4n_solid_orb(ctx, float(r), ctypes.byref(out)))
@@ -265,6 +273,8 @@ def build_scene(ctx, scene) -> int:
             solids.append(g4n_solid_box(ctx, *s.params))
         elif s.kind == G4N_TUBE:
             solids.append(g4n_solid_tube(ctx, *s.params))
+        elif s.kind == G4N_CONE:
+            solids.append(g4n_solid_cone(ctx, *s.params))
         else:
             solids.append(g4n_solid_orb(ctx, *s.params))
     for pl in scene.placements:

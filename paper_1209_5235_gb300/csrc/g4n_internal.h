@@ -31,7 +31,7 @@ namespace g4n {
 constexpr int kDMax = G4N_DMAX;
 constexpr int kMaxLevels = 3;
 
-enum SolidKind : int32_t { kBox = 0, kTube = 1, kOrb = 2 };
+enum SolidKind : int32_t { kBox = 0, kTube = 1, kOrb = 2, kCone = 3 };
 // tube bits; world rotation is identity; placement rotation (mother -> local) is identity
 // kKeyBox: a world-aligned box whose Inside test is answered by its DKeyBox thresholds
 enum VolFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4, kWorldAligned = 8, kPlacedAligned = 16, kKeyBox = 32 };
@@ -39,6 +39,7 @@ enum VolFlags : int32_t { kSeg = 1, kWide = 2, kHasRmin = 4, kWorldAligned = 8, 
 struct alignas(128) DVol {
   double tx, ty, tz, c, s;  // placement: local = R(theta)^T (mother - t)
   double p[7];              // box: hx hy hz | orb: r | tube: rmin rmax hz cos(sphi) sin(sphi) cos(ephi) sin(ephi)
+                            // | cone: ki ci ko co hz cos(inner half-angle) cos(outer half-angle)
   int32_t kind, flags, mother, mat;
   int32_t vox;              // root voxel header of this volume's daughters (-1: no daughters)
   int32_t depth;            // 1 for the world
@@ -71,7 +72,7 @@ struct alignas(32) DKeyBox {
 // err = relative rounding allowance of the FP32 local coordinates.
 struct alignas(16) DVol32 {
   float tx, ty, tz, c, s;
-  float q0, q1, q2;   // box: hx hy hz | orb: r 0 0 | tube: rmin rmax hz
+  float q0, q1, q2;   // box: hx hy hz | orb: r 0 0 | tube: rmin rmax hz | cone: its bounding tube
   int32_t kind, flags;
   float scale;        // |t| + extent: magnitude of the quantities involved
   float pad;
@@ -138,10 +139,11 @@ struct DGeom {
   double tol, half;
 };
 
-// Host-side record of a solid.
+// Host-side record of a solid (cone: a = rmin1, b = rmax1 at z = -c; d = rmin2, e = rmax2 at +c).
 struct HSolid {
   int32_t kind;
   double a, b, c, sphi, dphi;
+  double d, e;
 };
 
 struct HMat {

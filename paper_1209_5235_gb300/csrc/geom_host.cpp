@@ -53,6 +53,9 @@ Box3 solid_extent(const HSolid &so, double c, double s, const double *t) {
     b = {{-ex, -ey, -so.c}, {ex, ey, so.c}};
   } else if (so.kind == kOrb) {
     b = {{-so.a, -so.a, -so.a}, {so.a, so.a, so.a}};
+  } else if (so.kind == kCone) {
+    const double rmax = std::max(so.b, so.e);
+    b = {{-rmax, -rmax, -so.c}, {rmax, rmax, so.c}};
   } else {
     double rmin = so.a, rmax = so.b;
     if (so.dphi >= kTwoPi - 1e-12) {
@@ -99,6 +102,12 @@ double solid_outside(const HSolid &so, const double *p) {
     return std::max({std::fabs(p[0]) - so.a, std::fabs(p[1]) - so.b, std::fabs(p[2]) - so.c});
   }
   if (so.kind == kOrb) return std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) - so.a;
+  if (so.kind == kCone) {
+    const double r = std::hypot(p[0], p[1]), f = (p[2] + so.c) / (2.0 * so.c);
+    double m = std::max(std::fabs(p[2]) - so.c, r - (so.b + (so.e - so.b) * f));
+    if (so.a > 0.0) m = std::max(m, so.a + (so.d - so.a) * f - r);
+    return m;
+  }
   double r = std::hypot(p[0], p[1]);
   double m = std::max(r - so.b, std::fabs(p[2]) - so.c);
   if (so.a > 0.0) m = std::max(m, so.a - r);
@@ -125,6 +134,16 @@ void surface_samples(const HSolid &so, std::mt19937_64 &rng, int n, std::vector<
     } else if (so.kind == kOrb) {
       double z = 2.0 * U(rng) - 1.0, ph = kTwoPi * U(rng), st = std::sqrt(std::max(0.0, 1.0 - z * z));
       p[0] = so.a * st * std::cos(ph); p[1] = so.a * st * std::sin(ph); p[2] = so.a * z;
+    } else if (so.kind == kCone) {
+      // outer surface, inner surface, end faces
+      const int f = i % 4;
+      const double ph = kTwoPi * U(rng);
+      double z = (2.0 * U(rng) - 1.0) * so.c;
+      if (f == 2) z = (i % 8 < 4) ? so.c : -so.c;
+      const double fr = (z + so.c) / (2.0 * so.c);
+      const double ro = so.b + (so.e - so.b) * fr, ri = so.a + (so.d - so.a) * fr;
+      const double r = f == 0 ? ro : (f == 1 ? ri : ri + (ro - ri) * U(rng));
+      p[0] = r * std::cos(ph); p[1] = r * std::sin(ph); p[2] = z;
     } else {
       int f = i % 4;
       double ph = so.sphi + so.dphi * (f == 3 ? (i % 8 < 4 ? 0.0 : 1.0) : U(rng));
@@ -549,6 +568,16 @@ int g4n_solid_tube(g4n_ctx *ctx, double rmin, double rmax, double hz, double sph
   return add_solid(ctx, {kTube, rmin, rmax, hz, sphi, dphi}, out);
 }
 
+int g4n_solid_cone(g4n_ctx *ctx, double rmin1, double rmax1, double rmin2, double rmax2, double hz, int32_t *out) {
+  if (!ctx) return G4N_ERR_ARG;
+  if (!(hz > ctx->tol && rmax1 > rmin1 + ctx->tol && rmax2 > rmin2 + ctx->tol && rmin1 >= 0.0 && rmin2 >= 0.0 &&
+        std::isfinite(rmax1 + rmax2 + hz)))
+    return g4n_fail(ctx, G4N_ERR_ARG, "cone: need 0 <= rmin < rmax at both ends, hz > tolerance");
+  if (!((rmin1 == 0.0 && rmin2 == 0.0) || (rmin1 > ctx->tol && rmin2 > ctx->tol)))
+    return g4n_fail(ctx, G4N_ERR_ARG, "cone: rmin1 and rmin2 both 0 or both above the tolerance");
+  return add_solid(ctx, {kCone, rmin1, rmax1, hz, 0.0, kTwoPi, rmin2, rmax2}, out);
+}
+
 int g4n_solid_orb(g4n_ctx *ctx, double r, int32_t *out) {
   if (!ctx) return G4N_ERR_ARG;
   if (!(r > ctx->tol && std::isfinite(r))) return g4n_fail(ctx, G4N_ERR_ARG, "orb: radius must exceed the tolerance");
@@ -631,7 +660,15 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
     v.vox = -1;
     if (so.kind == kBox) { v.p[0] = so.a; v.p[1] = so.b; v.p[2] = so.c; }
     else if (so.kind == kOrb) { v.p[0] = so.a; }
-    else {
+    else if (so.kind == kCone) {
+      // R(z) = k z + c of the inner and outer surfaces, hz, cos of the half-opening angles
+      const double ko = (so.e - so.b) / (2.0 * so.c), co = 0.5 * (so.b + so.e);
+      const double ki = (so.d - so.a) / (2.0 * so.c), ci = 0.5 * (so.a + so.d);
+      v.p[0] = ki; v.p[1] = ci; v.p[2] = ko; v.p[3] = co; v.p[4] = so.c;
+      v.p[5] = 1.0 / std::sqrt(1.0 + ki * ki);
+      v.p[6] = 1.0 / std::sqrt(1.0 + ko * ko);
+      v.flags = so.a > 0.0 ? kHasRmin : 0;
+    } else {
       v.p[0] = so.a; v.p[1] = so.b; v.p[2] = so.c;
       v.p[3] = std::cos(so.sphi); v.p[4] = std::sin(so.sphi);
       v.p[5] = std::cos(so.sphi + so.dphi); v.p[6] = std::sin(so.sphi + so.dphi);
@@ -694,7 +731,17 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
     w.q0 = (float)v.p[0]; w.q1 = (float)v.p[1]; w.q2 = (float)v.p[2];
     w.kind = v.kind;
     w.flags = v.flags;
-    const double ext = v.kind == kOrb ? v.p[0] : (v.kind == kTube ? std::max(v.p[1], v.p[2]) : std::max({v.p[0], v.p[1], v.p[2]}));
+    if (v.kind == kCone) {
+      // the bounding tube: the distance to it bounds the distance to the cone from below
+      const HSolid &so = B.solids[B.places[i].solid];
+      w.q0 = (float)std::min(so.a, so.d);
+      w.q1 = (float)std::max(so.b, so.e);
+      w.q2 = (float)so.c;
+    }
+    const double ext = v.kind == kOrb ? v.p[0]
+                       : v.kind == kTube ? std::max(v.p[1], v.p[2])
+                       : v.kind == kCone ? std::max({B.solids[B.places[i].solid].b, B.solids[B.places[i].solid].e, v.p[4]})
+                                         : std::max({v.p[0], v.p[1], v.p[2]});
     w.scale = (float)(std::fabs(v.tx) + std::fabs(v.ty) + std::fabs(v.tz) + 2.0 * ext);
   }
   // --- validation: containment (surface samples) and sibling overlaps (interior samples)

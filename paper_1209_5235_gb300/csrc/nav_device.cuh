@@ -53,6 +53,7 @@ __device__ __forceinline__ void diag_kind(Counters &c, int kind) {
   if (COUNT) {
     if (kind == kBox) c.c[G4N_C_CAND_BOX]++;
     else if (kind == kTube) c.c[G4N_C_CAND_TUBE]++;
+    else if (kind == kCone) c.c[G4N_C_CAND_CONE]++;
     else c.c[G4N_C_CAND_ORB]++;
   }
 }
@@ -357,17 +358,123 @@ __device__ __forceinline__ double tube_safety_out(const double *q, int flags, co
   return fmax(m, 0.0);
 }
 
+// ---------------------------------------------------------------- cone (full in phi)
+// q[0..6] = ki, ci, ko, co, hz, cos(inner half-angle), cos(outer half-angle): between
+// z = -hz and +hz the solid is Rin(z) <= r <= Rout(z), Rout = ko z + co, Rin = ki z + ci
+// (flag kHasRmin: inner surface present).  Bands along r at the point's z; outward normal of
+// the outer surface along (x / r, y / r, -ko), of the inner one along (-x / r, -y / r, ki).
+
+__device__ __noinline__ bool cone_inside(const double *q, int flags, const V3 &p, const V3 &v, double half) {
+  const double sz = fabs(p.z) - q[4];
+  if (sz > half) return false;
+  const double r2 = p.x * p.x + p.y * p.y;
+  const double ro = q[2] * p.z + q[3];
+  const double rop = ro + half, rom = ro - half;
+  if (r2 > rop * rop) return false;
+  const bool nz = sz >= -half;
+  const bool nrmax = r2 >= rom * rom;
+  bool nrmin = false;
+  if (flags & kHasRmin) {
+    const double ri = q[0] * p.z + q[1];
+    const double rim = ri - half, rip = ri + half;
+    if (r2 < rim * rim) return false;
+    nrmin = r2 <= rip * rip;
+  }
+  if (!(nz || nrmax || nrmin)) return true;
+  const double r = sqrt(r2);
+  const double vr = p.x * v.x + p.y * v.y;
+  if (nz && !(p.z * v.z < 0.0)) return false;
+  if (nrmax && !(vr - q[2] * r * v.z < 0.0)) return false;
+  if (nrmin && !(vr - q[0] * r * v.z > 0.0)) return false;
+  return true;
+}
+
+// enter = true: first entering crossing with t > half; enter = false: first exiting crossing
+// with t > -half.  Conical surfaces: a t^2 + 2 b t + cc = 0 with d = a t + b half the rate of
+// change of r^2 - R^2 along the ray (entering the solid: d < 0 at the outer surface, d > 0 at
+// the inner one); roots on the other half of the double cone (R < 0) are not surface points.
+__device__ __noinline__ double cone_cross(const double *q, int flags, const V3 &p, const V3 &v, double half, bool enter) {
+  const double tmin = enter ? half : -half;
+  const double hz = q[4];
+  double best = kInf;
+  if (v.z != 0.0) {
+    const double sg = ((v.z < 0.0) == enter) ? 1.0 : -1.0;
+    const double t = (sg * hz - p.z) / v.z;
+    if (t > tmin) {
+      const double qx = p.x + t * v.x, qy = p.y + t * v.y;
+      const double r2 = qx * qx + qy * qy;
+      const double ro = q[2] * (sg * hz) + q[3] + half;
+      bool ok = r2 <= ro * ro;
+      if (flags & kHasRmin) {
+        const double ri = q[0] * (sg * hz) + q[1] - half;
+        ok = ok && !(r2 < ri * ri);
+      }
+      if (ok) best = t;
+    }
+  }
+  const int nw = (flags & kHasRmin) ? 2 : 1;
+#pragma unroll 1
+  for (int w = 0; w < nw; ++w) {
+    const double k = w == 0 ? q[2] : q[0], c = w == 0 ? q[3] : q[1];
+    const double rz = k * p.z + c;
+    const double a = v.x * v.x + v.y * v.y - k * k * v.z * v.z;
+    const double b = p.x * v.x + p.y * v.y - k * v.z * rz;
+    const double cc = p.x * p.x + p.y * p.y - rz * rz;
+    double t0 = kInf, t1 = kInf;
+    if (a != 0.0) {
+      const double disc = b * b - a * cc;
+      if (disc > 0.0) {
+        const double sq = sqrt(disc);
+        const double qq = -(b + copysign(sq, b));
+        t0 = qq / a;
+        t1 = cc / qq;
+      }
+    } else if (b != 0.0) {
+      t0 = -cc / (2.0 * b);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const double t = i == 0 ? t0 : t1;
+      if (!(t > tmin && t < best)) continue;
+      const double d = a * t + b;
+      const bool into = w == 0 ? d < 0.0 : d > 0.0;
+      if (into != enter) continue;
+      const double qz = p.z + t * v.z;
+      if (fabs(qz) > hz + half) continue;
+      if (!(k * qz + c >= 0.0)) continue;
+      best = t;
+    }
+  }
+  return best;
+}
+
+__device__ __forceinline__ double cone_safety_in(const double *q, int flags, const V3 &p) {
+  const double r = sqrt(p.x * p.x + p.y * p.y);
+  double m = fmax(fabs(p.z) - q[4], (r - (q[2] * p.z + q[3])) * q[6]);
+  if (flags & kHasRmin) m = fmax(m, ((q[0] * p.z + q[1]) - r) * q[5]);
+  return fmax(m, 0.0);
+}
+
+__device__ __forceinline__ double cone_safety_out(const double *q, int flags, const V3 &p) {
+  const double r = sqrt(p.x * p.x + p.y * p.y);
+  double m = fmin(q[4] - fabs(p.z), ((q[2] * p.z + q[3]) - r) * q[6]);
+  if (flags & kHasRmin) m = fmin(m, (r - (q[0] * p.z + q[1])) * q[5]);
+  return fmax(m, 0.0);
+}
+
 // ---------------------------------------------------------------- dispatch on the solid kind
 
 __device__ __forceinline__ bool vol_inside(const DVol &d, const V3 &p, const V3 &v, double half) {
   if (d.kind == kBox) return box_inside(d.p, p, v, half);
   if (d.kind == kOrb) return orb_inside(d.p[0], p, v, half);
+  if (d.kind == kCone) return cone_inside(d.p, d.flags, p, v, half);
   return tube_inside(d.p, d.flags, p, v, half);
 }
 
 __device__ __forceinline__ double vol_dist_in(const DVol &d, const V3 &p, const V3 &v, double half) {
   if (d.kind == kBox) return box_dist_in(d.p, p, v, half);
   if (d.kind == kOrb) return orb_dist_in(d.p[0], p, v, half);
+  if (d.kind == kCone) return cone_cross(d.p, d.flags, p, v, half, true);
   return tube_cross(d.p, d.flags, p, v, half, true);
 }
 
@@ -376,19 +483,21 @@ __device__ __forceinline__ double vol_dist_out(const DVol &d, const V3 &p, const
   *face = -1;
   if (d.kind == kBox) return box_dist_out(d.p, p, v, iv, face);
   if (d.kind == kOrb) return orb_dist_out(d.p[0], p, v);
-  const double t = tube_cross(d.p, d.flags, p, v, half, false);
+  const double t = d.kind == kCone ? cone_cross(d.p, d.flags, p, v, half, false) : tube_cross(d.p, d.flags, p, v, half, false);
   return t == kInf ? 0.0 : fmax(t, 0.0);
 }
 
 __device__ __forceinline__ double vol_safety_in(const DVol &d, const V3 &p) {
   if (d.kind == kBox) return box_safety_in(d.p, p);
   if (d.kind == kOrb) return orb_safety_in(d.p[0], p);
+  if (d.kind == kCone) return cone_safety_in(d.p, d.flags, p);
   return tube_safety_in(d.p, d.flags, p);
 }
 
 __device__ __forceinline__ double vol_safety_out(const DVol &d, const V3 &p) {
   if (d.kind == kBox) return box_safety_out(d.p, p);
   if (d.kind == kOrb) return orb_safety_out(d.p[0], p);
+  if (d.kind == kCone) return cone_safety_out(d.p, d.flags, p);
   return tube_safety_out(d.p, d.flags, p);
 }
 
@@ -512,7 +621,13 @@ __device__ __forceinline__ void exit_bounds32(const DVol &V, const Ray32 &r, con
   float ax = absmax(r.plo[0], r.phi[0]), ay = absmax(r.plo[1], r.phi[1]), az = absmax(r.plo[2], r.phi[2]);
   float s;
   float ext[3];
-  if (V.kind == kOrb) {
+  if (V.kind == kCone) {
+    // no FP32 safety (0 bounds it); the exit lies within the bounding box of the end radii
+    s = 0.f;
+    const double rmax = fmax(V.p[3] - V.p[2] * V.p[4], V.p[3] + V.p[2] * V.p[4]);
+    ext[0] = ext[1] = __double2float_ru(rmax);
+    ext[2] = __double2float_ru(V.p[4]);
+  } else if (V.kind == kOrb) {
     const float R = __double2float_rd(V.p[0]);
     const float rr = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az)));
     s = __fsub_rd(R, rr);
@@ -551,6 +666,7 @@ __device__ __forceinline__ bool certainly_inside32(const DVol &V, const Ray32 &r
       if (!(absmax(r.plo[a], r.phi[a]) < __fsub_rd(__double2float_rd(V.p[a]), band))) return false;
     return true;
   }
+  if (V.kind == kCone) return false;
   const float ax = absmax(r.plo[0], r.phi[0]), ay = absmax(r.plo[1], r.phi[1]), az = absmax(r.plo[2], r.phi[2]);
   if (V.kind == kOrb) {
     const float R = __fsub_rd(__double2float_rd(V.p[0]), band);
@@ -1219,6 +1335,9 @@ __device__ __forceinline__ void node_features(const DGeom &G, const DVol &V, con
     h[2] = V.p[2];
   } else if (V.kind == kOrb) {
     h[0] = h[1] = h[2] = V.p[0];
+  } else if (V.kind == kCone) {
+    h[0] = h[1] = fmax(V.p[3] - V.p[2] * V.p[4], V.p[3] + V.p[2] * V.p[4]);
+    h[2] = V.p[4];
   } else {
     h[0] = h[1] = V.p[1];
     h[2] = V.p[2];

@@ -609,10 +609,10 @@ constexpr int kTrackWords = 62;  // Track (50 words), phase (1), voxel chain (11
 
 __device__ __forceinline__ int regroup_key(const TParams &P, const Track &t, int phase) {
   if (phase == kEmpty) return 0;
-  const int kind = P.geoms[P.items[t.item].geom].vol[t.leaf].kind;  // box, tube, orb
-  return phase == kStep ? 1 + kind : (phase == kWalk ? 4 + kind : 7 + kind);
+  const int kind = P.geoms[P.items[t.item].geom].vol[t.leaf].kind;  // box, tube, orb, cone
+  return phase == kStep ? 1 + kind : (phase == kWalk ? 5 + kind : 9 + kind);
 }
-constexpr int kRegroupKeys = 10;
+constexpr int kRegroupKeys = 13;
 
 struct WordIO {
   uint32_t *S;

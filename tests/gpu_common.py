@@ -6,7 +6,7 @@ import numpy as np
 
 import oracle
 import synth
-from synth.scenes import Scene, Solid, Placement, VoxelSpec, BOX, TUBE, ORB
+from synth.scenes import Scene, Solid, Placement, VoxelSpec, BOX, TUBE, ORB, CONE
 from synth.materials import toy_materials
 
 
@@ -107,3 +107,55 @@ def random_queries(og, scene, n, seed, box_half=None, surface_frac=0.5, aim_frac
 
 def to_soa(a, torch, device="cuda"):
     return torch.tensor(np.ascontiguousarray(a.T), dtype=torch.float64, device=device)
+
+
+def cones_scene(seed=21, n_random=40, half=500.0):
+    """Cones as leaves and as mothers: a solid cone holding a box, an orb and a small hollow cone; a hollow
+    cone with orbs in its wall; and seeded random cones (solid and hollow, widening and narrowing, rotated
+    about z) kept apart by their bounding spheres, among a few boxes."""
+    rng = np.random.default_rng(seed)
+    m = toy_materials()
+    mats = [m["water"], m["lead"], m["scint"], m["al"]]
+    solids = [Solid(BOX, (half, half, half)),
+              Solid(CONE, (0.0, 200.0, 0.0, 120.0, 150.0)),      # 1 solid cone mother
+              Solid(BOX, (20.0, 20.0, 20.0)),                    # 2
+              Solid(ORB, (30.0,)),                               # 3
+              Solid(CONE, (10.0, 40.0, 15.0, 30.0, 40.0)),       # 4 small hollow cone
+              Solid(CONE, (30.0, 80.0, 50.0, 120.0, 100.0)),     # 5 hollow cone mother
+              Solid(ORB, (15.0,))]                               # 6
+    places = [Placement(-1, 0, 0, (0.0, 0.0, 0.0)),
+              Placement(0, 1, 1, (200.0, 200.0, 0.0)),
+              Placement(1, 2, 2, (0.0, 0.0, -50.0)),
+              Placement(1, 3, 3, (0.0, 0.0, 60.0)),
+              Placement(1, 4, 2, (60.0, 0.0, -40.0), (math.cos(0.4), math.sin(0.4))),
+              Placement(0, 5, 3, (-250.0, -100.0, 100.0), (math.cos(1.1), math.sin(1.1)))]
+    for k in range(6):
+        a = k * math.pi / 3
+        places.append(Placement(5, 6, 1, (70.0 * math.cos(a), 70.0 * math.sin(a), 0.0)))
+    centres = [np.array([200.0, 200.0, 0.0]), np.array([-250.0, -100.0, 100.0])]
+    radii = [math.hypot(200.0, 150.0), math.hypot(120.0, 100.0)]
+    placed = tries = 0
+    while placed < n_random and tries < 100000:
+        tries += 1
+        if placed % 4 == 3:
+            so = Solid(BOX, tuple(float(x) for x in rng.uniform(10.0, 40.0, 3)))
+            r = float(np.linalg.norm(so.params))
+        else:
+            hz = float(rng.uniform(10.0, 40.0))
+            rmax1, rmax2 = (float(x) for x in rng.uniform(8.0, 45.0, 2))
+            if rng.uniform() < 0.5:
+                rmin1, rmin2 = 0.0, 0.0
+            else:
+                rmin1, rmin2 = float(rng.uniform(0.2, 0.7) * rmax1), float(rng.uniform(0.2, 0.7) * rmax2)
+            so = Solid(CONE, (rmin1, rmax1, rmin2, rmax2, hz))
+            r = math.hypot(max(rmax1, rmax2), hz)
+        c = rng.uniform(-half + r + 1.0, half - r - 1.0, 3)
+        if any(np.linalg.norm(c - c2) < r + r2 + 1.0 for c2, r2 in zip(centres, radii)):
+            continue
+        centres.append(c)
+        radii.append(r)
+        solids.append(so)
+        th = float(rng.uniform(0.0, 2 * math.pi))
+        places.append(Placement(0, len(solids) - 1, 1 + placed % 3, tuple(float(x) for x in c), (math.cos(th), math.sin(th))))
+        placed += 1
+    return Scene("cones", mats, solids, places, VoxelSpec(mode="smart"))

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import synth
-from synth.scenes import Scene, Solid, Placement, VoxelSpec, BOX, TUBE, ORB
+from synth.scenes import Scene, Solid, Placement, VoxelSpec, BOX, TUBE, ORB, CONE
 from synth.materials import vacuum
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -74,7 +74,7 @@ def _depth(sc, i):
 
 @pytest.mark.parametrize("case,code", [
     ("overlap", -2), ("sticks_out", -2), ("too_deep", -2), ("bad_rotation", -1), ("bad_box", -1),
-    ("bad_tube", -1), ("world_not_first", -1), ("bad_material_id", -1)])
+    ("bad_tube", -1), ("bad_cone", -1), ("cone_sticks_out", -2), ("world_not_first", -1), ("bad_material_id", -1)])
 def test_host_only_validation(g4, case, code):
     ctx = g4.g4n_create(-1)
     try:
@@ -94,6 +94,12 @@ def test_host_only_validation(g4, case, code):
                 g4.g4n_solid_box(ctx, 1.0, 0.0, 1.0)
             elif case == "bad_tube":
                 g4.g4n_solid_tube(ctx, 2.0, 1.0, 1.0, 0.0, 1.0)
+            elif case == "bad_cone":
+                g4.g4n_solid_cone(ctx, 0.0, 1.0, 2.0, 1.5, 1.0)
+            elif case == "cone_sticks_out":
+                # the wide end (radius 30) of the cone does not fit the 20 mm mother box
+                g4.build_scene(ctx, _scene([Solid(BOX, (20, 20, 20)), Solid(CONE, (0, 5, 0, 30, 10))],
+                                           [Placement(0, 1, 0, (0, 0, 0)), Placement(1, 2, 0, (0, 0, 0))]))
             elif case == "world_not_first":
                 m = g4.g4n_material_add(ctx, 1.0, [1, 2], [0, 0], [0, 0])
                 s = g4.g4n_solid_box(ctx, 1, 1, 1)

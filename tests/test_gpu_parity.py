@@ -9,7 +9,7 @@ import pytest
 import oracle
 import synth
 from synth.scenes import VoxelSpec, Source
-from gpu_common import mixed_scene, nested_scene, random_queries, segments_scene, to_soa
+from gpu_common import cones_scene, mixed_scene, nested_scene, random_queries, segments_scene, to_soa
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +43,7 @@ SCENES = {
     "spheres": lambda: synth.scenes.spheres_scene(),
     "segments": lambda: segments_scene(),
     "nested_barrel": lambda: synth.scenes.nested_barrel_scene(),
+    "cones": lambda: cones_scene(),
 }
 BOX_HALF = {"barrel": (1600.0, 1600.0, 1600.0), "nested_barrel": (1600.0, 1600.0, 1600.0), "calorimeter": (600.0, 600.0, 400.0), "nested_core": (12.0, 12.0, 12.0),
             "segments": (360.0, 360.0, 90.0)}
@@ -206,7 +207,7 @@ def _compare_transport(g4, r, edep, cnt, h, ln, nv, exact_tally_rel=1e-9):
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name,n", [("tiny", 10000), ("calorimeter", 20000), ("mixed_smart", 20000),
                                     ("barrel", 20000), ("nested", 20000), ("spheres", 5000), ("segments", 20000),
-                                    ("nested_barrel", 20000)])
+                                    ("nested_barrel", 20000), ("cones", 20000)])
 def test_transport_parity(env, name, n, mode):
     g4, torch, ctx = env
     sc, og, gid = _build(env, name)
