@@ -48,6 +48,30 @@ FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_transport launch of the default workload,
+# from the ncu capture summarised in profiles/k_transport_fp64_calorimeter_full.md.  It is reported only while
+# the CUDA sources hash to the value they had when the capture was taken (else the kernel has changed since).
+NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+
+
+def cuda_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1209_5235_gb300", "csrc")
+    files = [os.path.join(csrc, f) for f in sorted(os.listdir(csrc)) if f.endswith((".cu", ".cuh", ".h", ".cpp"))]
+    for f in files + [os.path.join(ROOT, "include", "g4nav.h")]:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    if NCU_TRAFFIC["bytes_per_launch"] is None or NCU_TRAFFIC["sources_sha256"] != cuda_sources_sha256():
+        return None
+    return NCU_TRAFFIC["bytes_per_launch"]
+
+
 def algorithmic_flops(c: dict) -> float:
     return float(sum(FLOPS[k] * c[k] for k in FLOPS))
 
@@ -418,7 +442,8 @@ def run_gpu(args):
         "graph_replay_steps_per_s": graph_value,
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": measured_traffic() if args.workload == "calorimeter" else None,
                      "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (recipe nominal 1.25 TFLOP/s)",
                      "kernel": "k_transport", "flops_per_launch": flops},
         "hbm": {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / t_launch / 1e9,

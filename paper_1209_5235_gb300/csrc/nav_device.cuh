@@ -1037,6 +1037,7 @@ __device__ __forceinline__ int locate_world_warp(const DGeom &G, bool active, co
 template <int MODE, bool COUNT>
 __device__ __forceinline__ int relocate_warp(const DGeom &G, bool active, int leaf, const V3 &x, const V3 &u,
                                              bool left_leaf, Counters &cnt) {
+  if (!__any_sync(kFull, active)) return -1;  // no lane relocates: skip the warp's whole search
   int blocked = -1;
   if (active && left_leaf) {
     blocked = leaf;

@@ -181,6 +181,8 @@ struct Track {
   WalkResume w;      // phase kWalk: the yielded boundary search of the current step
 };
 
+// The per-track history hash and path length are outputs: a launch that does not ask for
+// them (out_hash / out_len null) does not compute them.
 struct TParams {
   const DGeom *geoms;
   const DItem *items;
@@ -337,7 +339,7 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
   if (leaf < 0) {
     cnt.c[G4N_C_ESCAPED]++;
     tally(P, t, G.n_vol, t.E);
-    t.h = hash_step(t.h, -1, G4N_LIM_MOTHER, kEvEscape);
+    if (P.out_hash) t.h = hash_step(t.h, -1, G4N_LIM_MOTHER, kEvEscape);
     finish(P, t);
     t.leaf = 0;
     return kEmpty;
@@ -422,7 +424,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   if (act && !resume && t.steps >= P.max_steps) {
     cnt.c[G4N_C_STEP_LIMIT]++;
     flag(P.status, kStStepLimit);
-    t.h = hash_step(t.h, t.leaf, kLimStepLimit, kEvStepLimit);
+    if (P.out_hash) t.h = hash_step(t.h, t.leaf, kLimStepLimit, kEvStepLimit);
     finish(P, t);
     next = kEmpty;
     act = false;
@@ -490,7 +492,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     t.x.x += s * t.u.x;
     t.x.y += s * t.u.y;
     t.x.z += s * t.u.z;
-    t.len += s;
+    if (P.out_len) t.len += s;
     if (!geo) {
       // free path ends inside the volume: the interaction is done in the interaction phase
       t.safety = fmax(t.safety - s, 0.0);
@@ -524,7 +526,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
         t.x.x += push * t.u.x;
         t.x.y += push * t.u.y;
         t.x.z += push * t.u.z;
-        t.len += push;
+        if (P.out_len) t.len += push;
         cnt.c[G4N_C_PUSHES]++;
         t.nzero = 0;
         pushing = need = true;
@@ -534,17 +536,17 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     }
     if (!__any_sync(kFull, need)) break;
   }
-  if (pushing) t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
+  if (pushing && P.out_hash) t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
   if (geo) {
     if (leaf < 0) {
       cnt.c[G4N_C_ESCAPED]++;
       tally(P, t, G.n_vol, t.E);
-      t.h = hash_step(t.h, -1, lim, kEvEscape);
+      if (P.out_hash) t.h = hash_step(t.h, -1, lim, kEvEscape);
       finish(P, t);
       next = kEmpty;
     } else {
       t.leaf = leaf;
-      t.h = hash_step(t.h, leaf, lim, kEvNone);
+      if (P.out_hash) t.h = hash_step(t.h, leaf, lim, kEvNone);
       update_mu(G, t);
       next = kStep;
     }
@@ -562,7 +564,7 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   if (U * t.mu < t.mupe) {
     cnt.c[G4N_C_PHOTO]++;
     tally(P, t, t.leaf, t.E);
-    t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvPhoto);
+    if (P.out_hash) t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvPhoto);
     finish(P, t);
     return kEmpty;
   }
@@ -576,14 +578,14 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   if (E1 < P.cutoff) {
     cnt.c[G4N_C_CUTOFF]++;
     tally(P, t, t.leaf, t.E);
-    t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCutoff);
+    if (P.out_hash) t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCutoff);
     finish(P, t);
     return kEmpty;
   }
   tally(P, t, t.leaf, t.E - E1);
   set_energy(G, t, E1);
   t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
-  t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCompton);
+  if (P.out_hash) t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCompton);
   update_mu(G, t);
   // FP64 mode: the isotropic safety of a leaf without daughters, at the interaction point
   // (the step phase does not compute it there; a safety only lets the next step skip a
