@@ -74,6 +74,7 @@ def lib():
             "o_locate": (i, [i, vp, vp, vp]), "o_relocate": (i, [i, vp, i, vp, vp]),
             "o_compute_step": (i, [i, i, vp, vp, vp, d, vp, vp, vp]),
             "o_philox4x32_10": (None, [vp, vp, vp]), "o_uniform": (d, [u64, i64, ctypes.c_uint32, ctypes.c_uint32]),
+            "o_uniform_pair": (None, [u64, i64, ctypes.c_uint32, ctypes.c_uint32, vp]),
             "o_fnv1a": (u64, [vp, i64]), "o_mu": (None, [i, i, d, vp]),
             "o_kahn_sample": (i, [d, u64, i64, i64, vp, vp]),
             "o_source_sample": (None, [vp, u64, i64, i64, vp, vp, vp]),
@@ -247,6 +248,12 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def uniform(seed: int, tid: int, stream: int, draw: int) -> float:
     return lib().o_uniform(ctypes.c_uint64(seed), int(tid), stream, draw)
+
+
+def uniform_pair(seed: int, tid: int, stream: int, draw: int):
+    out = np.zeros(2)
+    lib().o_uniform_pair(ctypes.c_uint64(seed), int(tid), stream, draw, _p(out))
+    return float(out[0]), float(out[1])
 
 
 def fnv1a(data: bytes) -> int:

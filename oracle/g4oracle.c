@@ -808,19 +808,33 @@ void o_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
 
 typedef struct { uint64_t seed; int64_t tid; uint32_t stream, draw; } ORng;
 
-/* One uniform in (0, 1]: the top 53 bits of (x1:x0), plus one, times 2^-53. */
-static double rng_u(ORng *r) {
+/* Two uniforms in (0, 1] from one block: the top 53 bits of (x1:x0) and of (x3:x2), each
+ * plus one, times 2^-53.  A draw site takes whole blocks: a single uniform uses the first. */
+static void rng_pair(ORng *r, double *ua, double *ub) {
   uint32_t ctr[4] = {r->draw++, (uint32_t)(uint64_t)r->tid, (uint32_t)((uint64_t)r->tid >> 32), r->stream};
   uint32_t key[2] = {(uint32_t)r->seed, (uint32_t)(r->seed >> 32)};
   uint32_t x[4];
   o_philox4x32_10(ctr, key, x);
-  uint64_t w = ((uint64_t)x[1] << 32) | x[0];
-  return (double)((w >> 11) + 1) * 0x1.0p-53;
+  uint64_t wa = ((uint64_t)x[1] << 32) | x[0];
+  uint64_t wb = ((uint64_t)x[3] << 32) | x[2];
+  *ua = (double)((wa >> 11) + 1) * 0x1.0p-53;
+  *ub = (double)((wb >> 11) + 1) * 0x1.0p-53;
+}
+
+static double rng_u(ORng *r) {
+  double a, b;
+  rng_pair(r, &a, &b);
+  return a;
 }
 
 double o_uniform(uint64_t seed, int64_t tid, uint32_t stream, uint32_t draw) {
   ORng r = {seed, tid, stream, draw};
   return rng_u(&r);
+}
+
+void o_uniform_pair(uint64_t seed, int64_t tid, uint32_t stream, uint32_t draw, double *out) {
+  ORng r = {seed, tid, stream, draw};
+  rng_pair(&r, &out[0], &out[1]);
 }
 
 /* FNV-1a, 64 bit, over little-endian bytes. */
@@ -870,12 +884,15 @@ void o_mu(int gi, int mat, double E, double *out) {
 }
 
 /* Kahn's rejection method for the Klein-Nishina distribution of eta = E / E'
- * (three uniforms per trial).  Returns the number of trials (0 = cap hit). */
+ * (three uniforms per trial: r1, r2 from one block, r3 from the next).  Returns the
+ * number of trials (0 = cap hit). */
 static int kahn(double E, ORng *r, double *eta_out, double *cost_out) {
   double al = E / ME_C2;
   double p1 = (1.0 + 2.0 * al) / (9.0 + 2.0 * al);
   for (int trial = 1; trial <= 1000; ++trial) {
-    double r1 = rng_u(r), r2 = rng_u(r), r3 = rng_u(r);
+    double r1, r2, r3, unused;
+    rng_pair(r, &r1, &r2);
+    rng_pair(r, &r3, &unused);
     double eta, cost;
     if (r1 <= p1) {
       eta = 1.0 + 2.0 * al * r2;
@@ -895,10 +912,13 @@ static int kahn(double E, ORng *r, double *eta_out, double *cost_out) {
   return 0;
 }
 
-/* Uniform azimuth by rejection on the unit disc: (cos 2psi, sin 2psi) of a uniform point. */
+/* Uniform azimuth by rejection on the unit disc: (cos 2psi, sin 2psi) of a uniform point
+ * (one block per trial). */
 static int azimuth(ORng *r, double *cph, double *sph) {
   for (int trial = 1; trial <= 1000; ++trial) {
-    double a = 2.0 * rng_u(r) - 1.0, b = 2.0 * rng_u(r) - 1.0;
+    double ua, ub;
+    rng_pair(r, &ua, &ub);
+    double a = 2.0 * ua - 1.0, b = 2.0 * ub - 1.0;
     double s = a * a + b * b;
     if (!(s > 0.0 && s <= 1.0)) continue;
     *cph = (a * a - b * b) / s;
@@ -943,9 +963,11 @@ static void gen_source(const double *src, uint64_t seed, int64_t tid, double *po
   ORng r = {seed, tid, 0u, 0u};
   pos[0] = src[0]; pos[1] = src[1]; pos[2] = src[2];
   if (src[3] > 0.0) {
-    /* Marsaglia polar method */
+    /* Marsaglia polar method (one block per trial) */
     for (int trial = 0; trial < 1000; ++trial) {
-      double a = 2.0 * rng_u(&r) - 1.0, b = 2.0 * rng_u(&r) - 1.0;
+      double ua, ub;
+      rng_pair(&r, &ua, &ub);
+      double a = 2.0 * ua - 1.0, b = 2.0 * ub - 1.0;
       double s = a * a + b * b;
       if (!(s > 0.0 && s < 1.0)) continue;
       double f = sqrt(-2.0 * log(s) / s);
@@ -1047,7 +1069,9 @@ static void transport_one(const OGeom *g, const double *src, uint64_t seed, int6
     len += sphys;
     nzero = 0;
     cnt[C_PHYS]++;
-    double U = rng_u(&rp);
+    /* one block per interaction: U chooses the process, W gives the next free path */
+    double U, W;
+    rng_pair(&rp, &U, &W);
     if (U * mu < mupe) {
       cnt[C_PHOTO]++;
       tally_row[leaf] += E;
@@ -1068,7 +1092,7 @@ static void transport_one(const OGeom *g, const double *src, uint64_t seed, int6
     }
     tally_row[leaf] += E - E1;
     E = E1;
-    Y = -log(rng_u(&rp));
+    Y = -log(W);
     h = hash_step(h, leaf, LIM_PHYS, EV_COMPTON);
   }
   if (hash_out) *hash_out = h;
@@ -1225,7 +1249,8 @@ int o_transport_trace(int gi, const double *src, uint64_t seed, int64_t tid, dou
     ++n;
     x[0] += sph * u[0]; x[1] += sph * u[1]; x[2] += sph * u[2];
     nzero = 0;
-    double U = rng_u(&rp);
+    double U, W;
+    rng_pair(&rp, &U, &W);
     if (U * mu < mupe) break;
     double eta, cost, cph, sph2;
     kahn(E, &rp, &eta, &cost);
@@ -1234,7 +1259,7 @@ int o_transport_trace(int gi, const double *src, uint64_t seed, int64_t tid, dou
     double E1 = E / eta;
     if (E1 < cutoff) break;
     E = E1;
-    Y = -log(rng_u(&rp));
+    Y = -log(W);
   }
   return (int)n;
 }

@@ -1666,14 +1666,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// The 53-bit integer m of one Philox block (counter (draw, id lo, id hi, stream)): the
-// uniform in (0, 1] is m 2^-53.  Out of line: its ~100 instructions would otherwise be
-// repeated at each of the ~15 draw sites of the transport kernel (measured: 1.5 % faster).
-__device__ __noinline__ uint64_t philox_m53(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw) {
+// The two 53-bit integers of one Philox block (counter (draw, id lo, id hi, stream)): the
+// uniforms in (0, 1] are a 2^-53 (from x1:x0) and b 2^-53 (from x3:x2).  A draw site takes
+// whole blocks; a single uniform uses a.  Out of line: its ~100 instructions would otherwise
+// be repeated at each of the draw sites of the transport kernel.
+struct M53x2 {
+  uint64_t a, b;
+};
+
+__device__ __noinline__ M53x2 philox_m53_pair(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw) {
   const uint4 x = philox4x32_10(make_uint4(draw++, (uint32_t)(uint64_t)tid, (uint32_t)((uint64_t)tid >> 32), stream),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-  const uint64_t w = ((uint64_t)x.y << 32) | x.x;
-  return (w >> 11) + 1;
+  const uint64_t wa = ((uint64_t)x.y << 32) | x.x, wb = ((uint64_t)x.w << 32) | x.z;
+  return M53x2{(wa >> 11) + 1, (wb >> 11) + 1};
+}
+
+__device__ __forceinline__ uint64_t philox_m53(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw) {
+  return philox_m53_pair(seed, tid, stream, draw).a;
 }
 
 __device__ __forceinline__ double m53_double(uint64_t m) { return (double)m * 0x1.0p-53; }

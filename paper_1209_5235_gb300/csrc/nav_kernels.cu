@@ -217,15 +217,15 @@ __device__ __forceinline__ int find_item(const DItem *items, int n_items, int64_
   return lo;
 }
 
-// Unit-disc rejection: (cos, sin) of a uniform azimuth.  Points with a^2 + b^2 > 1 + 1e-5 in
-// FP32 (from the Philox integers; error < 2e-6) are rejected without FP64 work; the others
-// take the FP64 test and, if accepted, the FP64 evaluation.
+// Unit-disc rejection: (cos, sin) of a uniform azimuth, one Philox block per trial.  Points
+// with a^2 + b^2 > 1 + 1e-5 in FP32 (from the Philox integers; error < 2e-6) are rejected
+// without FP64 work; the others take the FP64 test and, if accepted, the FP64 evaluation.
 __device__ __forceinline__ bool disc_azimuth(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw, double &c,
                                              double &s) {
 #pragma unroll 1
   for (int t = 0; t < 1000; ++t) {
-    const uint64_t ma = philox_m53(seed, tid, stream, draw);
-    const uint64_t mb = philox_m53(seed, tid, stream, draw);
+    const M53x2 ab = philox_m53_pair(seed, tid, stream, draw);
+    const uint64_t ma = ab.a, mb = ab.b;
     const float af = 2.0f * m53_float(ma) - 1.0f, bf = 2.0f * m53_float(mb) - 1.0f;
     const float r2f = af * af + bf * bf;
     if (r2f > 1.0f + 1e-5f) continue;
@@ -252,8 +252,9 @@ __device__ void make_source(const double *src, uint64_t seed, int64_t tid, V3 &x
     bool ok = false;
 #pragma unroll 1
     for (int t = 0; t < 1000; ++t) {
-      const double a = 2.0 * philox_uniform(seed, tid, 0, draw) - 1.0;
-      const double b = 2.0 * philox_uniform(seed, tid, 0, draw) - 1.0;
+      const M53x2 ab = philox_m53_pair(seed, tid, 0, draw);  // one block per trial
+      const double a = 2.0 * m53_double(ab.a) - 1.0;
+      const double b = 2.0 * m53_double(ab.b) - 1.0;
       const double s = a * a + b * b;
       if (s > 0.0 && s < 1.0) {
         const double f = sqrt(-2.0 * log(s) / s);
@@ -352,8 +353,8 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
 }
 
 // Kahn's rejection method for the Klein-Nishina law of eta = E / E' (three uniforms per
-// trial).  Each comparison of a uniform with its threshold is first made in FP32 and kept
-// when they differ by more than 1e-5.  All three thresholds lie in [0, 1]; their FP32
+// trial: r1, r2 from one Philox block, r3 from the next).  Each comparison of a uniform
+// with its threshold is first made in FP32 and kept when they differ by more than 1e-5.  All three thresholds lie in [0, 1]; their FP32
 // values (written without cancellation: 1 - (eta - 1) / alpha = 1 - 2 (1 - r2) / (1 + 2
 // alpha r2)) and the uniforms' FP32 copies (built from the Philox integers, relative error
 // < 2^-23) are within 2e-6 of the exact ones, so such a decision is the exact one; the
@@ -367,8 +368,8 @@ __device__ __forceinline__ bool kahn(double E, uint64_t seed, int64_t tid, uint3
   const float p1f = (1.0f + 2.0f * alf) / (9.0f + 2.0f * alf);
 #pragma unroll 1
   for (int t = 0; t < 1000; ++t) {
-    const uint64_t m1 = philox_m53(seed, tid, 1, draw);
-    const uint64_t m2 = philox_m53(seed, tid, 1, draw);
+    const M53x2 b12 = philox_m53_pair(seed, tid, 1, draw);
+    const uint64_t m1 = b12.a, m2 = b12.b;
     const uint64_t m3 = philox_m53(seed, tid, 1, draw);
     const float d1 = m53_float(m1) - p1f;
     const bool first = fabsf(d1) > kMargin ? d1 <= 0.f : m53_double(m1) <= (1.0 + 2.0 * al) / (9.0 + 2.0 * al);
@@ -560,7 +561,9 @@ template <int MODE>
 __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   const DItem &it = P.items[t.item];
   const DGeom &G = P.geoms[it.geom];
-  const double U = philox_uniform(P.seed, t.tid, 1, t.draw);
+  // one block per interaction: U chooses the process, W gives the next free path
+  const M53x2 uw = philox_m53_pair(P.seed, t.tid, 1, t.draw);
+  const double U = m53_double(uw.a);
   if (U * t.mu < t.mupe) {
     cnt.c[G4N_C_PHOTO]++;
     tally(P, t, t.leaf, t.E);
@@ -584,7 +587,7 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   }
   tally(P, t, t.leaf, t.E - E1);
   set_energy(G, t, E1);
-  t.Y = -log(philox_uniform(P.seed, t.tid, 1, t.draw));
+  t.Y = -log(m53_double(uw.b));
   if (P.out_hash) t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCompton);
   update_mu(G, t);
   // FP64 mode: the isotropic safety of a leaf without daughters, at the interaction point

@@ -48,10 +48,13 @@ def test_uniform_range_and_law(oracle_lib):
 
 
 def test_uniform_is_top_53_bits_plus_one(oracle_lib):
+    """A block gives two uniforms: the top 53 bits of (x1:x0) and of (x3:x2), each plus one, times 2^-53."""
     seed, tid, stream, draw = 0x0123456789ABCDEF, (7 << 32) + 5, 1, 3
     x = oracle.philox4x32_10([draw, tid & 0xffffffff, tid >> 32, stream], [seed & 0xffffffff, seed >> 32])
-    w = (int(x[1]) << 32) | int(x[0])
-    assert oracle.uniform(seed, tid, stream, draw) == ((w >> 11) + 1) * 2.0 ** -53
+    wa = (int(x[1]) << 32) | int(x[0])
+    wb = (int(x[3]) << 32) | int(x[2])
+    assert oracle.uniform(seed, tid, stream, draw) == ((wa >> 11) + 1) * 2.0 ** -53
+    assert oracle.uniform_pair(seed, tid, stream, draw) == (((wa >> 11) + 1) * 2.0 ** -53, ((wb >> 11) + 1) * 2.0 ** -53)
 
 
 def test_isotropic_source_law(oracle_lib):
