@@ -10,7 +10,9 @@ Metric: navigation steps/s (every track advance, geometry- or physics-limited)
 with tracks/s beside it.  Inputs (geometry tables) are resident before the
 timed region; L2 is flushed between timed steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--tracks T]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--tracks T] [--workload W]
+                  [--autotune 0 --mode M --block B --blocks-per-sm S --refill-min R --interact-min I
+                   --walk-budget K --regroup P]
 
 With --impl reference the FP64 CPU oracle is timed instead, on the host cores,
 on a bounded sample of the same workload.
@@ -51,7 +53,8 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flop
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_transport launch of the default workload,
 # from the ncu capture summarised in profiles/k_transport_fp64_calorimeter_full.md.  It is reported only while
 # the CUDA sources hash to the value they had when the capture was taken (else the kernel has changed since).
-NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"sources_sha256": "3eaaf0cd5eb50ef139130956f1e1d04b0ed1f31deab2b09ebe78bb0db2a444c9",
+               "bytes_per_launch": 1903104 + 9932288}
 
 
 def cuda_sources_sha256() -> str:
@@ -354,7 +357,7 @@ def run_gpu(args):
         for m in mode_names:
             tuned[m] = tune["per_mode"][code[m]]["cfg"]
     manual = dict(block_size=args.block, blocks_per_sm=args.blocks_per_sm, refill_min=args.refill_min,
-                  interact_min=args.interact_min)
+                  interact_min=args.interact_min, walk_budget=args.walk_budget, regroup_period=args.regroup)
     launch = {m: tuned.get(m, manual) for m in mode_names}
     # matched results: the same histories, bit for bit, in every mode (one launch with hashes each)
     ref_h = None
@@ -607,7 +610,7 @@ def run_free_path(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--tracks", type=int, default=1_000_000)
@@ -616,6 +619,8 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--refill-min", type=int, default=0)
     ap.add_argument("--interact-min", type=int, default=0)
+    ap.add_argument("--walk-budget", type=int, default=0)
+    ap.add_argument("--regroup", type=int, default=0)
     ap.add_argument("--mode", default="auto", choices=["auto", "fp64", "fp32_recheck"])
     ap.add_argument("--voxel", default="smart")
     ap.add_argument("--workload", default="calorimeter",

@@ -20,8 +20,8 @@ SPACE = {
     "regroup_period": (1, 2, 4),
     "block_size": (64, 96, 128),
     "blocks_per_sm": (0, 2, 3),
-    "refill_min": (4, 6, 8, 12, 16),
-    "interact_min": (4, 6, 8, 12, 16),
+    "refill_min": (4, 8, 12, 16, 20, 24),
+    "interact_min": (4, 8, 12, 16, 20, 24),
 }
 DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8, "walk_budget": 16,
            "regroup_period": 0}
