@@ -137,3 +137,29 @@ def test_queries_refused_on_host_only_context(g4):
         assert L.g4n_locate(ctx, gid, 1, None, None, None, None, None) == g4.G4N_ERR_STATE
     finally:
         g4.g4n_destroy(ctx)
+
+
+@pytest.mark.parametrize("field,value", [("walk_budget", -1), ("regroup_period", -2), ("refill_min", 33),
+                                         ("interact_min", 40), ("block_size", 48), ("mode", 7)])
+def test_transport_rejects_bad_launch_fields(g4, field, value):
+    """Launch-shape fields are validated on the host before any device work (G4N_ERR_ARG); with valid fields the
+    same call on a host-only context is refused as a device query (G4N_ERR_STATE).  The output pointers are host
+    placeholders that the refused calls never touch."""
+    import ctypes
+    from paper_1209_5235_gb300 import binding
+    ctx = g4.g4n_create(-1)
+    try:
+        gid = g4.build_scene(ctx, synth.scenes.tiny_scene())
+        items = g4.make_items([(gid, 10, 0, synth.scenes.tiny_source(), 0)])
+        edep = np.zeros((100, 13))
+        cnt = np.zeros(g4.G4N_N_COUNTERS, dtype=np.uint64)
+        L = g4.load()
+        d = binding._desc(items, 1, 0.01, 0, 100, 13, 0, 0, 0)
+        assert L.g4n_transport_batch(ctx, ctypes.byref(d), edep.ctypes.data, cnt.ctypes.data, None, None,
+                                     None) == g4.G4N_ERR_STATE
+        setattr(d, field, value)
+        assert L.g4n_transport_batch(ctx, ctypes.byref(d), edep.ctypes.data, cnt.ctypes.data, None, None,
+                                     None) == g4.G4N_ERR_ARG
+        assert g4.g4n_last_error(ctx)
+    finally:
+        g4.g4n_destroy(ctx)
