@@ -301,6 +301,7 @@ def setup_workload(g4, ctx, args, rank):
         entries, off, tid = [], 0, 0
         for s2, nt in synth.scenes.batched_scenes():
             gid = g4.build_scene(ctx, s2)
+            nt = max(1, int(round(nt * args.track_scale)))
             entries.append((gid, nt, rank * 10_000_000 + tid, synth.scenes.batched_source(), off))
             off += s2.n_volumes + 2
             tid += nt
@@ -308,7 +309,7 @@ def setup_workload(g4, ctx, args, rank):
             ["fp64", "fp32_recheck"]
     sc = synth.scenes.nested_barrel_scene() if w == "barrel_nested" else synth.scenes.barrel_scene()
     gid = g4.build_scene(ctx, sc)
-    n = 10_000_000
+    n = int(round(10_000_000 * args.track_scale))
     items = g4.make_items([(gid, n, rank * n, synth.scenes.barrel_source(), 0)])
     seed = synth.scenes.CONFIG_SEEDS[4 if w == "barrel_learned" else 3][1]
     modes = ["fp64", "fp32_recheck"]
@@ -614,6 +615,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--tracks", type=int, default=1_000_000)
+    ap.add_argument("--track-scale", type=float, default=1.0,
+                    help="batched / barrel workloads: fraction of their track counts (profiling a smaller case)")
     ap.add_argument("--ref-tracks", type=int, default=4000)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)

@@ -47,7 +47,7 @@ SCENES = {
 }
 BOX_HALF = {"barrel": (1600.0, 1600.0, 1600.0), "nested_barrel": (1600.0, 1600.0, 1600.0), "calorimeter": (600.0, 600.0, 400.0), "nested_core": (12.0, 12.0, 12.0),
             "segments": (360.0, 360.0, 90.0)}
-AIM = {"segments": 0.8, "mixed_smart": 0.3, "mixed_fixed": 0.3, "mixed_none": 0.3}
+AIM = {"segments": 0.8, "mixed_smart": 0.3, "mixed_fixed": 0.3, "mixed_none": 0.3, "cones": 0.6}
 
 
 def _build(env, name):
@@ -125,6 +125,61 @@ def test_locate_band_edges(env, voxel):
     assert bad.size == 0, f"{bad.size} mismatches, first: {p[bad[0]]!r} {v[bad[0]]!r} gpu {path[bad[0]]} ref {path_ref[bad[0]]}"
     # both outcomes of the band rule occur
     assert 0 < (d_ref == 2).sum() < len(d_ref)
+
+
+def test_locate_cone_bands(env):
+    """Points around the conical surfaces and end faces of cones (offsets along r or z of 0, +-0.3, +-0.7, +-2 and +-3
+    half-tolerances, i.e. on both sides of both band edges) with random directions: located paths agree with the oracle."""
+    g4, torch, ctx = env
+    from synth.scenes import CONE
+    from synth.materials import toy_materials
+    m = toy_materials()
+    cones = [(0.0, 40.0, 0.0, 90.0, 60.0), (20.0, 70.0, 35.0, 50.0, 45.0), (15.0, 60.0, 5.0, 25.0, 30.0)]
+    centres = [(-200.0, 0.0, 0.0), (0.0, 150.0, 50.0), (200.0, -100.0, -80.0)]
+    rot = (math.cos(0.7), math.sin(0.7))
+    solids = [synth.scenes.Solid(synth.scenes.BOX, (400.0, 400.0, 400.0))] + [synth.scenes.Solid(CONE, c) for c in cones]
+    places = [synth.scenes.Placement(-1, 0, 0, (0.0, 0.0, 0.0))] + [
+        synth.scenes.Placement(0, k + 1, 1, centres[k], rot) for k in range(len(cones))]
+    sc = synth.scenes.Scene("cone_bands", [m["water"], m["lead"]], solids, places, VoxelSpec(mode="smart"))
+    og = oracle.Geometry(sc)
+    gid = g4.build_scene(ctx, sc)
+    half = 0.5e-9
+    rng = np.random.default_rng(17)
+    pts, dirs = [], []
+    offs = np.array([0.0, 0.3, -0.3, 0.7, -0.7, 2.0, -2.0, 3.0, -3.0]) * half
+    for _ in range(4000):
+        k = int(rng.integers(len(cones)))
+        rmin1, rmax1, rmin2, rmax2, hz = cones[k]
+        surf = int(rng.integers(3))          # outer cone, inner cone, end face
+        off = offs[int(rng.integers(len(offs)))]
+        ph = rng.uniform(0, 2 * math.pi)
+        if surf == 2:
+            zsign = 1.0 if rng.uniform() < 0.5 else -1.0
+            z = zsign * hz + zsign * off
+            ro, ri = (rmax2, rmin2) if zsign > 0 else (rmax1, rmin1)
+            r = ri + (ro - ri) * rng.uniform(0.05, 0.95)
+        else:
+            z = rng.uniform(-0.95, 0.95) * hz
+            ko, co = (rmax2 - rmax1) / (2 * hz), 0.5 * (rmax1 + rmax2)
+            ki, ci = (rmin2 - rmin1) / (2 * hz), 0.5 * (rmin1 + rmin2)
+            if surf == 1 and rmin1 == 0.0:
+                surf = 0
+            r = (ko * z + co + off) if surf == 0 else (ki * z + ci + off)
+        local = np.array([r * math.cos(ph), r * math.sin(ph), z])
+        c, s_ = rot
+        world = np.array([c * local[0] - s_ * local[1], s_ * local[0] + c * local[1], local[2]]) + np.array(centres[k])
+        pts.append(world)
+        w = rng.normal(size=3)
+        dirs.append(w / np.linalg.norm(w))
+    p, v = np.array(pts), np.array(dirs)
+    d_ref, path_ref = og.locate_many(p, v)
+    d, path = g4.g4n_locate(ctx, gid, to_soa(p, torch), to_soa(v, torch))
+    g4.g4n_sync(ctx)
+    d = d.cpu().numpy()
+    path = path.cpu().numpy().T
+    bad = np.nonzero((d != d_ref) | np.any(path != path_ref, axis=1))[0]
+    assert bad.size == 0, f"{bad.size} mismatches, first: {p[bad[0]]!r} {v[bad[0]]!r} gpu {path[bad[0]]} ref {path_ref[bad[0]]}"
+    assert 0.2 < (d_ref == 2).mean() < 0.8   # both sides of the surfaces occur
 
 
 MODES = [0, 1, 2]   # G4N_MODE_FP64, G4N_MODE_FP32_RECHECK, G4N_MODE_LEARNED
