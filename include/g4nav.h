@@ -152,6 +152,24 @@ typedef struct {
 } g4n_voxel_params;
 int g4n_voxelize(g4n_ctx *ctx, const g4n_voxel_params *params);
 
+/* Logical volumes (reuse of one volume description in many places, as Geant4's logical volumes;
+ * the paper's CMS geometry is built that way, Sec. 3.5).  A logical volume is a solid and a material
+ * with daughters placed in its own frame.  Placing it (g4n_place_logical) expands its whole subtree
+ * into physical volumes, depth first (the volume, then each daughter's subtree in the order they
+ * were added), with consecutive ids: every volume id is a touchable (one physical path from the
+ * world), the unit the navigation state and the tallies use.  Expansion happens on the host; the
+ * device tables then hold one record per touchable.  A logical volume may not contain itself.
+ * g4n_logical_add_daughter returns the daughter's copy number (its index among the logical
+ * mother's daughters); a logical volume placed with g4n_place_logical has copy number 0, a volume
+ * placed with g4n_place logical volume -1 and copy number -1.  t / rot: HOST pointers as for
+ * g4n_place.  out_first_vol, out_n_vols: the ids [first, first + n) of the expanded volumes.
+ * Logical volumes belong to the geometry being built and are discarded by g4n_geom_finalize. */
+int g4n_logical_create(g4n_ctx *ctx, int32_t solid, int32_t mat, int32_t *out_lv);
+int g4n_logical_add_daughter(g4n_ctx *ctx, int32_t mother_lv, int32_t daughter_lv, const double *t, const double *rot,
+                             int32_t *out_copy);
+int g4n_place_logical(g4n_ctx *ctx, int32_t mother_vol, int32_t lv, const double *t, const double *rot,
+                      int32_t *out_first_vol, int32_t *out_n_vols);
+
 /* Validate the volumes placed since the last finalize (every daughter inside its mother,
  * siblings not overlapping, depth <= G4N_DMAX), build the voxels and upload the tables.
  * Returns the geometry id in *out_geom. */
@@ -160,6 +178,13 @@ int g4n_geom_finalize(g4n_ctx *ctx, int32_t *out_geom);
 /* Table sizes of a finalized geometry (HOST array of 8): n_volumes, n_voxel_headers,
  * n_voxel_slices, n_candidate_lists, n_candidate_entries, device bytes, max depth, materials. */
 int g4n_geom_info(g4n_ctx *ctx, int32_t geom, int64_t *out8);
+
+/* The touchable path of volume `vol` of a finalized geometry: for each level from the world (0)
+ * down to vol, the logical volume and copy number (-1, -1 for volumes placed with g4n_place).
+ * *out_depth = number of levels; at most `cap` levels are written to the HOST arrays out_lv,
+ * out_copy. */
+int g4n_touchable(g4n_ctx *ctx, int32_t geom, int32_t vol, int32_t cap, int32_t *out_lv, int32_t *out_copy,
+                  int32_t *out_depth);
 
 /* ---------------------------------------------------------------- navigation queries (device) */
 

@@ -38,12 +38,13 @@ PARITY_COUNTERS = ["tracks", "steps", "geom_steps", "phys_steps", "photo", "comp
                    "step_limit"]
 
 EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_scale", "g4n_sync", "g4n_material_add",
-            "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_solid_cone", "g4n_place", "g4n_voxelize", "g4n_geom_finalize",
+            "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_solid_cone", "g4n_place",
+            "g4n_logical_create", "g4n_logical_add_daughter", "g4n_place_logical", "g4n_touchable", "g4n_voxelize", "g4n_geom_finalize",
             "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_free_path", "g4n_transport_batch", "g4n_transport_batch_host",
             "g4n_transport_batch_noalloc", "g4n_mlp_load", "g4n_mlp_get", "g4n_mlp_log", "g4n_mlp_train",
             "g4n_mlp_grad", "g4n_mlp_predict", "g4n_graph_create", "g4n_graph_launch", "g4n_graph_destroy"]
 
-__all__ = EXPORTED + ["G4N_FLAG_DIAGNOSTICS", "G4NError", "load", "lib_path", "build_scene", "make_items", "counters_dict", "voxel_params",
+__all__ = EXPORTED + ["G4N_FLAG_DIAGNOSTICS", "G4NError", "load", "lib_path", "build_scene", "build_logical_scene", "make_items", "counters_dict", "voxel_params",
                       "COUNTER_NAMES", "PARITY_COUNTERS", "G4N_DMAX", "G4N_N_COUNTERS", "G4N_MODE_FP64",
                       "G4N_MODE_FP32_RECHECK", "G4N_MODE_LEARNED", "G4N_LIM_PHYSICS", "G4N_LIM_MOTHER",
                       "G4N_ERR_ARG", "G4N_ERR_GEOM", "G4N_ERR_STEP_LIMIT", "G4N_ERR_TIMEOUT", "G4N_ERR_STATE",
@@ -105,6 +106,8 @@ def load():
         "g4n_material_add": [vp, d, i32, vp, vp, vp, vp],
         "g4n_solid_box": [vp, d, d, d, vp], "g4n_solid_tube": [vp, d, d, d, d, d, vp], "g4n_solid_orb": [vp, d, vp],
         "g4n_solid_cone": [vp, d, d, d, d, d, vp],
+        "g4n_logical_create": [vp, i32, i32, vp], "g4n_logical_add_daughter": [vp, i32, i32, vp, vp, vp],
+        "g4n_place_logical": [vp, i32, i32, vp, vp, vp, vp], "g4n_touchable": [vp, i32, i32, i32, vp, vp, vp],
         "g4n_place": [vp, i32, i32, i32, vp, vp, vp], "g4n_voxelize": [vp, ctypes.POINTER(g4n_voxel_params)],
         "g4n_geom_finalize": [vp, vp], "g4n_geom_info": [vp, i32, vp],
         "g4n_locate": [vp, i32, i64, vp, vp, vp, vp, vp],
@@ -229,6 +232,61 @@ def g4n_place(ctx, mother: int, solid: int, mat: int, t: Sequence[float], rot: O
     _check(ctx, load().g4n_place(ctx, int(mother), int(solid), int(mat), tt.ctypes.data,
                                  rr.ctypes.data if rr is not None else None, ctypes.byref(out)))
     return out.value
+
+
+def _rot(rot):
+    return (ctypes.c_double * 2)(*[float(x) for x in rot]) if rot is not None else None
+
+
+def g4n_logical_create(ctx, solid: int, mat: int) -> int:
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_logical_create(ctx, int(solid), int(mat), ctypes.byref(out)))
+    return out.value
+
+
+def g4n_logical_add_daughter(ctx, mother_lv: int, daughter_lv: int, t: Sequence[float],
+                             rot: Optional[Sequence[float]] = None) -> int:
+    tt = (ctypes.c_double * 3)(*[float(x) for x in t])
+    out = ctypes.c_int32()
+    _check(ctx, load().g4n_logical_add_daughter(ctx, int(mother_lv), int(daughter_lv), tt, _rot(rot), ctypes.byref(out)))
+    return out.value
+
+
+def g4n_place_logical(ctx, mother: int, lv: int, t: Sequence[float], rot: Optional[Sequence[float]] = None):
+    """Returns (first volume id, number of volumes) of the expanded subtree."""
+    tt = (ctypes.c_double * 3)(*[float(x) for x in t])
+    first, n = ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, load().g4n_place_logical(ctx, int(mother), int(lv), tt, _rot(rot), ctypes.byref(first), ctypes.byref(n)))
+    return first.value, n.value
+
+
+def g4n_touchable(ctx, geom: int, vol: int):
+    """[(logical volume, copy number)] from the world down to vol."""
+    lv = (ctypes.c_int32 * G4N_DMAX)()
+    cp = (ctypes.c_int32 * G4N_DMAX)()
+    depth = ctypes.c_int32()
+    _check(ctx, load().g4n_touchable(ctx, int(geom), int(vol), G4N_DMAX, lv, cp, ctypes.byref(depth)))
+    return [(lv[k], cp[k]) for k in range(depth.value)]
+
+
+def build_logical_scene(ctx, base, logicals, placements) -> int:
+    """Marshal a scene whose base placements are given directly and whose logical volumes
+    (synth.scenes.LogicalVolume) are placed through the logical-volume calls; geometry id."""
+    mats = [g4n_material_add(ctx, m.density, m.energies, m.mu_compton, m.mu_photo) for m in base.materials]
+    solids = []
+    for s in base.solids:
+        f = {G4N_BOX: g4n_solid_box, G4N_TUBE: g4n_solid_tube, G4N_CONE: g4n_solid_cone}.get(s.kind, g4n_solid_orb)
+        solids.append(f(ctx, *s.params))
+    for pl in base.placements:
+        g4n_place(ctx, pl.mother, solids[pl.solid], mats[pl.material], pl.t, pl.rot)
+    lvs = [g4n_logical_create(ctx, solids[lv.solid], mats[lv.material]) for lv in logicals]
+    for k, lv in enumerate(logicals):
+        for d in lv.daughters:
+            g4n_logical_add_daughter(ctx, lvs[k], lvs[d.lv], d.t, d.rot)
+    for p in placements:
+        g4n_place_logical(ctx, p.mother, lvs[p.lv], p.t, p.rot)
+    g4n_voxelize(ctx, voxel_params(base.voxel))
+    return g4n_geom_finalize(ctx)
 
 
 def voxel_params(spec) -> g4n_voxel_params:

@@ -172,6 +172,7 @@ struct HGeom {
   std::vector<DKeyBox> kbox;
   std::vector<int64_t> skey;
   std::vector<DFace> face;
+  std::vector<int32_t> touch_lv, touch_copy;  // per volume (touchable): logical volume, copy number
   int32_t max_depth = 0;
   // device blob
   void *blob = nullptr;
@@ -179,16 +180,34 @@ struct HGeom {
   DGeom dview{};
 };
 
+// A logical volume: a solid and a material with daughters placed in its own frame (reused
+// wherever the logical volume is placed).
+struct HLogDaughter {
+  int32_t lv;
+  double t[3], c, s;
+};
+struct HLogical {
+  int32_t solid, mat;
+  std::vector<HLogDaughter> dau;
+};
+
 struct Builder {
   std::vector<HMat> mats;
   std::vector<HSolid> solids;
   std::vector<HPlace> places;
+  std::vector<HLogical> lvs;
+  // per placement: the logical volume it expands (-1: placed directly) and its copy number
+  // (index among the logical mother's daughters; 0 for a logical volume placed directly)
+  std::vector<int32_t> touch_lv, touch_copy;
   g4n_voxel_params vox{0, 0, {0, 1, 2}, {0, 0, 0}, 2.0, 1000, 4};
   bool vox_set = false;
   void clear() {
     mats.clear();
     solids.clear();
     places.clear();
+    lvs.clear();
+    touch_lv.clear();
+    touch_copy.clear();
     vox_set = false;
   }
 };

@@ -602,7 +602,130 @@ int g4n_place(g4n_ctx *ctx, int32_t mother, int32_t solid, int32_t mat, const do
   p.s = rot ? rot[1] : 0.0;
   if (!(std::fabs(p.c * p.c + p.s * p.s - 1.0) <= 1e-12)) return g4n_fail(ctx, G4N_ERR_ARG, "place: rotation (cos, sin) not unit");
   B.places.push_back(p);
+  B.touch_lv.push_back(-1);
+  B.touch_copy.push_back(-1);
   *out_vol = (int32_t)B.places.size() - 1;
+  return G4N_OK;
+}
+
+// ---------------------------------------------------------------- logical volumes (reuse)
+
+static bool read_placement(g4n_ctx *ctx, const double *t, const double *rot, double *tt, double *c, double *s,
+                           const char *who) {
+  for (int i = 0; i < 3; ++i) {
+    if (!std::isfinite(t[i])) {
+      g4n_fail(ctx, G4N_ERR_ARG, std::string(who) + ": non-finite translation");
+      return false;
+    }
+    tt[i] = t[i];
+  }
+  *c = rot ? rot[0] : 1.0;
+  *s = rot ? rot[1] : 0.0;
+  if (!(std::fabs(*c * *c + *s * *s - 1.0) <= 1e-12)) {
+    g4n_fail(ctx, G4N_ERR_ARG, std::string(who) + ": rotation (cos, sin) not unit");
+    return false;
+  }
+  return true;
+}
+
+int g4n_logical_create(g4n_ctx *ctx, int32_t solid, int32_t mat, int32_t *out_lv) {
+  if (!ctx || !out_lv) return g4n_fail(ctx, G4N_ERR_ARG, "logical_create: null argument");
+  auto &B = ctx->b;
+  if (solid < 0 || solid >= (int32_t)B.solids.size()) return g4n_fail(ctx, G4N_ERR_ARG, "logical_create: bad solid id");
+  if (mat < 0 || mat >= (int32_t)B.mats.size()) return g4n_fail(ctx, G4N_ERR_ARG, "logical_create: bad material id");
+  B.lvs.push_back({solid, mat, {}});
+  *out_lv = (int32_t)B.lvs.size() - 1;
+  return G4N_OK;
+}
+
+// Does logical volume `from` contain `target` anywhere in its subtree (or is it)?
+static bool lv_reaches(const std::vector<HLogical> &lvs, int32_t from, int32_t target) {
+  if (from == target) return true;
+  for (const HLogDaughter &d : lvs[from].dau)
+    if (lv_reaches(lvs, d.lv, target)) return true;
+  return false;
+}
+
+int g4n_logical_add_daughter(g4n_ctx *ctx, int32_t mother_lv, int32_t daughter_lv, const double *t, const double *rot,
+                             int32_t *out_copy) {
+  if (!ctx || !t || !out_copy) return g4n_fail(ctx, G4N_ERR_ARG, "logical_add_daughter: null argument");
+  auto &B = ctx->b;
+  const int32_t n = (int32_t)B.lvs.size();
+  if (mother_lv < 0 || mother_lv >= n || daughter_lv < 0 || daughter_lv >= n)
+    return g4n_fail(ctx, G4N_ERR_ARG, "logical_add_daughter: bad logical volume id");
+  if (lv_reaches(B.lvs, daughter_lv, mother_lv))
+    return g4n_fail(ctx, G4N_ERR_ARG, "logical_add_daughter: a logical volume cannot contain itself");
+  HLogDaughter d;
+  d.lv = daughter_lv;
+  if (!read_placement(ctx, t, rot, d.t, &d.c, &d.s, "logical_add_daughter")) return G4N_ERR_ARG;
+  B.lvs[mother_lv].dau.push_back(d);
+  *out_copy = (int32_t)B.lvs[mother_lv].dau.size() - 1;
+  return G4N_OK;
+}
+
+// Expand logical volume lv placed in physical volume `mother` (depth first: the volume, then each
+// daughter's subtree in order); returns false after g4n_fail on a depth overflow.
+static bool expand_logical(g4n_ctx *ctx, int32_t mother, int32_t lv, int32_t copy, const double *t, double c, double s,
+                           int level) {
+  auto &B = ctx->b;
+  if (level >= kDMax) {
+    g4n_fail(ctx, G4N_ERR_GEOM, "place_logical: expansion deeper than G4N_DMAX");
+    return false;
+  }
+  HPlace p;
+  p.mother = mother;
+  p.solid = B.lvs[lv].solid;
+  p.mat = B.lvs[lv].mat;
+  for (int i = 0; i < 3; ++i) p.t[i] = t[i];
+  p.c = c;
+  p.s = s;
+  B.places.push_back(p);
+  B.touch_lv.push_back(lv);
+  B.touch_copy.push_back(copy);
+  const int32_t me = (int32_t)B.places.size() - 1;
+  const std::vector<HLogDaughter> dau = B.lvs[lv].dau;  // copy: B.places grows below
+  for (size_t k = 0; k < dau.size(); ++k)
+    if (!expand_logical(ctx, me, dau[k].lv, (int32_t)k, dau[k].t, dau[k].c, dau[k].s, level + 1)) return false;
+  return true;
+}
+
+int g4n_place_logical(g4n_ctx *ctx, int32_t mother, int32_t lv, const double *t, const double *rot,
+                      int32_t *out_first_vol, int32_t *out_n_vols) {
+  if (!ctx || !t || !out_first_vol || !out_n_vols) return g4n_fail(ctx, G4N_ERR_ARG, "place_logical: null argument");
+  auto &B = ctx->b;
+  if (lv < 0 || lv >= (int32_t)B.lvs.size()) return g4n_fail(ctx, G4N_ERR_ARG, "place_logical: bad logical volume id");
+  if (B.places.empty() ? mother != -1 : (mother < 0 || mother >= (int32_t)B.places.size()))
+    return g4n_fail(ctx, G4N_ERR_ARG, "place_logical: the first placement is the world (mother -1), later ones need a placed mother");
+  double tt[3], c, s;
+  if (!read_placement(ctx, t, rot, tt, &c, &s, "place_logical")) return G4N_ERR_ARG;
+  const size_t first = B.places.size();
+  if (!expand_logical(ctx, mother, lv, 0, tt, c, s, 0)) {
+    B.places.resize(first);
+    B.touch_lv.resize(first);
+    B.touch_copy.resize(first);
+    return G4N_ERR_GEOM;
+  }
+  *out_first_vol = (int32_t)first;
+  *out_n_vols = (int32_t)(B.places.size() - first);
+  return G4N_OK;
+}
+
+int g4n_touchable(g4n_ctx *ctx, int32_t geom, int32_t vol, int32_t cap, int32_t *out_lv, int32_t *out_copy,
+                  int32_t *out_depth) {
+  if (!ctx || !out_depth || (cap > 0 && (!out_lv || !out_copy)) || cap < 0)
+    return g4n_fail(ctx, G4N_ERR_ARG, "touchable: bad arguments");
+  if (geom < 0 || geom >= (int32_t)ctx->geoms.size()) return g4n_fail(ctx, G4N_ERR_ARG, "touchable: bad geometry id");
+  const HGeom *g = ctx->geoms[geom];
+  if (vol < 0 || vol >= (int32_t)g->vol.size()) return g4n_fail(ctx, G4N_ERR_ARG, "touchable: bad volume id");
+  const int depth = g->vol[vol].depth;
+  *out_depth = depth;
+  // the chain from the world (level 0) down to vol
+  for (int32_t v = vol, k = depth - 1; v >= 0; v = g->vol[v].mother, --k) {
+    if (k < cap) {
+      out_lv[k] = g->touch_lv[v];
+      out_copy[k] = g->touch_copy[v];
+    }
+  }
   return G4N_OK;
 }
 
@@ -868,6 +991,9 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
     }
   }
   if (g->face.empty()) g->face.push_back(DFace{});
+  // --- touchables: the logical volume and copy number of every volume
+  g->touch_lv = B.touch_lv;
+  g->touch_copy = B.touch_copy;
   // --- FP32 copies of the voxel headers
   g->hdr32.resize(g->hdr.size());
   for (size_t h = 0; h < g->hdr.size(); ++h) {

@@ -439,3 +439,78 @@ def layered_scene(thicknesses: list, materials: list, half_xy: float = 1.0e5) ->
         places.append(Placement(0, len(solids) - 1, 1 + k, (0.0, 0.0, z + th / 2.0)))
         z += th
     return Scene("layered", mats, solids, places, VoxelSpec(mode="none"))
+
+
+# ---------------------------------------------------------------- logical volumes (reuse)
+
+@dataclasses.dataclass
+class LogicalDaughter:
+    lv: int                   # index of the daughter logical volume
+    t: tuple                  # translation in the logical mother's frame
+    rot: tuple = (1.0, 0.0)
+
+
+@dataclasses.dataclass
+class LogicalVolume:
+    solid: int
+    material: int
+    daughters: list
+
+
+@dataclasses.dataclass
+class LogicalPlacement:
+    mother: int               # physical volume of the base scene (or an earlier expansion)
+    lv: int
+    t: tuple
+    rot: tuple = (1.0, 0.0)
+
+
+def expand_logical(base: Scene, logicals: list, placements: list):
+    """The flat scene of a base scene plus placed logical volumes: each placement expands its
+    logical volume's subtree depth first (the volume, then its daughters' subtrees in order).
+    Returns (scene, touchable) where touchable[v] = (logical volume, copy number) of volume v
+    ((-1, -1) for the base placements)."""
+    places = list(base.placements)
+    touch = [(-1, -1)] * len(places)
+
+    def expand(mother, lv, copy, t, rot):
+        L = logicals[lv]
+        places.append(Placement(mother, L.solid, L.material, tuple(t), tuple(rot)))
+        touch.append((lv, copy))
+        me = len(places) - 1
+        for k, d in enumerate(L.daughters):
+            expand(me, d.lv, k, d.t, d.rot)
+
+    for p in placements:
+        expand(p.mother, p.lv, 0, p.t, p.rot)
+    return Scene(base.name + "_expanded", base.materials, base.solids, places, base.voxel), touch
+
+
+def modular_calorimeter(n_mod: int = 2, n_tower: int = 4, n_pairs: int = 10):
+    """A sampling calorimeter built from reused logical volumes: modules of n_tower x n_tower towers, each
+    tower a stack of n_pairs (lead 5 mm + scintillator 10 mm) cells, n_mod x n_mod modules in a vacuum
+    world.  Depth: world, module, tower, pair, cell.  Returns (base scene, logical volumes, placements)."""
+    mats, mi = _std_materials()
+    cell_xy, pb, sc = 20.0, 2.5, 5.0
+    pair_hz = pb + sc
+    tower_hz = n_pairs * pair_hz
+    mod_half = n_tower * cell_xy
+    solids = [Solid(BOX, (1000.0, 1000.0, 1000.0)),
+              Solid(BOX, (cell_xy, cell_xy, pb)), Solid(BOX, (cell_xy, cell_xy, sc)),
+              Solid(BOX, (cell_xy, cell_xy, pair_hz)), Solid(BOX, (cell_xy, cell_xy, tower_hz)),
+              Solid(BOX, (mod_half, mod_half, tower_hz))]
+    base = Scene("modular_calorimeter", mats, solids, [Placement(-1, 0, mi["vacuum"], (0.0, 0.0, 0.0))],
+                 VoxelSpec(mode="smart"))
+    lv_pb = LogicalVolume(1, mi["lead"], [])
+    lv_sc = LogicalVolume(2, mi["scint"], [])
+    lv_pair = LogicalVolume(3, mi["vacuum"], [LogicalDaughter(0, (0.0, 0.0, -sc)), LogicalDaughter(1, (0.0, 0.0, pb))])
+    lv_tower = LogicalVolume(4, mi["vacuum"], [LogicalDaughter(2, (0.0, 0.0, -tower_hz + pair_hz * (2 * k + 1)))
+                                               for k in range(n_pairs)])
+    lv_mod = LogicalVolume(5, mi["vacuum"], [LogicalDaughter(3, (-mod_half + cell_xy * (2 * i + 1),
+                                                                 -mod_half + cell_xy * (2 * j + 1), 0.0))
+                                             for i in range(n_tower) for j in range(n_tower)])
+    logicals = [lv_pb, lv_sc, lv_pair, lv_tower, lv_mod]
+    placements = [LogicalPlacement(0, 4, (-n_mod * mod_half + mod_half * (2 * i + 1),
+                                         -n_mod * mod_half + mod_half * (2 * j + 1), tower_hz))
+                  for i in range(n_mod) for j in range(n_mod)]
+    return base, logicals, placements

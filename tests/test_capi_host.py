@@ -163,3 +163,54 @@ def test_transport_rejects_bad_launch_fields(g4, field, value):
         assert g4.g4n_last_error(ctx)
     finally:
         g4.g4n_destroy(ctx)
+
+
+def test_logical_volumes_expand_into_touchables(g4):
+    """Placing reused logical volumes gives the same geometry as writing the expanded placements out (an
+    independent expansion in synth), with the touchable path (logical volume, copy number) of every volume."""
+    base, lvs, pls = synth.scenes.modular_calorimeter()
+    flat, touch = synth.scenes.expand_logical(base, lvs, pls)
+    ctx = g4.g4n_create(-1)
+    try:
+        gid = g4.build_logical_scene(ctx, base, lvs, pls)
+        gid_flat = g4.build_scene(ctx, flat)
+        assert g4.g4n_geom_info(ctx, gid) == g4.g4n_geom_info(ctx, gid_flat)
+        assert g4.g4n_geom_info(ctx, gid)["n_volumes"] == flat.n_volumes == 1 + 4 * (1 + 16 * (1 + 10 * 3))
+        for v in range(flat.n_volumes):
+            chain, x = [], v
+            while x >= 0:
+                chain.append(touch[x])
+                x = flat.placements[x].mother
+            assert g4.g4n_touchable(ctx, gid, v) == chain[::-1]
+    finally:
+        g4.g4n_destroy(ctx)
+
+
+def test_logical_volume_errors(g4):
+    ctx = g4.g4n_create(-1)
+    try:
+        m = g4.g4n_material_add(ctx, 1.0, [1, 2], [0, 0], [0, 0])
+        s = g4.g4n_solid_box(ctx, 10, 10, 10)
+        a = g4.g4n_logical_create(ctx, s, m)
+        b = g4.g4n_logical_create(ctx, s, m)
+        g4.g4n_logical_add_daughter(ctx, a, b, [0, 0, 0])
+        for mother, daughter in ((b, a), (a, a)):          # a logical volume may not contain itself
+            with pytest.raises(g4.G4NError) as e:
+                g4.g4n_logical_add_daughter(ctx, mother, daughter, [0, 0, 0])
+            assert e.value.code == -1
+        with pytest.raises(g4.G4NError) as e:
+            g4.g4n_logical_create(ctx, 7, m)
+        assert e.value.code == -1
+        with pytest.raises(g4.G4NError) as e:
+            g4.g4n_place_logical(ctx, 3, a, [0, 0, 0])     # no world yet: the first placement has mother -1
+        assert e.value.code == -1
+        # a chain of nested logical volumes deeper than the hierarchy limit
+        chain = [g4.g4n_logical_create(ctx, g4.g4n_solid_box(ctx, 500.0 - k, 500.0 - k, 500.0 - k), m)
+                 for k in range(g4.G4N_DMAX + 1)]
+        for k in range(g4.G4N_DMAX):
+            g4.g4n_logical_add_daughter(ctx, chain[k], chain[k + 1], [0, 0, 0])
+        with pytest.raises(g4.G4NError) as e:
+            g4.g4n_place_logical(ctx, -1, chain[0], [0, 0, 0])
+        assert e.value.code == -2
+    finally:
+        g4.g4n_destroy(ctx)
