@@ -232,7 +232,9 @@ int g4n_free_path(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, cons
 /* ---------------------------------------------------------------- transport (device) */
 
 /* Per-track source.  Every random quantity is drawn from Philox4x32-10 keyed by the 64-bit seed
- * with counter (draw, track id lo, track id hi, stream 0); one uniform in (0, 1] per block.
+ * with counter (block, track id lo, track id hi, stream 0); a block gives two uniforms in (0, 1]
+ * (the top 53 bits of x1:x0 and of x3:x2, plus one, times 2^-53): a rejection trial of the spot
+ * or the azimuth uses both, every single draw (z, cos theta, energy) the first of a new block.
  * Position = pos, plus a Gaussian spot of sigma spot_sigma in x and y (Marsaglia polar method) if
  * spot_sigma > 0, with z uniform in [z0, z1] if has_z.  Direction: isotropic (cos theta uniform,
  * azimuth by rejection on the unit disc) or dir.  Energy: e_kind 0 mono e0, 1 uniform [e0, e1],

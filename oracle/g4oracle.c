@@ -22,8 +22,9 @@
  *  - free_path: Algorithm 1 exactly, returning T for a given Y.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
- * 64-bit seed, counter = (draw, track id lo, track id hi, stream).  One
- * uniform in (0, 1] per block.  Written here from the published definition.
+ * 64-bit seed, counter = (block, track id lo, track id hi, stream).  Two
+ * uniforms in (0, 1] per block (from x1:x0 and x3:x2); every draw site takes
+ * whole blocks.  Written here from the published definition.
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -fopenmp -shared -fPIC.
  * Every floating-point operation is an IEEE double operation evaluated in
