@@ -404,7 +404,11 @@ def run_gpu(args):
     g4.g4n_sync(ctx, stream)
     cdiag = g4.counters_dict(cnt)
     # end to end through the host-buffer entry point: H2D of the batch description, D2H of the tallies
-    e2e_steps, e2e_t, out = 0, 0.0, None
+    # the host result buffers are pinned (page-locked) memory, as a caller streaming results would use
+    out = {"edep": torch.zeros((nb, stride), dtype=torch.float64).pin_memory().numpy(),
+           "counters": torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64).pin_memory().numpy().view(np.uint64),
+           "hashes": None, "lengths": None}
+    e2e_steps, e2e_t = 0, 0.0
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         out = g4.g4n_transport_batch_host(ctx, items, seed + k, stride, n_batches=nb, mode=mode, stream=stream,
