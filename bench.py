@@ -50,11 +50,12 @@ FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_transport launch of the default workload,
-# from the ncu capture summarised in profiles/k_transport_fp64_calorimeter_full.md.  It is reported only while
-# the CUDA sources hash to the value they had when the capture was taken (else the kernel has changed since).
-NCU_TRAFFIC = {"sources_sha256": "3eaaf0cd5eb50ef139130956f1e1d04b0ed1f31deab2b09ebe78bb0db2a444c9",
-               "bytes_per_launch": 1903104 + 9932288}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_transport launch of the default workload:
+# a single-pass ncu capture of the first timed launch (after the 256 MB L2 flush, whose dirty lines are written back
+# during the launch), summarised in profiles/k_transport_fp64_calorimeter_full.md.  It is reported only while the
+# CUDA sources hash to the value they had when the capture was taken (else the kernel has changed since).
+NCU_TRAFFIC = {"sources_sha256": "624d1c666637fcb3b1487593100914c608504bb63f4a16c6503fc3af6028c3f3",
+               "bytes_per_launch": 2187008 + 19130624}
 
 
 def cuda_sources_sha256() -> str:
