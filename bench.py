@@ -204,6 +204,30 @@ def cpu_baseline(sc, src, seed, target_s: float = 12.0) -> dict:
                       f"OpenMP over tracks"}
 
 
+def cpu_baseline_batched(target_s: float = 12.0) -> dict:
+    """The oracle on the batched worlds: a bounded sample of each geometry's tracks, geometries in order, until
+    the time target; steps/s over the whole sample."""
+    import oracle
+    import synth
+    threads = os.cpu_count() or 1
+    src, seed = synth.scenes.batched_source(), synth.scenes.CONFIG_SEEDS[2][1]
+    dt, steps, n_tracks, n_geo = 0.0, 0, 0, 0
+    for s2, nt in synth.scenes.batched_scenes():
+        if dt >= target_s:
+            break
+        og = oracle.Geometry(s2)
+        n = min(nt, 2000)
+        t0 = time.perf_counter()
+        r = og.transport(src, seed, n, tid0=n_tracks, want_hash=False, want_len=False, threads=threads)
+        dt += time.perf_counter() - t0
+        steps += int(r["counters"][1])
+        n_tracks += n
+        n_geo += 1
+    return {"value": steps / dt, "unit": "steps/s", "cores": threads, "kind": "oracle", "tracks_per_s": n_tracks / dt,
+            "seconds": dt, "sample": f"up to 2000 tracks of each of the first {n_geo} of the 256 worlds ({n_tracks} "
+                                     f"histories), brute-force FP64 oracle, OpenMP over tracks"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -466,8 +490,15 @@ def run_gpu(args):
     }
     if getattr(args, "train_losses", None):
         line["learned"] = {"train_samples": args.train_samples, "epoch_losses": args.train_losses}
-    if not args.no_cpu_baseline and world == 1 and args.workload == "calorimeter":
-        line["cpu_baseline"] = cpu_baseline(*calorimeter(args.voxel))
+    if not args.no_cpu_baseline and world == 1:
+        import synth
+        if args.workload == "calorimeter":
+            line["cpu_baseline"] = cpu_baseline(*calorimeter(args.voxel))
+        elif args.workload == "batched":
+            line["cpu_baseline"] = cpu_baseline_batched()
+        elif args.workload.startswith("barrel"):
+            sc = synth.scenes.nested_barrel_scene() if args.workload == "barrel_nested" else synth.scenes.barrel_scene()
+            line["cpu_baseline"] = cpu_baseline(sc, synth.scenes.barrel_source(), seed)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
