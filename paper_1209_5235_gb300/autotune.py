@@ -53,10 +53,10 @@ def autotune(ctx, items, stride, seed, modes=(b.G4N_MODE_FP64, b.G4N_MODE_FP32_R
     space = space or SPACE
     edep = torch.zeros((n_batches, stride), dtype=torch.float64, device="cuda")
     cnt = torch.zeros(b.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
-    t_end = time.perf_counter() + budget_s
     trials = []
     per_mode = {}
     for mode in modes:
+        t_end = time.perf_counter() + budget_s / len(modes)   # each mode gets its share of the budget
         time_launch(ctx, items, seed, edep, cnt, mode, DEFAULT, reps=1, stream=stream)   # warm-up
         cfg = dict(DEFAULT)
         best = time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps, stream)
