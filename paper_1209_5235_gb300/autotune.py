@@ -10,6 +10,7 @@ binding.
 """
 from __future__ import annotations
 
+import ctypes
 import itertools
 import time
 
@@ -46,11 +47,28 @@ def time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps=2, stream=None):
     return ts[len(ts) // 2]
 
 
+def subset_items(items, max_tracks):
+    """The batch's items with their track counts scaled down to about `max_tracks` in total
+    (every non-empty item keeps at least one track; ids and tally columns unchanged)."""
+    total = sum(int(w.n_tracks) for w in items)
+    if max_tracks <= 0 or total <= max_tracks:
+        return items
+    out = (b.g4n_work_item * len(items))()
+    for k, w in enumerate(items):
+        ctypes.pointer(out[k])[0] = w
+        if w.n_tracks > 0:
+            out[k].n_tracks = max(1, int(w.n_tracks) * max_tracks // total)
+    return out
+
+
 def autotune(ctx, items, stride, seed, modes=(b.G4N_MODE_FP64, b.G4N_MODE_FP32_RECHECK), n_batches=100, reps=2,
-             budget_s=30.0, space=None, stream=None):
-    """Best (mode, launch shape) for the batch; returns dict(mode, cfg, ms, per_mode, trials)."""
+             budget_s=30.0, space=None, stream=None, max_tracks=2_000_000):
+    """Best (mode, launch shape) for the batch; returns dict(mode, cfg, ms, per_mode, trials).
+    Batches of more than `max_tracks` tracks are tuned on a proportional subset (shorter
+    trials, so that the budget covers the whole search)."""
     import torch
     space = space or SPACE
+    items = subset_items(items, max_tracks)
     edep = torch.zeros((n_batches, stride), dtype=torch.float64, device="cuda")
     cnt = torch.zeros(b.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
     trials = []
