@@ -198,10 +198,23 @@ def cpu_baseline(sc, src, seed, target_s: float = 12.0) -> dict:
         tid += n
         n2 += n
         n *= 2
-    return {"value": steps / dt, "unit": "steps/s", "cores": int(r["threads"]), "kind": "oracle",
-            "tracks_per_s": n2 / dt, "seconds": dt,
-            "sample": f"{n2} histories (track ids from 10^7) of the same workload, brute-force FP64 oracle, "
-                      f"OpenMP over tracks"}
+    out = {"value": steps / dt, "unit": "steps/s", "cores": int(r["threads"]), "kind": "oracle",
+           "tracks_per_s": n2 / dt, "seconds": dt,
+           "sample": f"{n2} histories (track ids from 10^7) of the same workload, brute-force FP64 oracle, "
+                     f"OpenMP over tracks"}
+    # one thread as well (the paper's 1-thread rows): a smaller sample of the following track ids
+    n, n1, dt1, steps1 = 256, 0, 0.0, 0
+    while dt1 < target_s / 4 and n1 < 10_000_000:
+        t0 = time.perf_counter()
+        r = og.transport(src, seed, n, tid0=tid, want_hash=False, want_len=False, threads=1)
+        dt1 += time.perf_counter() - t0
+        steps1 += int(r["counters"][1])
+        tid += n
+        n1 += n
+        n *= 2
+    out["single_thread"] = {"value": steps1 / dt1, "unit": "steps/s", "cores": int(r["threads"]),
+                            "tracks_per_s": n1 / dt1, "seconds": dt1, "sample": f"{n1} histories, one thread"}
+    return out
 
 
 def cpu_baseline_batched(target_s: float = 12.0) -> dict:
