@@ -59,6 +59,16 @@ __device__ __forceinline__ bool bad_dir(const V3 &u) {
 
 __device__ __forceinline__ void flag(uint32_t *status, uint32_t bits) { atomicOr(status, bits); }
 
+// Transport kernels with EV count once-per-track events (starts, ends, pushes, interactions) in
+// shared memory, one array per block, so that the per-lane counter registers hold only the per-step
+// counts (registers are what limits these kernels at 4 blocks per SM); the others count in registers.
+__shared__ unsigned long long s_events[G4N_N_COUNTERS];
+template <bool EV>
+__device__ __forceinline__ void event(Counters &cnt, int k) {
+  if (EV) atomicAdd(&s_events[k], 1ull);
+  else cnt.c[k]++;
+}
+
 // ---------------------------------------------------------------- locate
 
 __global__ void __launch_bounds__(128) k_locate(const DGeom *__restrict__ geoms, int gid, int64_t n,
@@ -311,7 +321,7 @@ __device__ __forceinline__ void set_direction(Track &t, const V3 &u) {
 // Start track number g of the concatenated items on the lanes with `active` set
 // (warp-collective: locate runs across the warp).  Returns the new phase of the
 // lane: kStep, or kEmpty if the track ended at once (or the lane was not active).
-template <int MODE, bool COUNT>
+template <int MODE, bool COUNT, bool EV>
 __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Counters &cnt) {
   const DGeom *Gp = &P.geoms[P.items[0].geom];
   if (active) {
@@ -325,7 +335,7 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
     make_source(it.src, P.seed, t.tid, t.x, u, E, P.status);
     set_direction(t, u);
     tally(P, t, Gp->n_vol + 1, E);
-    cnt.c[G4N_C_TRACKS]++;
+    event<EV>(cnt, G4N_C_TRACKS);
     t.h = kFnvOffset;
     t.len = 0.0;
     t.steps = 0;
@@ -338,7 +348,7 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
   if (!active) return kEmpty;
   t.leaf = leaf;
   if (leaf < 0) {
-    cnt.c[G4N_C_ESCAPED]++;
+    event<EV>(cnt, G4N_C_ESCAPED);
     tally(P, t, G.n_vol, t.E);
     if (P.out_hash) t.h = hash_step(t.h, -1, G4N_LIM_MOTHER, kEvEscape);
     finish(P, t);
@@ -416,14 +426,14 @@ __device__ __forceinline__ V3 deflect(const V3 &u, double ct, double cph, double
 // (warp-collective): the free path (Eq. 7) races the geometric step; a boundary
 // crossing relocates, a physics end point waits for the interaction phase.
 // Returns the lane's next phase.
-template <int MODE, bool COUNT, bool YIELD>
+template <int MODE, bool COUNT, bool YIELD, bool EV>
 __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, MlpCtx mc, Chain &wch) {
   const bool resume = YIELD && phase == kWalk;  // continue the step's yielded boundary search
   bool act = phase == kStep || resume;
   const DGeom &G = P.geoms[P.items[act ? t.item : 0].geom];
   int next = phase;
   if (act && !resume && t.steps >= P.max_steps) {
-    cnt.c[G4N_C_STEP_LIMIT]++;
+    event<EV>(cnt, G4N_C_STEP_LIMIT);
     flag(P.status, kStStepLimit);
     if (P.out_hash) t.h = hash_step(t.h, t.leaf, kLimStepLimit, kEvStepLimit);
     finish(P, t);
@@ -489,7 +499,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
       }
     }
     ++t.steps;
-    cnt.c[G4N_C_STEPS]++;
+    if (!EV) cnt.c[G4N_C_STEPS]++;  // EV: the sum of the geometry- and physics-limited counts
     t.x.x += s * t.u.x;
     t.x.y += s * t.u.y;
     t.x.z += s * t.u.z;
@@ -528,7 +538,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
         t.x.y += push * t.u.y;
         t.x.z += push * t.u.z;
         if (P.out_len) t.len += push;
-        cnt.c[G4N_C_PUSHES]++;
+        event<EV>(cnt, G4N_C_PUSHES);
         t.nzero = 0;
         pushing = need = true;
         from = leaf;
@@ -540,7 +550,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   if (pushing && P.out_hash) t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
   if (geo) {
     if (leaf < 0) {
-      cnt.c[G4N_C_ESCAPED]++;
+      event<EV>(cnt, G4N_C_ESCAPED);
       tally(P, t, G.n_vol, t.E);
       if (P.out_hash) t.h = hash_step(t.h, -1, lim, kEvEscape);
       finish(P, t);
@@ -557,7 +567,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
 
 // The interaction at the end of a free path: photoabsorption if U mu_tot < mu_photo,
 // else a Compton scatter (Kahn), the cutoff, and a new Y = -log W.
-template <int MODE>
+template <int MODE, bool EV>
 __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   const DItem &it = P.items[t.item];
   const DGeom &G = P.geoms[it.geom];
@@ -565,13 +575,13 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   const M53x2 uw = philox_m53_pair(P.seed, t.tid, 1, t.draw);
   const double U = m53_double(uw.a);
   if (U * t.mu < t.mupe) {
-    cnt.c[G4N_C_PHOTO]++;
+    event<EV>(cnt, G4N_C_PHOTO);
     tally(P, t, t.leaf, t.E);
     if (P.out_hash) t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvPhoto);
     finish(P, t);
     return kEmpty;
   }
-  cnt.c[G4N_C_COMPTON]++;
+  event<EV>(cnt, G4N_C_COMPTON);
   double eta, cost, cph, sph;
   bool ok = kahn(t.E, P.seed, t.tid, t.draw, eta, cost);
   ok &= disc_azimuth(P.seed, t.tid, 1, t.draw, cph, sph);
@@ -579,7 +589,7 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   set_direction(t, deflect(t.u, cost, cph, sph));
   const double E1 = t.E / eta;
   if (E1 < P.cutoff) {
-    cnt.c[G4N_C_CUTOFF]++;
+    event<EV>(cnt, G4N_C_CUTOFF);
     tally(P, t, t.leaf, t.E);
     if (P.out_hash) t.h = hash_step(t.h, t.leaf, G4N_LIM_PHYSICS, kEvCutoff);
     finish(P, t);
@@ -729,9 +739,14 @@ __device__ __forceinline__ void regroup_block(const TParams &P, Track &t, int &p
 // barrel.  The FP32 kernel with yielding searches spills most at 128 registers and keeps 3.
 template <int MODE, bool COUNT, bool YIELD, bool REGROUP>
 __global__ void __launch_bounds__(128, (MODE == kFP32 && YIELD) ? 3 : 4) k_transport(const TParams P) {
+  constexpr bool kEv = !REGROUP;  // the regrouping kernels keep every count in registers
   Counters cnt;
 #pragma unroll
   for (int k = 0; k < G4N_N_COUNTERS; ++k) cnt.c[k] = 0;
+  if (kEv) {
+    for (int k = threadIdx.x; k < G4N_N_COUNTERS; k += blockDim.x) s_events[k] = 0;
+    __syncthreads();
+  }
   const unsigned lane = threadIdx.x & 31u;
   MlpCtx mc{nullptr, nullptr, P.log, 0.f};
   if (MODE == kLearned) {
@@ -770,19 +785,19 @@ __global__ void __launch_bounds__(128, (MODE == kFP32 && YIELD) ? 3 : 4) k_trans
       if (base + __popc(idle) >= (unsigned long long)P.total) drained = true;
       const int64_t g = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
       const bool take = phase == kEmpty && g < P.total;
-      const int started = start_warp<MODE, COUNT>(P, take, g, t, cnt);
+      const int started = start_warp<MODE, COUNT, kEv>(P, take, g, t, cnt);
       if (take) phase = started;
     }
     const unsigned waiting = __ballot_sync(0xffffffffu, phase == kInteract);
     const unsigned stepping = __ballot_sync(0xffffffffu, phase == kStep || phase == kWalk);
     const long long c1 = COUNT ? clock64() : 0;
     if (waiting && (__popc(waiting) >= P.interact_min || stepping == 0)) {
-      if (phase == kInteract) phase = interact<MODE>(P, t, cnt);
+      if (phase == kInteract) phase = interact<MODE, kEv>(P, t, cnt);
     }
     __syncwarp();
     const long long c2 = COUNT ? clock64() : 0;
     const unsigned stepping2 = __ballot_sync(0xffffffffu, phase == kStep || phase == kWalk);
-    if (!REGROUP || stepping2) phase = step_warp<MODE, COUNT, YIELD>(P, t, phase, cnt, mc, wch);
+    if (!REGROUP || stepping2) phase = step_warp<MODE, COUNT, YIELD, kEv>(P, t, phase, cnt, mc, wch);
     if (COUNT) {
       __syncwarp();
       const long long c3 = clock64();
@@ -798,7 +813,14 @@ __global__ void __launch_bounds__(128, (MODE == kFP32 && YIELD) ? 3 : 4) k_trans
     }
     if (!REGROUP && drained && __ballot_sync(0xffffffffu, phase != kEmpty) == 0) break;
   }
-  // flush counters: warp reduction, one atomic per counter per warp
+  // flush counters: the block's event counts, then a warp reduction of the lanes' counts, one atomic
+  // per counter per warp
+  if (kEv) {
+    cnt.c[G4N_C_STEPS] = cnt.c[G4N_C_GEOM_STEPS] + cnt.c[G4N_C_PHYS_STEPS];
+    __syncthreads();
+    for (int k = threadIdx.x; k < G4N_N_COUNTERS; k += blockDim.x)
+      if (s_events[k]) atomicAdd(&P.counters[k], s_events[k]);
+  }
 #pragma unroll
   for (int k = 0; k < G4N_N_COUNTERS; ++k) {
     unsigned long long v = cnt.c[k];
