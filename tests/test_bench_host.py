@@ -1,0 +1,56 @@
+"""Host logic of bench.py (no GPU): clock-record parsing, the traffic figure's source check,
+the algorithmic flop count and the voxel option."""
+import bench
+
+
+def test_clock_summary_reads_clocks_and_reasons():
+    s = bench.ClockSampler(0)
+    s.lines = [
+        "0, 2070, 2070, 812.3, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2040, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    r = s.summary()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_clock_summary_flags_thermal_and_hw_slowdown():
+    s = bench.ClockSampler(0)
+    s.lines = ["0, 1500, 2070, 900, 0x48, Active, Not Active, Active, Not Active"]
+    r = s.summary()
+    assert r["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and r["sm_mhz"] == 1500.0
+
+
+def test_clock_summary_without_samples():
+    r = bench.ClockSampler(0).summary()
+    assert r == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    sha = bench.cuda_sources_sha256()
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "sources_sha256", sha)
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "bytes_per_launch", 1234)
+    assert bench.measured_traffic() == 1234
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "sources_sha256", "0" * 64)
+    assert bench.measured_traffic() is None
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "sources_sha256", sha)
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "bytes_per_launch", None)
+    assert bench.measured_traffic() is None
+
+
+def test_algorithmic_flops_weights_each_counted_event():
+    counts = {k: 0 for k in bench.FLOPS}
+    assert bench.algorithmic_flops(counts) == 0.0
+    for k in bench.FLOPS:
+        c = dict(counts, **{k: 3})
+        assert bench.algorithmic_flops(c) == 3.0 * bench.FLOPS[k]
+    assert bench.algorithmic_flops({k: 1 for k in bench.FLOPS}) == float(sum(bench.FLOPS.values()))
+
+
+def test_voxel_option():
+    assert bench.parse_voxel("default") is None
+    assert bench.parse_voxel("smart").mode == "smart"
+    v = bench.parse_voxel("fixed:2,0:51,11")
+    assert (v.mode, tuple(v.axes), tuple(v.slices)) == ("fixed", (2, 0), (51, 11))
