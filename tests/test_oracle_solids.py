@@ -297,3 +297,43 @@ def test_rejects_bad_cones(oracle_lib):
     for par in [(0, 1, 0, 1, 0), (1, 0.5, 0, 1, 1), (0, 1, 2, 1, 1), (0, 1, 0.5, 2, 1), (-1, 1, 0, 1, 1)]:
         a = np.array(par, dtype=np.float64)
         assert L.o_add_solid(g.gid, CONE, a.ctypes.data) < 0
+
+
+@pytest.mark.parametrize("kind,par", [(BOX, (2.0, 1.0, 0.5)), (ORB, (1.5,)), (TUBE, (0.5, 2.0, 1.0, 0.0, 2 * math.pi))]
+                         + [(TUBE, s) for s in SEGMENTS] + [(CONE, c) for c in CONES])
+def test_reported_crossings_lie_on_the_surface(oracle_lib, kind, par):
+    """At the exit DistanceToOut reports, the point belongs to the solid moving back and not moving on, and
+    DistanceToOut from there is 0; at the entry DistanceToIn reports (chord > 1e-6), the reverse."""
+    g = lab([Solid(kind, par)])
+    pred = lambda q: inside_strict(kind, par, q)
+    rng = np.random.default_rng(4)
+    n_out = n_in = 0
+    for _ in range(20000):
+        if n_out >= 40:
+            break
+        p = rng.uniform(-3, 3, 3)
+        if not pred(p):
+            continue
+        v = random_unit(rng, 1)[0]
+        s = g.solid_dist_out(1, p, v)
+        x = p + s * v
+        assert g.solid_dist_out(1, x, v) <= 1e-9
+        assert not g.solid_inside(1, x, v) and g.solid_inside(1, x, -v), (p, v, s)
+        n_out += 1
+    for _ in range(20000):
+        if n_in >= 40:
+            break
+        p = rng.uniform(-5, 5, 3)
+        if pred(p):
+            continue
+        aim = rng.uniform(-2, 2, 3)
+        v = (aim - p) / np.linalg.norm(aim - p)
+        t = g.solid_dist_in(1, p, v)
+        if t == INF:
+            continue
+        y = p + t * v
+        if g.solid_dist_out(1, y, v) < 1e-6:
+            continue
+        assert g.solid_inside(1, y, v) and not g.solid_inside(1, y, -v), (p, v, t)
+        n_in += 1
+    assert n_out == 40 and n_in == 40
