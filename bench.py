@@ -271,8 +271,9 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream, launch):
-    """W warm-up launches, then K timed launches (CUDA events on the launch stream, L2 flushed between)."""
+def time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream, launch, barrier=None):
+    """W warm-up launches, then K timed launches (CUDA events on the launch stream, L2 flushed between),
+    bracketed by a synchronize and (several ranks) a barrier on both sides."""
     for k in range(args.warmup):
         g4.g4n_transport_batch(ctx, items, seed + 1000 + k, edep, cnt, n_batches=edep.shape[0], mode=mode,
                                stream=stream, **launch)
@@ -281,6 +282,8 @@ def time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream,
     cnt.zero_()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     t_wall = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -289,6 +292,8 @@ def time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream,
                                **launch)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     t_wall = time.perf_counter() - t_wall
     g4.g4n_sync(ctx, stream)
     ms = [a.elapsed_time(b) for a, b in ev]
@@ -418,7 +423,8 @@ def run_gpu(args):
         dist.barrier()
     with ClockSampler(local) as clk:
         for m in mode_names:
-            ms, c, t_wall = time_mode(g4, torch, ctx, items, seed, code[m], args, edep, cnt, flush, stream, launch[m])
+            ms, c, t_wall = time_mode(g4, torch, ctx, items, seed, code[m], args, edep, cnt, flush, stream, launch[m],
+                                      barrier=dist.barrier if dist else None)
             t_dev = sum(ms) / 1e3
             steps_total, tracks_total = c["steps"], c["tracks"]
             if dist:
@@ -566,12 +572,16 @@ def run_free_path(args):
             g4.g4n_sync(ctx, stream)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
             torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
             for k in range(args.steps):
                 flush.fill_(float(k))
                 ev[k][0].record(stream)
                 g4.g4n_free_path(ctx, gid, pos, dirs, Yd, E, mode=code[m], out_T=T, out_steps=st, stream=stream)
                 ev[k][1].record(stream)
             torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
             g4.g4n_sync(ctx, stream)
             ms = [a.elapsed_time(c) for a, c in ev]
             t_dev = sum(ms) / 1e3

@@ -54,3 +54,72 @@ def test_voxel_option():
     assert bench.parse_voxel("smart").mode == "smart"
     v = bench.parse_voxel("fixed:2,0:51,11")
     assert (v.mode, tuple(v.axes), tuple(v.slices)) == ("fixed", (2, 0), (51, 11))
+
+
+class _Event:
+    def __init__(self, **kw):
+        self.t = None
+
+    def record(self, stream=None):
+        _Event.clock += 1.0
+        self.t = _Event.clock
+
+    def elapsed_time(self, end):
+        return end.t - self.t
+
+
+class _FakeTorch:
+    class cuda:
+        Event = _Event
+        syncs = []
+
+        @staticmethod
+        def synchronize():
+            _FakeTorch.cuda.syncs.append(len(_FakeTorch.log))
+
+    log = []
+
+
+class _FakeG4:
+    def __init__(self):
+        self.launches = []
+
+    def g4n_transport_batch(self, ctx, items, seed, edep, cnt, **kw):
+        self.launches.append(seed)
+        _FakeTorch.log.append(("launch", seed))
+
+    def g4n_sync(self, ctx, stream=None):
+        pass
+
+    def counters_dict(self, cnt):
+        return {"steps": 7}
+
+
+class _Arr:
+    shape = (100, 1)
+
+    def zero_(self):
+        pass
+
+    def fill_(self, x):
+        _FakeTorch.log.append(("flush", x))
+
+
+def test_timed_region_is_bracketed_by_synchronize_and_barrier():
+    _Event.clock = 0.0
+    _FakeTorch.log, _FakeTorch.cuda.syncs = [], []
+    calls = []
+    barrier = lambda: calls.append(len(_FakeTorch.log))
+    g4 = _FakeG4()
+
+    class A:
+        warmup, steps = 3, 4
+
+    ms, c, _ = bench.time_mode(g4, _FakeTorch, None, None, 100, 0, A, _Arr(), _Arr(), _Arr(), None, {},
+                               barrier=barrier)
+    assert g4.launches == [1100, 1101, 1102, 100, 101, 102, 103]     # W warm-ups, then exactly K timed launches
+    assert len(ms) == 4 and c == {"steps": 7}
+    first_timed = _FakeTorch.log.index(("flush", 0.0))
+    # a synchronize and a barrier right before the first timed launch and right after the last
+    assert calls == [first_timed, len(_FakeTorch.log)]
+    assert first_timed in _FakeTorch.cuda.syncs and len(_FakeTorch.log) in _FakeTorch.cuda.syncs
