@@ -54,7 +54,7 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flop
 # a single-pass ncu capture of the first timed launch (after the 256 MB L2 flush, whose dirty lines are written back
 # during the launch), summarised in profiles/k_transport_fp64_calorimeter_full.md.  It is reported only while the
 # CUDA sources hash to the value they had when the capture was taken (else the kernel has changed since).
-NCU_TRAFFIC = {"sources_sha256": "e974a1ad3da7b9cc22fd6d1f85cecf0dbd83184e279002d08b5e5f0e16b90b3f",
+NCU_TRAFFIC = {"sources_sha256": "f5b74612af8e56fc1b5b7f15d7be3aee93e6e3a602aff8ff4f7502fce686035d",
                "bytes_per_launch": 2223104 + 41046016}
 
 

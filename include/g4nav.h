@@ -274,7 +274,8 @@ typedef struct {
  * kernel without that code), regroup_period (0 = off: every that many rounds each thread block
  * sorts its tracks by phase and solid kind of the leaf and deals them out again, so that each
  * warp runs one kind of work; FP64 and FP32_RECHECK modes without diagnostics).  flags:
- * G4N_FLAG_DIAGNOSTICS also fills the diagnostic counters (G4N_C_FACE_RELOC and above).  Results
+ * G4N_FLAG_DIAGNOSTICS also fills the diagnostic counters (G4N_C_WALK_YIELDS and above; the
+ * counters below it are always filled).  Results
  * never depend on the launch shape. */
 #define G4N_FLAG_DIAGNOSTICS 1
 typedef struct {
