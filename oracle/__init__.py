@@ -21,7 +21,12 @@ Parity status of each function (how it is pinned, see ``tests/test_oracle_*``):
   * attenuation / free path (Eqs. 2-8): uncollided fraction through a slab vs
     exp(-mu x), and the free-path CDF of a two-layer medium (KS test);
   * Kahn sampling: histogram of E'/E vs the Klein-Nishina differential law;
-  * transport: energy conservation and the closed-form slab limits.
+  * Compton direction change (rotate): unit norm, u.u' = cos theta of Compton's
+    relation from the recorded energies, azimuth uniform and right-handed in an
+    independently built frame, the u = +-z special cases;
+  * transport: energy conservation and the closed-form slab limits; the trace
+    is the transport loop with a recorder, and its hashed records reproduce the
+    history hash, step count and path length.
 """
 from __future__ import annotations
 
@@ -82,7 +87,9 @@ def lib():
             "o_free_path": (d, [i, vp, vp, d, d, vp]),
             "o_free_path_many": (i, [i, i64, vp, vp, d, vp, vp, vp, i]),
             "o_locate_many": (None, [i, i64, vp, vp, vp, vp]),
-            "o_transport_trace": (i, [i, vp, u64, i64, d, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "o_transport_trace": (i, [i, vp, u64, i64, d, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                      vp, vp]),
+            "o_rotate": (None, [vp, d, d, d, vp]),
             "o_compute_step_many": (None, [i, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -162,17 +169,25 @@ class Geometry:
         lib().o_locate_many(self.gid, int(n), _p(_f64(pos)), _p(_f64(dirs)), _p(depth), _p(paths))
         return depth, paths
 
-    def trace(self, source, seed: int, tid: int, cutoff: float = 0.01, cap: int = 100000):
-        """Per-step states of one history: dict of pos, dir, E, path, depth, step, limiter, sphys."""
+    def trace(self, source, seed: int, tid: int, cutoff: float = 0.01, cap: int = 100000,
+              max_steps: int = 1_000_000):
+        """One history as the transport computes it (the same loop, with a recorder): per step the state
+        before it (pos, dir, E, path, depth, sphys = Y / mu) and its outcome (step, limiter, event); the
+        hashed (leaf, limiter, event) records in order; the history's hash, path length and step count."""
         src = _f64(source.as_array())
         pos, dirs = np.zeros((cap, 3)), np.zeros((cap, 3))
         E, steps, sph = np.zeros(cap), np.zeros(cap), np.zeros(cap)
         paths = np.zeros((cap, DMAX), dtype=np.int32)
-        depth, lim = np.zeros(cap, dtype=np.int32), np.zeros(cap, dtype=np.int32)
-        n = lib().o_transport_trace(self.gid, _p(src), ctypes.c_uint64(seed), int(tid), float(cutoff), int(cap),
-                                    _p(pos), _p(dirs), _p(E), _p(paths), _p(depth), _p(steps), _p(lim), _p(sph))
+        depth, lim, ev = np.zeros(cap, dtype=np.int32), np.zeros(cap, dtype=np.int32), np.zeros(cap, dtype=np.int32)
+        rec = np.zeros((2 * cap + 2, 3), dtype=np.int32)
+        nrec, nsteps = np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.int64)
+        h, ln = np.zeros(1, dtype=np.uint64), np.zeros(1)
+        n = lib().o_transport_trace(self.gid, _p(src), ctypes.c_uint64(seed), int(tid), float(cutoff), int(max_steps),
+                                    int(cap), _p(pos), _p(dirs), _p(E), _p(paths), _p(depth), _p(steps), _p(lim),
+                                    _p(sph), _p(ev), _p(rec), _p(nrec), _p(h), _p(ln), _p(nsteps))
         return {"pos": pos[:n], "dir": dirs[:n], "E": E[:n], "path": paths[:n], "depth": depth[:n],
-                "step": steps[:n], "limiter": lim[:n], "sphys": sph[:n]}
+                "step": steps[:n], "limiter": lim[:n], "event": ev[:n], "sphys": sph[:n],
+                "records": rec[:int(nrec[0])], "hash": int(h[0]), "length": float(ln[0]), "n_steps": int(nsteps[0])}
 
     def compute_step_many(self, pos, dirs, depth, paths, proposed=None):
         """Brute-force steps for n queries; returns (step, limiter, safety)."""
@@ -259,6 +274,13 @@ def uniform_pair(seed: int, tid: int, stream: int, draw: int):
 def fnv1a(data: bytes) -> int:
     buf = np.frombuffer(data, dtype=np.uint8).copy() if data else np.zeros(1, dtype=np.uint8)
     return int(lib().o_fnv1a(_p(buf), len(data)))
+
+
+def rotate(u, ct: float, cph: float, sph: float) -> np.ndarray:
+    """The Compton direction rotation: u turned to polar cosine ct and azimuth (cph, sph) about itself."""
+    out = np.zeros(3)
+    lib().o_rotate(_p(_f64(u)), float(ct), float(cph), float(sph), _p(out))
+    return out
 
 
 def kahn_sample(E: float, seed: int, n: int, tid0: int = 0):

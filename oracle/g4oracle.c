@@ -999,11 +999,53 @@ void o_source_sample(const double *src, uint64_t seed, int64_t tid0, int64_t n, 
 
 /* ------------------------------------------------------------------ transport */
 
+/* Optional record of one history (o_transport_trace): for each step the state before it
+ * (position, direction, energy, path, free path Y / mu) and its outcome (step length,
+ * limiter, event), and every (leaf, limiter, event) record in the order it is hashed.
+ * Recording stops at the capacities; the history itself runs to its end. */
+typedef struct {
+  int64_t cap, n, caprec, nrec;
+  double *pos, *dir, *E, *step, *sphys;
+  int *path, *depth, *lim, *ev;
+  int32_t *rec;
+} OTrace;
+
+static void trace_state(OTrace *tr, const double *x, const double *u, double E, const int *path, int depth,
+                        double sphys) {
+  if (!tr || tr->n >= tr->cap) return;
+  int64_t n = tr->n;
+  memcpy(tr->pos + 3 * n, x, 3 * sizeof(double));
+  memcpy(tr->dir + 3 * n, u, 3 * sizeof(double));
+  tr->E[n] = E;
+  memcpy(tr->path + O_DMAX * n, path, O_DMAX * sizeof(int));
+  tr->depth[n] = depth;
+  tr->sphys[n] = sphys;
+}
+
+static void trace_outcome(OTrace *tr, double s, int lim, int ev) {
+  if (!tr || tr->n >= tr->cap) return;
+  tr->step[tr->n] = s;
+  tr->lim[tr->n] = lim;
+  tr->ev[tr->n] = ev;
+  tr->n++;
+}
+
+/* hash_step, with the record kept in the trace */
+static uint64_t record(OTrace *tr, uint64_t h, int32_t leaf, int32_t limiter, int32_t event) {
+  if (tr && tr->nrec < tr->caprec) {
+    tr->rec[3 * tr->nrec] = leaf;
+    tr->rec[3 * tr->nrec + 1] = limiter;
+    tr->rec[3 * tr->nrec + 2] = event;
+    tr->nrec++;
+  }
+  return hash_step(h, leaf, limiter, event);
+}
+
 /* One history (Algorithm 1 extended with the gamma interactions).  Deposits
  * go to tally[nv] rows per batch: columns 0..nv-1 per volume, nv = escaped
- * energy, nv+1 = source energy. */
+ * energy, nv+1 = source energy.  tr (may be NULL) records the history. */
 static void transport_one(const OGeom *g, const double *src, uint64_t seed, int64_t tid, double cutoff, int64_t max_steps,
-                          double *tally_row, uint64_t *cnt, uint64_t *hash_out, double *len_out) {
+                          double *tally_row, uint64_t *cnt, uint64_t *hash_out, double *len_out, OTrace *tr) {
   const int nv = g->nvol;
   double x[3], u[3], E;
   gen_source(src, seed, tid, x, u, &E);
@@ -1017,7 +1059,7 @@ static void transport_one(const OGeom *g, const double *src, uint64_t seed, int6
   if (depth == 0) {
     cnt[C_ESCAPED]++;
     tally_row[nv] += E;
-    h = hash_step(h, -1, LIM_MOTHER, EV_ESCAPE);
+    h = record(tr, h, -1, LIM_MOTHER, EV_ESCAPE);
     if (hash_out) *hash_out = h;
     if (len_out) *len_out = 0.0;
     return;
@@ -1029,13 +1071,14 @@ static void transport_one(const OGeom *g, const double *src, uint64_t seed, int6
   for (;;) {
     if (steps >= max_steps) {
       cnt[C_STEPLIMIT]++;
-      h = hash_step(h, path[depth - 1], LIM_STEPLIMIT, EV_STEPLIMIT);
+      h = record(tr, h, path[depth - 1], LIM_STEPLIMIT, EV_STEPLIMIT);
       break;
     }
     int leaf = path[depth - 1];
     double mu, mupe;
     mu_lookup(&g->mat[g->vol[leaf].mat], E, &mu, &mupe);
     double sphys = mu > 0.0 ? Y / mu : O_INF;
+    trace_state(tr, x, u, E, path, depth, sphys);
     int lim;
     double sgeo = geom_step(g, path, depth, x, u, &lim, NULL, cnt);
     ++steps;
@@ -1054,15 +1097,17 @@ static void transport_one(const OGeom *g, const double *src, uint64_t seed, int6
         cnt[C_PUSH]++;
         nzero = 0;
         depth = relocate_impl(g, path, depth, x, u, cnt);
-        h = hash_step(h, depth > 0 ? path[depth - 1] : -1, LIM_PUSH, EV_PUSH);
+        h = record(tr, h, depth > 0 ? path[depth - 1] : -1, LIM_PUSH, EV_PUSH);
       }
       if (depth == 0) {
         cnt[C_ESCAPED]++;
         tally_row[nv] += E;
-        h = hash_step(h, -1, lim, EV_ESCAPE);
+        h = record(tr, h, -1, lim, EV_ESCAPE);
+        trace_outcome(tr, sgeo, lim, EV_ESCAPE);
         break;
       }
-      h = hash_step(h, path[depth - 1], lim, EV_NONE);
+      h = record(tr, h, path[depth - 1], lim, EV_NONE);
+      trace_outcome(tr, sgeo, lim, EV_NONE);
       continue;
     }
     /* interaction at T = t_{j-1} + (Y - S_{j-1}) / mu_j */
@@ -1076,7 +1121,8 @@ static void transport_one(const OGeom *g, const double *src, uint64_t seed, int6
     if (U * mu < mupe) {
       cnt[C_PHOTO]++;
       tally_row[leaf] += E;
-      h = hash_step(h, leaf, LIM_PHYS, EV_PHOTO);
+      h = record(tr, h, leaf, LIM_PHYS, EV_PHOTO);
+      trace_outcome(tr, sphys, LIM_PHYS, EV_PHOTO);
       break;
     }
     cnt[C_COMPTON]++;
@@ -1088,13 +1134,15 @@ static void transport_one(const OGeom *g, const double *src, uint64_t seed, int6
     if (E1 < cutoff) {
       cnt[C_CUTOFF]++;
       tally_row[leaf] += E;
-      h = hash_step(h, leaf, LIM_PHYS, EV_CUTOFF);
+      h = record(tr, h, leaf, LIM_PHYS, EV_CUTOFF);
+      trace_outcome(tr, sphys, LIM_PHYS, EV_CUTOFF);
       break;
     }
     tally_row[leaf] += E - E1;
     E = E1;
     Y = -log(W);
-    h = hash_step(h, leaf, LIM_PHYS, EV_COMPTON);
+    h = record(tr, h, leaf, LIM_PHYS, EV_COMPTON);
+    trace_outcome(tr, sphys, LIM_PHYS, EV_COMPTON);
   }
   if (hash_out) *hash_out = h;
   if (len_out) *len_out = len;
@@ -1128,7 +1176,8 @@ int o_transport(int gi, const double *src, uint64_t seed, int64_t tid0, int64_t 
 #endif
     int64_t tid = tid0 + i;
     double *row = tl[t] + (tid % nb) * stride;
-    transport_one(g, src, seed, tid, cutoff, max_steps, row, cl[t], hashes ? &hashes[i] : NULL, lengths ? &lengths[i] : NULL);
+    transport_one(g, src, seed, tid, cutoff, max_steps, row, cl[t], hashes ? &hashes[i] : NULL, lengths ? &lengths[i] : NULL,
+                  NULL);
   }
   for (int t = 0; t < used; ++t) {
     for (int64_t k = 0; k < (int64_t)nb * stride; ++k) tally[k] += tl[t][k];
@@ -1199,68 +1248,31 @@ void o_compute_step_many(int gi, int64_t n, const double *pos, const double *dir
   }
 }
 
-/* Per-step trace of one history (debugging aid for parity failures): for every step the
- * state before it (position, direction, energy, path) and its outcome (step length,
- * limiter, event code of the record hashed after it).  Returns the steps recorded. */
-int o_transport_trace(int gi, const double *src, uint64_t seed, int64_t tid, double cutoff, int64_t cap,
-                      double *pos, double *dir, double *E_out, int *paths, int *depth_out, double *steps,
-                      int *limiters, double *sphys_out) {
+/* Per-step trace of one history (debugging aid for parity failures): transport_one itself
+ * run with a recorder, so the trace is the history the transport computes.  For every step
+ * the state before it (position, direction, energy, path, Y / mu) and its outcome (step
+ * length, limiter, event of the step); every hashed (leaf, limiter, event) record in order
+ * (records: 3 int32 each, capacity 2 cap + 2); the history's hash, path length and step
+ * count.  Returns the steps recorded (at most cap). */
+int o_transport_trace(int gi, const double *src, uint64_t seed, int64_t tid, double cutoff, int64_t max_steps,
+                      int64_t cap, double *pos, double *dir, double *E_out, int *paths, int *depth_out, double *steps,
+                      int *limiters, double *sphys_out, int *events, int32_t *records, int64_t *n_records,
+                      uint64_t *hash_out, double *len_out, int64_t *n_steps) {
   const OGeom *g = G[gi];
-  double x[3], u[3], E;
-  gen_source(src, seed, tid, x, u, &E);
-  int path[O_DMAX];
-  for (int k = 0; k < O_DMAX; ++k) path[k] = -1;
-  int depth = locate_impl(g, x, u, path, NULL);
-  if (depth == 0) return 0;
-  ORng rp = {seed, tid, 1u, 0u};
-  double Y = -log(rng_u(&rp));
-  int64_t n = 0;
-  int nzero = 0;
-  while (n < cap) {
-    int leaf = path[depth - 1];
-    double mu, mupe;
-    mu_lookup(&g->mat[g->vol[leaf].mat], E, &mu, &mupe);
-    double sph = mu > 0.0 ? Y / mu : O_INF;
-    int lim;
-    double sgeo = geom_step(g, path, depth, x, u, &lim, NULL, NULL);
-    memcpy(pos + 3 * n, x, sizeof(x));
-    memcpy(dir + 3 * n, u, sizeof(u));
-    E_out[n] = E;
-    memcpy(paths + O_DMAX * n, path, sizeof(path));
-    depth_out[n] = depth;
-    sphys_out[n] = sph;
-    if (sgeo <= sph) {
-      steps[n] = sgeo;
-      limiters[n] = lim;
-      ++n;
-      x[0] += sgeo * u[0]; x[1] += sgeo * u[1]; x[2] += sgeo * u[2];
-      if (mu > 0.0) { Y = Y - sgeo * mu; if (Y < 0.0) Y = 0.0; }
-      depth = relocate_impl(g, path, depth, x, u, NULL);
-      if (sgeo <= kHalf) ++nzero; else nzero = 0;
-      if (depth > 0 && nzero >= 10) {
-        x[0] += 100.0 * kTol * u[0]; x[1] += 100.0 * kTol * u[1]; x[2] += 100.0 * kTol * u[2];
-        nzero = 0;
-        depth = relocate_impl(g, path, depth, x, u, NULL);
-      }
-      if (depth == 0) break;
-      continue;
-    }
-    steps[n] = sph;
-    limiters[n] = LIM_PHYS;
-    ++n;
-    x[0] += sph * u[0]; x[1] += sph * u[1]; x[2] += sph * u[2];
-    nzero = 0;
-    double U, W;
-    rng_pair(&rp, &U, &W);
-    if (U * mu < mupe) break;
-    double eta, cost, cph, sph2;
-    kahn(E, &rp, &eta, &cost);
-    azimuth(&rp, &cph, &sph2);
-    rotate_about(u, cost, cph, sph2);
-    double E1 = E / eta;
-    if (E1 < cutoff) break;
-    E = E1;
-    Y = -log(W);
-  }
-  return (int)n;
+  OTrace tr = {cap, 0, 2 * cap + 2, 0, pos, dir, E_out, steps, sphys_out, paths, depth_out, limiters, events, records};
+  double *row = (double *)calloc((size_t)g->nvol + 2, sizeof(double));
+  uint64_t cnt[O_NCOUNT] = {0};
+  transport_one(g, src, seed, tid, cutoff, max_steps, row, cnt, hash_out, len_out, &tr);
+  free(row);
+  *n_records = tr.nrec;
+  *n_steps = (int64_t)cnt[C_STEPS];
+  return (int)tr.n;
+}
+
+/* The direction rotation of a Compton scatter (exported for its pins): u turned to polar
+ * cosine ct and azimuth (cph, sph) about itself. */
+void o_rotate(const double *u_in, double ct, double cph, double sph, double *u_out) {
+  double u[3] = {u_in[0], u_in[1], u_in[2]};
+  rotate_about(u, ct, cph, sph);
+  memcpy(u_out, u, sizeof(u));
 }
