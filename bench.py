@@ -667,10 +667,167 @@ def run_free_path(args):
         dist.destroy_process_group()
 
 
+QUERY_METRIC = "navigation queries/sec on 1 GB300 (the two navigation problems of Sec. 3.2: locate, compute_step)"
+
+
+def run_queries(args):
+    """Throughput of the query entry points g4n_locate / g4n_compute_step on resident SoA inputs: 10^7
+    points uniform in a box around the detector with isotropic directions (compute_step: from their
+    located paths, with a physics proposal per query), L2 flushed between timed launches."""
+    import torch
+    import paper_1209_5235_gb300 as g4
+    from paper_1209_5235_gb300 import build as b
+    import synth
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    b.build()
+    ctx = g4.g4n_create(local)
+    scene = args.scene
+    sc = synth.scenes.calorimeter_scene() if scene == "calorimeter" else synth.scenes.barrel_scene()
+    gid = g4.build_scene(ctx, sc)
+    n = args.queries
+    p, v = synth.scenes.query_points(scene, n, seed=0x7A0C0010 + rank)
+    pos = torch.from_numpy(p).cuda()
+    dirs = torch.from_numpy(v).cuda()
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    path = torch.empty((g4.G4N_DMAX, n), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    g4.g4n_locate(ctx, gid, pos, dirs, depth, path, stream=stream)
+    g4.g4n_sync(ctx, stream)
+    prop = torch.from_numpy(np.random.default_rng(0x7A0C0011 + rank).exponential(100.0, n)).cuda()
+    kind = args.workload
+    modes = {"fp64": g4.G4N_MODE_FP64, "fp32_recheck": g4.G4N_MODE_FP32_RECHECK}
+    if kind == "locate":
+        modes = {"fp64": g4.G4N_MODE_FP64}       # the descent is the same code in every mode
+        in_b, out_b = 48, 4 + 4 * g4.G4N_DMAX     # pos, dir | depth, path (all G4N_DMAX levels written)
+
+        def launch(mode):
+            g4.g4n_locate(ctx, gid, pos, dirs, depth, path, stream=stream)
+    else:
+        in_b, out_b = 48 + 4 + 4 + 8, 8 + 8 + 4   # pos, dir, depth, the leaf's path entry, proposal | step, safety, limiter
+        outs = {m: (torch.empty(n, dtype=torch.float64, device="cuda"), torch.empty(n, dtype=torch.float64, device="cuda"),
+                    torch.empty(n, dtype=torch.int32, device="cuda")) for m in modes.values()}
+
+        def launch(mode):
+            g4.g4n_compute_step(ctx, gid, pos, dirs, depth, path, prop, mode=mode, stream=stream, out=outs[mode])
+    results = {}
+    ref = None
+    matched = True
+    with ClockSampler(local) as clk:
+        for name, mode in modes.items():
+            launch(mode)
+            g4.g4n_sync(ctx, stream)
+            if kind == "compute_step":
+                got = tuple(x.clone() for x in outs[mode][::2])   # step, limiter
+                if ref is None:
+                    ref = got
+                else:
+                    matched = matched and all(bool(torch.equal(a, c)) for a, c in zip(got, ref))
+            for k in range(args.warmup):
+                launch(mode)
+            g4.g4n_sync(ctx, stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                launch(mode)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            g4.g4n_sync(ctx, stream)
+            ms = [a.elapsed_time(c) for a, c in ev]
+            t_dev = sum(ms) / 1e3
+            if dist:
+                tt = torch.tensor([t_dev], device="cuda")
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+                t_dev = float(tt.item())
+            results[name] = {"queries_per_s": world * n * args.steps / t_dev, "ms_per_step": 1e3 * t_dev / args.steps,
+                             "ms_launch_mean": float(np.mean(ms))}
+    chosen = max(results, key=lambda k: results[k]["queries_per_s"]) if matched else "fp64"
+    R = results[chosen]
+    # end to end: pinned host inputs in, outputs back, every step
+    hp = torch.from_numpy(p).pin_memory()
+    hv = torch.from_numpy(v).pin_memory()
+    if kind == "locate":
+        hout = [torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty((g4.G4N_DMAX, n), dtype=torch.int32).pin_memory()]
+    else:
+        hd = depth.cpu().pin_memory()
+        hpath = path.cpu().pin_memory()
+        hprop = prop.cpu().pin_memory()
+        hout = [torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory(),
+                torch.empty(n, dtype=torch.int32).pin_memory()]
+    e2e_t = 0.0
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pos.copy_(hp, non_blocking=True)
+        dirs.copy_(hv, non_blocking=True)
+        if kind == "locate":
+            g4.g4n_locate(ctx, gid, pos, dirs, depth, path, stream=stream)
+            devs = [depth, path]
+        else:
+            depth.copy_(hd, non_blocking=True)
+            path.copy_(hpath, non_blocking=True)
+            prop.copy_(hprop, non_blocking=True)
+            devs = list(g4.g4n_compute_step(ctx, gid, pos, dirs, depth, path, prop, mode=modes[chosen], stream=stream,
+                                            out=outs[modes[chosen]]))
+        for h, d in zip(hout, devs):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_t += time.perf_counter() - t0
+    g4.g4n_sync(ctx, stream)
+    h2d = n * (48 if kind == "locate" else 48 + 4 + 4 * g4.G4N_DMAX + 8)
+    d2h = n * (4 + 4 * g4.G4N_DMAX if kind == "locate" else 20)
+    g4.g4n_destroy(ctx)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = load_peaks()
+    t_launch = R["ms_launch_mean"] / 1e3
+    algo = n * (in_b + out_b)
+    achieved = algo / t_launch / 1e9
+    peak = peaks.get("hbm_gbs")
+    line = {
+        "metric": QUERY_METRIC, "value": R["queries_per_s"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{kind}: {n} queries on the {scene} scene, points uniform in the box "
+                               f"{synth.scenes.QUERY_BOXES[scene]} mm, isotropic directions"
+                               + ("" if kind == "locate" else ", from their located paths, physics proposal "
+                                                               "~ Exp(mean 100 mm)"),
+                   "queries_per_gpu": n, "mode": chosen, "l2": "flushed between timed steps (256 MB write)"},
+        "modes": results, "matched_results": matched, "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "kernel": "k_locate" if kind == "locate" else "k_compute_step",
+                     "algorithmic_bytes_per_query": in_b + out_b, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "clocks": clk.summary(),
+        "e2e": {"value": world * n * args.steps / e2e_t, "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed launches per mode (default 10 for the 10^7-track barrel workloads, else 20)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--tracks", type=int, default=1_000_000)
@@ -685,19 +842,26 @@ def main():
     ap.add_argument("--regroup", type=int, default=0)
     ap.add_argument("--mode", default="auto", choices=["auto", "fp64", "fp32_recheck"])
     ap.add_argument("--voxel", default="smart")
-    ap.add_argument("--workload", default="calorimeter",
+    ap.add_argument("--workload", default="barrel_learned",
                     choices=["calorimeter", "tiny", "batched", "barrel", "barrel_learned", "barrel_nested",
-                             "spheres_regular", "spheres_random"])
+                             "spheres_regular", "spheres_random", "locate", "compute_step"])
+    ap.add_argument("--scene", default="calorimeter", choices=["calorimeter", "barrel"],
+                    help="locate / compute_step workloads: the scene queried")
+    ap.add_argument("--queries", type=int, default=10_000_000)
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tune-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 10 if args.workload.startswith("barrel") else 20
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
     elif args.workload.startswith("spheres_"):
         run_free_path(args)
+    elif args.workload in ("locate", "compute_step"):
+        run_queries(args)
     else:
         run_gpu(args)
 

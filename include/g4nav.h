@@ -105,6 +105,14 @@ const char *g4n_last_error(const g4n_ctx *ctx);
 int g4n_set_tolerance_scale(g4n_ctx *ctx, double scale);
 /* Wait for `stream` and report any device-side error raised since the last sync. */
 int g4n_sync(g4n_ctx *ctx, g4n_stream stream);
+/* Caps of the context's device loops (failure detection; the paper has no counterpart).  Every
+ * loop of the kernels that is not bounded by its input is capped: the voxel walk of one boundary
+ * search (default 65536 nodes) and each rejection sampler -- Kahn's method, the disc azimuth, the
+ * Gaussian beam spot -- (default 1000 trials).  A kernel whose loop reaches its cap stops that loop,
+ * finishes the history with what it has and raises G4N_ERR_TIMEOUT at the next g4n_sync (or in the
+ * status slot of g4n_transport_batch_noalloc); results of such a run are not valid.  0 restores a
+ * default; negative values give G4N_ERR_ARG.  Applies to the calls made after it. */
+int g4n_set_loop_caps(g4n_ctx *ctx, int32_t max_walk_nodes, int32_t max_sampler_trials);
 
 /* ---------------------------------------------------------------- geometry build (host) */
 

@@ -37,7 +37,8 @@ COUNTER_NAMES = {0: "tracks", 1: "steps", 2: "geom_steps", 3: "phys_steps", 4: "
 PARITY_COUNTERS = ["tracks", "steps", "geom_steps", "phys_steps", "photo", "compton", "escaped", "cutoff", "pushes",
                    "step_limit"]
 
-EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_scale", "g4n_sync", "g4n_material_add",
+EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_scale", "g4n_sync", "g4n_set_loop_caps",
+            "g4n_material_add",
             "g4n_solid_box", "g4n_solid_tube", "g4n_solid_orb", "g4n_solid_cone", "g4n_place",
             "g4n_logical_create", "g4n_logical_add_daughter", "g4n_place_logical", "g4n_touchable", "g4n_voxelize", "g4n_geom_finalize",
             "g4n_geom_info", "g4n_locate", "g4n_compute_step", "g4n_free_path", "g4n_transport_batch", "g4n_transport_batch_host",
@@ -103,6 +104,7 @@ def load():
     sig = {
         "g4n_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int],
         "g4n_destroy": [vp], "g4n_set_tolerance_scale": [vp, d], "g4n_sync": [vp, vp],
+        "g4n_set_loop_caps": [vp, i32, i32],
         "g4n_material_add": [vp, d, i32, vp, vp, vp, vp],
         "g4n_solid_box": [vp, d, d, d, vp], "g4n_solid_tube": [vp, d, d, d, d, d, vp], "g4n_solid_orb": [vp, d, vp],
         "g4n_solid_cone": [vp, d, d, d, d, d, vp],
@@ -150,13 +152,52 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dptr(t, dtype, name):
-    """Device pointer of a contiguous CUDA tensor of the given dtype (None -> NULL)."""
+_CTX_DEVICE = {}   # context handle -> its CUDA device (set by g4n_create)
+
+
+def _dptr(t, dtype, name, min_numel: int = 0, device: Optional[int] = None):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (None -> NULL), holding at least
+    `min_numel` elements and, when `device` is given, on that CUDA device.  The kernels write every
+    element they are told exists, so an undersized or misplaced tensor is refused here."""
     if t is None:
         return None
     if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
         raise ValueError(f"{name}: need a contiguous CUDA tensor of {dtype}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name}: {t.numel()} elements, need at least {min_numel}")
+    if device is not None and t.device.index is not None and t.device.index != device:
+        raise ValueError(f"{name}: tensor on cuda:{t.device.index}, the context is on cuda:{device}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _ctx_device(ctx) -> Optional[int]:
+    return _CTX_DEVICE.get(getattr(ctx, "value", ctx))
+
+
+def _n_tracks(items) -> int:
+    return int(sum(max(0, int(items[k].n_tracks)) for k in range(len(items))))
+
+
+def _transport_ptrs(ctx, items, edep, counters, track_hash, track_len, n_batches):
+    """Checked device pointers of a transport's outputs: edep (n_batches, stride) float64, counters
+    (>= G4N_N_COUNTERS) int64, per-track hash / length (>= the batch's track count), all on the
+    context's device."""
+    import torch
+    if edep.dim() != 2 or edep.shape[0] != n_batches:
+        raise ValueError("edep: need shape (n_batches, tally_stride)")
+    dev = _ctx_device(ctx)
+    n = _n_tracks(items)
+    return (_dptr(edep, torch.float64, "edep", n_batches * edep.shape[1], dev),
+            _dptr(counters, torch.int64, "counters", G4N_N_COUNTERS, dev),
+            _dptr(track_hash, torch.int64, "track_hash", n, dev),
+            _dptr(track_len, torch.float64, "track_len", n, dev))
+
+
+def _soa3(t, name, n=None):
+    """A (3, n) structure-of-arrays tensor; returns n."""
+    if t.dim() != 2 or t.shape[0] != 3 or (n is not None and t.shape[1] != n):
+        raise ValueError(f"{name}: need shape (3, n)" + (f" with n = {n}" if n is not None else ""))
+    return int(t.shape[1])
 
 
 def _host(a, dtype):
@@ -170,10 +211,13 @@ def g4n_create(device: int = 0):
     rc = load().g4n_create(ctypes.byref(ctx), int(device))
     if rc != G4N_OK:
         raise G4NError(rc, "g4n_create failed (no CUDA device?)")
+    if int(device) >= 0:
+        _CTX_DEVICE[ctx.value] = int(device)
     return ctx
 
 
 def g4n_destroy(ctx) -> None:
+    _CTX_DEVICE.pop(getattr(ctx, "value", ctx), None)
     load().g4n_destroy(ctx)
 
 
@@ -187,6 +231,11 @@ def g4n_set_tolerance_scale(ctx, scale: float) -> None:
 
 def g4n_sync(ctx, stream=None) -> None:
     _check(ctx, load().g4n_sync(ctx, _stream(stream)))
+
+
+def g4n_set_loop_caps(ctx, max_walk_nodes: int = 0, max_sampler_trials: int = 0) -> None:
+    """Caps of the device loops (0 = default: 65536 voxel nodes per search, 1000 sampler trials)."""
+    _check(ctx, load().g4n_set_loop_caps(ctx, int(max_walk_nodes), int(max_sampler_trials)))
 
 
 # ---------------------------------------------------------------- geometry build
@@ -346,29 +395,35 @@ def build_scene(ctx, scene) -> int:
 def g4n_locate(ctx, geom: int, pos, dir, out_depth=None, out_path=None, stream=None):
     """pos, dir: (3, n) float64 CUDA tensors (SoA).  Returns (depth (n,) int32, path (G4N_DMAX, n) int32)."""
     import torch
-    n = pos.shape[1]
+    n = _soa3(pos, "pos")
+    _soa3(dir, "dir", n)
     if out_depth is None:
         out_depth = torch.empty(n, dtype=torch.int32, device=pos.device)
     if out_path is None:
         out_path = torch.empty((G4N_DMAX, n), dtype=torch.int32, device=pos.device)
-    _check(ctx, load().g4n_locate(ctx, int(geom), int(n), _dptr(pos, torch.float64, "pos"),
-                                  _dptr(dir, torch.float64, "dir"), _dptr(out_depth, torch.int32, "out_depth"),
-                                  _dptr(out_path, torch.int32, "out_path"), _stream(stream)))
+    dev = _ctx_device(ctx)
+    args = (_dptr(pos, torch.float64, "pos", 3 * n, dev), _dptr(dir, torch.float64, "dir", 3 * n, dev),
+            _dptr(out_depth, torch.int32, "out_depth", n, dev), _dptr(out_path, torch.int32, "out_path", G4N_DMAX * n, dev))
+    _check(ctx, load().g4n_locate(ctx, int(geom), int(n), *args, _stream(stream)))
     return out_depth, out_path
 
 
-def g4n_compute_step(ctx, geom: int, pos, dir, depth, path, proposed=None, mode: int = G4N_MODE_FP64, stream=None):
-    """Returns (step (n,) f64, safety (n,) f64, limiter (n,) int32)."""
+def g4n_compute_step(ctx, geom: int, pos, dir, depth, path, proposed=None, mode: int = G4N_MODE_FP64, stream=None,
+                     out=None):
+    """Returns (step (n,) f64, safety (n,) f64, limiter (n,) int32); `out` may give those three tensors."""
     import torch
-    n = pos.shape[1]
-    step = torch.empty(n, dtype=torch.float64, device=pos.device)
-    saf = torch.empty(n, dtype=torch.float64, device=pos.device)
-    lim = torch.empty(n, dtype=torch.int32, device=pos.device)
-    _check(ctx, load().g4n_compute_step(ctx, int(geom), int(n), _dptr(pos, torch.float64, "pos"),
-                                        _dptr(dir, torch.float64, "dir"), _dptr(depth, torch.int32, "depth"),
-                                        _dptr(path, torch.int32, "path"), _dptr(proposed, torch.float64, "proposed"),
-                                        _dptr(step, torch.float64, "step"), _dptr(saf, torch.float64, "safety"),
-                                        _dptr(lim, torch.int32, "limiter"), int(mode), _stream(stream)))
+    n = _soa3(pos, "pos")
+    _soa3(dir, "dir", n)
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float64, device=pos.device), torch.empty(n, dtype=torch.float64, device=pos.device),
+               torch.empty(n, dtype=torch.int32, device=pos.device))
+    step, saf, lim = out
+    dev = _ctx_device(ctx)
+    args = (_dptr(pos, torch.float64, "pos", 3 * n, dev), _dptr(dir, torch.float64, "dir", 3 * n, dev),
+            _dptr(depth, torch.int32, "depth", n, dev), _dptr(path, torch.int32, "path", G4N_DMAX * n, dev),
+            _dptr(proposed, torch.float64, "proposed", n, dev), _dptr(step, torch.float64, "step", n, dev),
+            _dptr(saf, torch.float64, "safety", n, dev), _dptr(lim, torch.int32, "limiter", n, dev))
+    _check(ctx, load().g4n_compute_step(ctx, int(geom), int(n), *args, int(mode), _stream(stream)))
     return step, saf, lim
 
 
@@ -378,14 +433,16 @@ def g4n_free_path(ctx, geom: int, pos, dir, Y, energy: float, mode: int = G4N_MO
     """Free path T of Algorithm 1 per ray.  Returns (T (n,) f64, steps (n,) int32 or None); `counters`
     (G4N_N_COUNTERS int64 device tensor) is accumulated if given."""
     import torch
-    n = pos.shape[1]
+    n = _soa3(pos, "pos")
+    _soa3(dir, "dir", n)
     T = out_T if out_T is not None else torch.empty(n, dtype=torch.float64, device=pos.device)
     st = out_steps if out_steps is not None else (torch.empty(n, dtype=torch.int32, device=pos.device) if want_steps
                                                   else None)
-    _check(ctx, load().g4n_free_path(ctx, int(geom), int(n), _dptr(pos, torch.float64, "pos"),
-                                     _dptr(dir, torch.float64, "dir"), _dptr(Y, torch.float64, "Y"), float(energy),
-                                     _dptr(T, torch.float64, "T"), _dptr(st, torch.int32, "steps"),
-                                     _dptr(counters, torch.int64, "counters"), int(mode), int(max_steps),
+    dev = _ctx_device(ctx)
+    args = (_dptr(pos, torch.float64, "pos", 3 * n, dev), _dptr(dir, torch.float64, "dir", 3 * n, dev),
+            _dptr(Y, torch.float64, "Y", n, dev), float(energy), _dptr(T, torch.float64, "T", n, dev),
+            _dptr(st, torch.int32, "steps", n, dev), _dptr(counters, torch.int64, "counters", G4N_N_COUNTERS, dev))
+    _check(ctx, load().g4n_free_path(ctx, int(geom), int(n), *args, int(mode), int(max_steps),
                                      G4N_FLAG_DIAGNOSTICS if diagnostics else 0, _stream(stream)))
     return T, st
 
@@ -433,15 +490,10 @@ def g4n_transport_batch(ctx, items, seed: int, edep, counters, track_hash=None, 
                         blocks_per_sm: int = 0, refill_min: int = 0, interact_min: int = 0,
                         diagnostics: bool = False, stream=None, walk_budget: int = 0, regroup_period: int = 0) -> None:
     """Device outputs (accumulated): edep (n_batches, stride) f64, counters (32,) int64 (as uint64 bits)."""
-    import torch
+    ptrs = _transport_ptrs(ctx, items, edep, counters, track_hash, track_len, n_batches)
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
               interact_min, diagnostics, walk_budget, regroup_period)
-    if edep.shape[0] != n_batches:
-        raise ValueError("edep rows must equal n_batches")
-    _check(ctx, load().g4n_transport_batch(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
-                                           _dptr(counters, torch.int64, "counters"),
-                                           _dptr(track_hash, torch.int64, "track_hash"),
-                                           _dptr(track_len, torch.float64, "track_len"), _stream(stream)))
+    _check(ctx, load().g4n_transport_batch(ctx, ctypes.byref(d), *ptrs, _stream(stream)))
 
 
 def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_hash=None, track_len=None,
@@ -455,15 +507,10 @@ def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_has
     scratch in a fixed device array instead of a cudaMalloc'd workspace.  Device-side errors are
     written to counters[G4N_NOALLOC_STATUS_SLOT] (0 = none) instead of being reported by g4n_sync.
     """
-    import torch
+    ptrs = _transport_ptrs(ctx, items, edep, counters, track_hash, track_len, n_batches)
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
               interact_min, diagnostics, walk_budget, regroup_period)
-    if edep.shape[0] != n_batches:
-        raise ValueError("edep rows must equal n_batches")
-    _check(ctx, load().g4n_transport_batch_noalloc(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
-                                                   _dptr(counters, torch.int64, "counters"),
-                                                   _dptr(track_hash, torch.int64, "track_hash"),
-                                                   _dptr(track_len, torch.float64, "track_len"), _stream(stream)))
+    _check(ctx, load().g4n_transport_batch_noalloc(ctx, ctypes.byref(d), *ptrs, _stream(stream)))
 
 
 def g4n_transport_batch_host(ctx, items, seed: int, stride: int, n_tracks: int = 0, want_hash: bool = False,
@@ -564,14 +611,11 @@ def g4n_graph_create(ctx, items, seed: int, edep, counters, track_hash=None, tra
                      blocks_per_sm: int = 0, refill_min: int = 0, interact_min: int = 0, diagnostics: bool = False,
                      walk_budget: int = 0, regroup_period: int = 0):
     """Record the batch as a CUDA graph writing into the given device outputs; returns the handle."""
-    import torch
+    ptrs = _transport_ptrs(ctx, items, edep, counters, track_hash, track_len, n_batches)
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
               interact_min, diagnostics, walk_budget, regroup_period)
     h = ctypes.c_void_p()
-    _check(ctx, load().g4n_graph_create(ctx, ctypes.byref(d), _dptr(edep, torch.float64, "edep"),
-                                        _dptr(counters, torch.int64, "counters"),
-                                        _dptr(track_hash, torch.int64, "track_hash"),
-                                        _dptr(track_len, torch.float64, "track_len"), ctypes.byref(h)))
+    _check(ctx, load().g4n_graph_create(ctx, ctypes.byref(d), *ptrs, ctypes.byref(h)))
     return (ctx, h)
 
 

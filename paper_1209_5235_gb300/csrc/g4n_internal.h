@@ -30,6 +30,8 @@ namespace g4n {
 
 constexpr int kDMax = G4N_DMAX;
 constexpr int kMaxLevels = 3;
+constexpr int kDefaultWalkCap = 1 << 16;   // voxel nodes one boundary search may walk
+constexpr int kDefaultTrialCap = 1000;     // trials of one rejection sampler
 
 enum SolidKind : int32_t { kBox = 0, kTube = 1, kOrb = 2, kCone = 3 };
 // tube bits; world rotation is identity; placement rotation (mother -> local) is identity
@@ -218,20 +220,28 @@ struct g4n_ctx {
   int device = 0;
   std::string err;
   double scale = 1.0;
+  // device loop caps (g4n_set_loop_caps): beyond them a kernel stops the loop and reports G4N_ERR_TIMEOUT
+  int walk_cap = g4n::kDefaultWalkCap;
+  int trial_cap = g4n::kDefaultTrialCap;
   double tol = 1e-9, half = 0.5e-9;
   g4n::Builder b;
   std::vector<g4n::HGeom *> geoms;
   // device geometry directory (DGeom per geometry id), grown on finalize
   g4n::DGeom *d_geoms = nullptr;
   int d_geoms_cap = 0;
-  // transport workspace: queue head, status word, item table
+  // transport workspace: queue head and status word (allocated once, never moved: graphs keep
+  // its status word), and the device item table (grown by doubling)
   void *ws = nullptr;
-  size_t ws_bytes = 0;
+  void *items = nullptr;
+  size_t items_bytes = 0;
   // host staging for g4n_transport_batch_host
   void *h_stage = nullptr;
   size_t h_stage_bytes = 0;
   void *d_stage = nullptr;
   size_t d_stage_bytes = 0;
+  // device buffers outgrown while work may still read them: freed by g4n_destroy (growth by
+  // doubling bounds them by the live size), so that growing never synchronizes the device
+  std::vector<void *> retired;
   int sm_count = 0;
   // candidate-proposal MLP state (owned by mlp.cu)
   void *mlp = nullptr;

@@ -191,11 +191,93 @@ void float_enclose(double x, float &lo, float &hi) {
 
 int smart_levels(const g4n_voxel_params &P) { return P.n_levels > 0 ? std::min(P.n_levels, kMaxLevels) : kMaxLevels; }
 
+// Distance from the origin to the convex quadrilateral with corners (x[i], y[i]) in order (0 inside).
+double origin_to_quad(const double *x, const double *y) {
+  bool pos = true, neg = true;
+  double d = HUGE_VAL;
+  for (int i = 0; i < 4; ++i) {
+    const int j = (i + 1) & 3;
+    const double ex = x[j] - x[i], ey = y[j] - y[i];
+    const double cr = ex * (-y[i]) - ey * (-x[i]);  // edge x (origin - corner)
+    pos = pos && cr >= 0.0;
+    neg = neg && cr <= 0.0;
+    const double l2 = ex * ex + ey * ey;
+    double t = l2 > 0.0 ? -(x[i] * ex + y[i] * ey) / l2 : 0.0;
+    t = std::min(1.0, std::max(0.0, t));
+    d = std::min(d, std::hypot(x[i] + t * ex, y[i] + t * ey));
+  }
+  return (pos || neg) ? 0.0 : d;
+}
+
+// Can the solid of placement pl, grown by m, reach into box R (the mother frame)?  False only when it
+// certainly cannot.  A voxel node lists the daughters whose padded extent overlaps its slab; this test
+// drops those whose extent box overlaps the slab but whose solid does not: concentric shells around a
+// node away from their annulus, phi segments whose wedge misses the node, rotated boxes.  The lists
+// stay conservative (every daughter within m of the node's region is kept).
+bool may_overlap(const HSolid &so, const HPlace &pl, const Box3 &R, double m) {
+  const double zh = so.kind == kOrb ? so.a : so.c;
+  if (R.lo[2] - pl.t[2] > zh + m || R.hi[2] - pl.t[2] < -zh - m) return false;
+  if (so.kind == kOrb) {
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double dd = std::max({R.lo[k] - pl.t[k], 0.0, pl.t[k] - R.hi[k]});
+      d2 += dd * dd;
+    }
+    return d2 <= (so.a + m) * (so.a + m);
+  }
+  // the region's rectangle in the solid's frame
+  double x[4], y[4];
+  const double cxs[4] = {R.lo[0], R.hi[0], R.hi[0], R.lo[0]}, cys[4] = {R.lo[1], R.lo[1], R.hi[1], R.hi[1]};
+  for (int i = 0; i < 4; ++i) {
+    const double mm[3] = {cxs[i], cys[i], 0.0};
+    double l[3];
+    to_local(pl, mm, l);
+    x[i] = l[0];
+    y[i] = l[1];
+  }
+  if (so.kind == kBox) {
+    const double xl = std::min({x[0], x[1], x[2], x[3]}), xh = std::max({x[0], x[1], x[2], x[3]});
+    const double yl = std::min({y[0], y[1], y[2], y[3]}), yh = std::max({y[0], y[1], y[2], y[3]});
+    return !(xl > so.a + m || xh < -so.a - m || yl > so.b + m || yh < -so.b - m);
+  }
+  const double rin = so.kind == kCone ? std::min(so.a, so.d) : so.a;
+  const double rout = so.kind == kCone ? std::max(so.b, so.e) : so.b;
+  double dmax = 0.0;
+  for (int i = 0; i < 4; ++i) dmax = std::max(dmax, std::hypot(x[i], y[i]));
+  if (origin_to_quad(x, y) > rout + m) return false;
+  if (rin > 0.0 && dmax < rin - m) return false;
+  if (so.kind == kTube && so.dphi < kTwoPi - 1e-12) {
+    // signed distances to the lines of the phi planes, positive on the solid's side (a linear function
+    // takes its maximum over the rectangle at a corner)
+    const double cs = std::cos(so.sphi), ss = std::sin(so.sphi);
+    const double ce = std::cos(so.sphi + so.dphi), se = std::sin(so.sphi + so.dphi);
+    double ps = -HUGE_VAL, pe = -HUGE_VAL;
+    for (int i = 0; i < 4; ++i) {
+      ps = std::max(ps, cs * y[i] - ss * x[i]);
+      pe = std::max(pe, se * x[i] - ce * y[i]);
+    }
+    if (so.dphi > M_PI ? (ps < -m && pe < -m) : (ps < -m || pe < -m)) return false;
+  }
+  return true;
+}
+
 struct VoxBuilder {
   HGeom &g;
   const g4n_voxel_params &P;
   const std::vector<Box3> &dbox;  // padded daughter extents in the mother frame
+  const std::vector<HSolid> &solids;
+  const std::vector<HPlace> &places;
+  double margin;                  // the lists' padding plus rounding slack (may_overlap)
   std::map<std::vector<int32_t>, int32_t> list_ids;
+
+  // The daughters of lst that may reach into region R.
+  std::vector<int32_t> filter(const std::vector<int32_t> &lst, const Box3 &R) const {
+    std::vector<int32_t> out;
+    out.reserve(lst.size());
+    for (int32_t d : lst)
+      if (may_overlap(solids[places[d].solid], places[d], R, margin)) out.push_back(d);
+    return out;
+  }
 
   int32_t list_id(const std::vector<int32_t> &lst) {
     auto it = list_ids.find(lst);
@@ -214,7 +296,8 @@ struct VoxBuilder {
     k1 = std::max(0, std::min(n - 1, k1));
   }
 
-  int32_t build(const Box3 &region, const std::vector<int32_t> &D, int level, int used) {
+  // region: the node's extent (slicing); freg: the same grown by the margin, where the node's points lie
+  int32_t build(const Box3 &region, const Box3 &freg, const std::vector<int32_t> &D, int level, int used) {
     int axis = -1, n = 1;
     if (P.mode == 1) {
       axis = P.axes[level];
@@ -251,6 +334,14 @@ struct VoxBuilder {
       slice_range(dbox[d], axis, region.lo[axis], w, n, k0, k1);
       for (int k = k0; k <= k1; ++k) lists[k].push_back(d);
     }
+    // the slab of slice k (grown by the margin; the end slices keep the node's own bounds)
+    auto slab = [&](int k0, int k1) {
+      Box3 b = freg;
+      if (k0 > 0) b.lo[axis] = region.lo[axis] + k0 * w - margin;
+      if (k1 < n - 1) b.hi[axis] = region.lo[axis] + (k1 + 1) * w + margin;
+      return b;
+    };
+    for (int k = 0; k < n; ++k) lists[k] = filter(lists[k], slab(k, k));
     int k = 0;
     while (k < n) {
       int k1 = k;
@@ -268,7 +359,7 @@ struct VoxBuilder {
         Box3 sub = region;
         sub.lo[axis] = region.lo[axis] + k * w;
         sub.hi[axis] = region.lo[axis] + (k1 + 1) * w;
-        child = -(build(sub, lst, level + 1, used2) + 1);
+        child = -(build(sub, slab(k, k1), lst, level + 1, used2) + 1);
       } else {
         child = list_id(lst);
       }
@@ -506,7 +597,9 @@ int g4n_destroy(g4n_ctx *ctx) {
   }
   cudaFree(ctx->d_geoms);
   cudaFree(ctx->ws);
+  cudaFree(ctx->items);
   cudaFree(ctx->d_stage);
+  for (void *p : ctx->retired) cudaFree(p);
   cudaFreeHost(ctx->h_stage);
   delete ctx;
   return G4N_OK;
@@ -924,8 +1017,16 @@ static int finalize_impl(g4n_ctx *ctx, int32_t *out_geom) {
     const HPlace &mp = B.places[m];
     double zero[3] = {0, 0, 0};
     Box3 region = solid_extent(B.solids[mp.solid], 1.0, 0.0, zero);
-    VoxBuilder vb{*g, P, ext, {}};
-    g->vol[m].vox = vb.build(region, dau[m], 0, 0);
+    double scale = 0.0;
+    for (int k = 0; k < 3; ++k) scale = std::max({scale, std::fabs(region.lo[k]), std::fabs(region.hi[k])});
+    const double margin = 2.0 * pad + 1e-10 * scale;
+    Box3 freg = region;
+    for (int k = 0; k < 3; ++k) {
+      freg.lo[k] -= margin;
+      freg.hi[k] += margin;
+    }
+    VoxBuilder vb{*g, P, ext, B.solids, B.places, margin, {}};
+    g->vol[m].vox = vb.build(region, freg, vb.filter(dau[m], freg), 0, 0);
   }
   if (g->clist.empty()) g->clist.push_back({0, 0});
   if (g->cand.empty()) g->cand.push_back(-1);

@@ -1129,7 +1129,7 @@ __device__ __forceinline__ void chain_fill(const DGeom &G, Chain &ch, int lev, i
 // Returns 0: the walk ends; 1: ch holds the next node.  With `saf` the distances from the
 // point to the node's slab faces lower *saf.
 __device__ __forceinline__ int walk_step64(const DGeom &G, Chain &ch, const V3 &p, const V3 &v, const Inv3 &iv,
-                                           double bound, bool saf, double *saf64, int *it, bool *timeout) {
+                                           double bound, bool saf, double *saf64, int *it, int cap, bool *timeout) {
   double texit = kInf;
   int lstar = -1;
 #pragma unroll 1
@@ -1149,8 +1149,8 @@ __device__ __forceinline__ int walk_step64(const DGeom &G, Chain &ch, const V3 &
   if (!(texit < bound)) return 0;
   const DVoxHdr H = G.hdr[ch.h[lstar]];
   const int nk = comp(v, H.axis) > 0.0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
-  if (nk < 0 || nk >= H.nslices || ++*it >= (1 << 16)) {
-    if (*it >= (1 << 16)) *timeout = true;
+  if (nk < 0 || nk >= H.nslices || ++*it >= cap) {
+    if (*it >= cap) *timeout = true;
     return 0;
   }
   const DVoxSlice S = G.slice[H.slice_base + nk];
@@ -1168,8 +1168,8 @@ __device__ __forceinline__ int walk_step64(const DGeom &G, Chain &ch, const V3 &
 
 // The same, out of line: the FP32 modes take it only when their intervals do not decide.
 __device__ __noinline__ int walk_step64_ool(const DGeom &G, Chain &ch, const V3 &p, const V3 &v, const Inv3 &iv,
-                                            double bound, bool saf, double *saf64, int *it, bool *timeout) {
-  return walk_step64(G, ch, p, v, iv, bound, saf, saf64, it, timeout);
+                                            double bound, bool saf, double *saf64, int *it, int cap, bool *timeout) {
+  return walk_step64(G, ch, p, v, iv, bound, saf, saf64, it, cap, timeout);
 }
 
 // chain_fill from the root header h0 for every FP64 point in the ray's enclosure (FP32
@@ -1213,7 +1213,7 @@ __device__ __forceinline__ float div_hi_a(float n, const Ray32 &r, int a) {
 // takes this node step.  With `saf` the distances from the point to the node's slab
 // faces lower the isotropic safety *saf_f.
 __device__ __forceinline__ int walk_step32(const DGeom &G, Chain &ch, const Ray32 &r, const V3 &v, float bound_f,
-                                           bool saf, float *saf_f, int *it, bool *timeout) {
+                                           bool saf, float *saf_f, int *it, int cap, bool *timeout) {
   float tl[kMaxLevels], th[kMaxLevels];
   const int nlev = ch.nlev;
   int lstar = -1;
@@ -1255,8 +1255,8 @@ __device__ __forceinline__ int walk_step32(const DGeom &G, Chain &ch, const Ray3
   if (ts_lo >= bound_f) return 0;  // texit >= bound_f >= min(best, stop)
   const DVoxHdr32 H = G.hdr32[ch.h[lstar]];
   const int nk = sel3i(r.sgn[0], r.sgn[1], r.sgn[2], H.n_axis & 3) > 0 ? ch.k1[lstar] + 1 : ch.k0[lstar] - 1;
-  if (nk < 0 || nk >= (H.n_axis >> 2) || ++*it >= (1 << 16)) {
-    if (*it >= (1 << 16)) *timeout = true;
+  if (nk < 0 || nk >= (H.n_axis >> 2) || ++*it >= cap) {
+    if (*it >= cap) *timeout = true;
     return 0;
   }
   const DVoxSlice S = G.slice[H.slice_base + nk];
@@ -1380,6 +1380,8 @@ struct StepResult {
   WalkResume resume;
 };
 
+// iv: the reciprocal of v; the FP32 modes read it only when the leaf is a box (its exit).
+//
 // Geometric step inside `leaf` from local point p along v (Sec. 3.2, problem 2),
 // warp-collective: DistanceToOut of the leaf, then DistanceToIn of the daughters
 // listed in the voxel nodes the ray crosses, stopping once the node exit lies
@@ -1388,6 +1390,9 @@ struct StepResult {
 // exceed the best exact distance so far, and no FP64 geometry at all is done when
 // the bounds prove that `limit` comes first.  Both return the FP64 result.
 //
+// walk_cap: the voxel nodes a search may walk in all (its rounds together); a search that reaches it
+// stops there and sets *timeout (the caller reports G4N_ERR_TIMEOUT).
+//
 // Budget (budget > 0): after `budget` node steps a lane's search yields (R.yielded, with the
 // state to continue from in R.resume and in `ch`, which then holds the node stepped into);
 // `resume` continues such a search from there.  The result of a search is the same whether
@@ -1395,7 +1400,8 @@ struct StepResult {
 template <int MODE, bool COUNT>
 __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active, int leaf, const V3 &p, const V3 &v,
                                                      const Inv3 &iv, double limit, bool want_safety, Counters &cnt,
-                                                     bool *timeout, const MlpCtx &mc, Chain &ch, bool resume = false,
+                                                     bool *timeout, int walk_cap, const MlpCtx &mc, Chain &ch,
+                                                     bool resume = false,
                                                      const WalkResume &from = WalkResume{kInf, 0.0, -1, 0},
                                                      int budget = 0) {
   const double half = G.half;
@@ -1503,14 +1509,15 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
         }
         // list done: exit of the current node along the ray; its slab boundaries bound the safety
         int w = 2;
-        if (MODE != kFP64) w = walk_step32(G, ch, r, v, bound_f, first && want_safety, &saf_f, &it, timeout);
+        if (MODE != kFP64) w = walk_step32(G, ch, r, v, bound_f, first && want_safety, &saf_f, &it, walk_cap, timeout);
         if (w == 2) {
           // FP64 node step (the FP32 modes come here only when the intervals do not decide)
           if (MODE == kFP64) {
-            w = walk_step64(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &R.safety, &it, timeout);
+            w = walk_step64(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &R.safety, &it, walk_cap, timeout);
           } else {
             double s64 = kInf;
-            w = walk_step64_ool(G, ch, p, v, iv, fmin(best, stop), first && want_safety, &s64, &it, timeout);
+            w = walk_step64_ool(G, ch, p, v, inv_dir(v), fmin(best, stop), first && want_safety, &s64, &it, walk_cap,
+                                timeout);
             saf_f = fminf(saf_f, __double2float_rd(s64));
           }
         }

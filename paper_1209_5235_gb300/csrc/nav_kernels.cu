@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
                                                       const int32_t *__restrict__ depth, const int32_t *__restrict__ path,
                                                       const double *__restrict__ proposed, double *__restrict__ out_step,
                                                       double *__restrict__ out_safety, int32_t *__restrict__ out_lim,
-                                                      uint32_t *status, const mlp::SmemWeights *__restrict__ mlp_w) {
+                                                      uint32_t *status, const mlp::SmemWeights *__restrict__ mlp_w,
+                                                      int walk_cap) {
   const DGeom &G = geoms[gid];
   Counters cnt;
   const int64_t lane = threadIdx.x & 31;
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
     }
     bool timeout = false;
     Chain ch;
-    const StepResult R = geom_step_warp<MODE, false>(G, ok, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout, mc, ch);
+    const StepResult R = geom_step_warp<MODE, false>(G, ok, leaf, p, v, inv_dir(v), prop, true, cnt, &timeout, walk_cap,
+                                                     mc, ch);
     if (ok) {
       if (timeout) flag(status, kStTimeout);
       double s = R.step;
@@ -213,6 +215,8 @@ struct TParams {
   int interact_min;  // run the interaction phase once at least this many lanes wait for it
   int walk_budget;   // voxel nodes a boundary search walks per round before it yields
   int regroup;       // regrouping kernel: rounds between block-wide regroups of the tracks
+  int walk_cap;      // voxel nodes a boundary search may walk (then G4N_ERR_TIMEOUT)
+  int trial_cap;     // trials of a rejection sampler (then G4N_ERR_TIMEOUT)
   const mlp::SmemWeights *mlp_w;  // learned mode: weights (device image)
   const MlpLog *log;              // plain mode: training-sample log (null: none)
 };
@@ -231,9 +235,9 @@ __device__ __forceinline__ int find_item(const DItem *items, int n_items, int64_
 // with a^2 + b^2 > 1 + 1e-5 in FP32 (from the Philox integers; error < 2e-6) are rejected
 // without FP64 work; the others take the FP64 test and, if accepted, the FP64 evaluation.
 __device__ __forceinline__ bool disc_azimuth(uint64_t seed, int64_t tid, uint32_t stream, uint32_t &draw, double &c,
-                                             double &s) {
+                                             double &s, int trials) {
 #pragma unroll 1
-  for (int t = 0; t < 1000; ++t) {
+  for (int t = 0; t < trials; ++t) {
     const M53x2 ab = philox_m53_pair(seed, tid, stream, draw);
     const uint64_t ma = ab.a, mb = ab.b;
     const float af = 2.0f * m53_float(ma) - 1.0f, bf = 2.0f * m53_float(mb) - 1.0f;
@@ -255,13 +259,14 @@ __device__ __forceinline__ bool disc_azimuth(uint64_t seed, int64_t tid, uint32_
 }
 
 // Source of track tid (stream 0).
-__device__ void make_source(const double *src, uint64_t seed, int64_t tid, V3 &x, V3 &u, double &E, uint32_t *status) {
+__device__ void make_source(const double *src, uint64_t seed, int64_t tid, V3 &x, V3 &u, double &E, uint32_t *status,
+                            int trials) {
   uint32_t draw = 0;
   x = V3{src[0], src[1], src[2]};
   if (src[3] > 0.0) {
     bool ok = false;
 #pragma unroll 1
-    for (int t = 0; t < 1000; ++t) {
+    for (int t = 0; t < trials; ++t) {
       const M53x2 ab = philox_m53_pair(seed, tid, 0, draw);  // one block per trial
       const double a = 2.0 * m53_double(ab.a) - 1.0;
       const double b = 2.0 * m53_double(ab.b) - 1.0;
@@ -280,7 +285,7 @@ __device__ void make_source(const double *src, uint64_t seed, int64_t tid, V3 &x
   if (src[7] != 0.0) {
     const double ct = 2.0 * philox_uniform(seed, tid, 0, draw) - 1.0;
     double cph, sph;
-    if (!disc_azimuth(seed, tid, 0, draw, cph, sph)) flag(status, kStRejection);
+    if (!disc_azimuth(seed, tid, 0, draw, cph, sph, trials)) flag(status, kStRejection);
     const double st = sqrt(fmax(0.0, (1.0 - ct) * (1.0 + ct)));
     u = V3{st * cph, st * sph, ct};
   } else {
@@ -332,7 +337,7 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
     Gp = &P.geoms[it.geom];
     V3 u;
     double E;
-    make_source(it.src, P.seed, t.tid, t.x, u, E, P.status);
+    make_source(it.src, P.seed, t.tid, t.x, u, E, P.status, P.trial_cap);
     set_direction(t, u);
     tally(P, t, Gp->n_vol + 1, E);
     event<EV>(cnt, G4N_C_TRACKS);
@@ -371,13 +376,14 @@ __device__ int start_warp(const TParams &P, bool active, int64_t g, Track &t, Co
 // others are taken on the FP64 thresholds of the plain formulas.  The accepted trial's eta
 // and cos theta are computed in FP64.  FP64 work is left for the accepted trial and the
 // rare close calls.
-__device__ __forceinline__ bool kahn(double E, uint64_t seed, int64_t tid, uint32_t &draw, double &eta, double &cost) {
+__device__ __forceinline__ bool kahn(double E, uint64_t seed, int64_t tid, uint32_t &draw, double &eta, double &cost,
+                                     int trials) {
   constexpr float kMargin = 1e-5f;
   const double al = E / kMeC2;
   const float alf = (float)al;
   const float p1f = (1.0f + 2.0f * alf) / (9.0f + 2.0f * alf);
 #pragma unroll 1
-  for (int t = 0; t < 1000; ++t) {
+  for (int t = 0; t < trials; ++t) {
     const M53x2 b12 = philox_m53_pair(seed, tid, 1, draw);
     const uint64_t m1 = b12.a, m2 = b12.b;
     const uint64_t m3 = philox_m53(seed, tid, 1, draw);
@@ -454,8 +460,11 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     const bool mu_pos = nonzero_bits(t.mu);  // mu >= 0
     lazy = MODE == kFP64 && mu_pos && !mc.log;
     if (!lazy) sphys = mu_pos ? t.Y / t.mu : kInf;
-    // a zero safety (after every boundary crossing) always needs the boundary search
-    need_geo = resume || !nonzero_bits(t.safety) || (lazy ? !(t.Y < t.safety * t.mu) : !(sphys < t.safety));
+    // a zero safety (after every boundary crossing) always needs the boundary search.  Lazy form: the
+    // search is skipped only when Y < safety mu by more than the rounding of the product, so that
+    // fl(Y / mu) < safety holds as well (the comparison the oracle makes)
+    need_geo = resume || !nonzero_bits(t.safety) ||
+               (lazy ? !(t.Y < t.safety * t.mu * (1.0 - 0x1p-50)) : !(sphys < t.safety));
     want_saf = !(MODE == kFP64 && L.vox < 0);
     if (!need_geo) {
       diag<COUNT>(cnt, G4N_C_SAFETY_SKIPS);
@@ -463,7 +472,9 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     } else {
       const bool aligned = L.flags & kWorldAligned;
       world_to_local(G.wxf[t.leaf], aligned, t.x, t.u, p, v);
-      iv = aligned ? t.iu : inv_dir(v);
+      // the reciprocal direction serves the FP64 voxel walk and a box's exit; the FP32 modes walk in
+      // FP32 (their rare FP64 node step forms it itself) and need it only in box leaves
+      iv = aligned ? t.iu : ((MODE == kFP64 || L.kind == kBox) ? inv_dir(v) : Inv3{0.0, 0.0, 0.0});
       // the voxel walk may stop at any bound >= sphys: candidates found beyond sphys lose
       // to the physics step all the same
       lim_geo = !lazy ? sphys
@@ -476,7 +487,7 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   // the learned proposal and the sample log look at the first node only: no yielding there
   const int budget = (!YIELD || MODE == kLearned || mc.log) ? 0 : P.walk_budget;
   const StepResult R = geom_step_warp<MODE, COUNT>(G, need_geo, need_geo ? t.leaf : 0, p, v, iv, lim_geo, want_saf,
-                                                   cnt, &timeout, mc, wch, resume, t.w, budget);
+                                                   cnt, &timeout, P.walk_cap, mc, wch, resume, t.w, budget);
   if (act && R.yielded) {
     // the search used its node budget: the step continues in a later round
     t.w = R.resume;
@@ -490,7 +501,19 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     if (timeout) flag(P.status, kStTimeout);
     if (need_geo) {
       t.safety = R.safety;
-      if (!R.physics && (lazy ? R.step * t.mu <= t.Y : R.step <= sphys)) {
+      // geometry wins iff step <= fl(Y / mu).  Lazy form: the product step mu decides when it lies
+      // outside Y (1 +- 2^-50), a margin that covers the rounding of both forms; a near-tie takes
+      // the division itself
+      bool geo_first;
+      if (!lazy) {
+        geo_first = R.step <= sphys;
+      } else {
+        const double a = R.step * t.mu;
+        if (a < t.Y * (1.0 - 0x1p-50)) geo_first = true;
+        else if (a > t.Y * (1.0 + 0x1p-50)) geo_first = false;
+        else geo_first = R.step <= t.Y / t.mu;
+      }
+      if (!R.physics && geo_first) {
         geo = true;
         s = R.step;
         lim = R.lim;
@@ -583,8 +606,8 @@ __device__ int interact(const TParams &P, Track &t, Counters &cnt) {
   }
   event<EV>(cnt, G4N_C_COMPTON);
   double eta, cost, cph, sph;
-  bool ok = kahn(t.E, P.seed, t.tid, t.draw, eta, cost);
-  ok &= disc_azimuth(P.seed, t.tid, 1, t.draw, cph, sph);
+  bool ok = kahn(t.E, P.seed, t.tid, t.draw, eta, cost, P.trial_cap);
+  ok &= disc_azimuth(P.seed, t.tid, 1, t.draw, cph, sph, P.trial_cap);
   if (!ok) flag(P.status, kStRejection);
   set_direction(t, deflect(t.u, cost, cph, sph));
   const double E1 = t.E / eta;
@@ -844,6 +867,7 @@ struct FParams {
   unsigned long long *q_head;
   uint32_t *status;
   int64_t max_steps;
+  int walk_cap;
   const mlp::SmemWeights *mlp_w;
 };
 
@@ -925,12 +949,12 @@ __global__ void __launch_bounds__(128, 3) k_free_path(const FParams P) {
     if (active) {
       const bool aligned = G.vol[leaf].flags & kWorldAligned;
       world_to_local(G.wxf[leaf], aligned, x, u, p, v);
-      iv = aligned ? iu : inv_dir(v);
+      iv = aligned ? iu : ((MODE == kFP64 || G.vol[leaf].kind == kBox) ? inv_dir(v) : Inv3{0.0, 0.0, 0.0});
     }
     bool timeout = false;
     Chain ch;
     const StepResult R = geom_step_warp<MODE, COUNT>(G, active, active ? leaf : 0, p, v, iv, kInf, false, cnt, &timeout,
-                                                     mc, ch);
+                                                     P.walk_cap, mc, ch);
     bool cross = false;
     double s = 0.0;
     if (active) {
@@ -1036,18 +1060,25 @@ int check_geom(g4n_ctx *ctx, int32_t geom) {
   return G4N_OK;
 }
 
+// The workspace header (queue head, status word, sample log) is allocated once and never moves;
+// the item table grows by doubling.  An outgrown table may still be read by work in flight on
+// some stream, so it is retired (freed by g4n_destroy) rather than freed: growing never
+// synchronizes the device.
 int ensure_ws(g4n_ctx *ctx, size_t item_bytes) {
-  const size_t need = sizeof(Workspace) + item_bytes;
-  if (ctx->ws && ctx->ws_bytes >= need) return G4N_OK;
-  if (ctx->ws) {
-    cudaDeviceSynchronize();
-    cudaFree(ctx->ws);
-    ctx->ws = nullptr;
+  if (!ctx->ws) {
+    if (cudaMalloc(&ctx->ws, sizeof(Workspace)) != cudaSuccess) {
+      ctx->ws = nullptr;
+      return g4n_fail(ctx, G4N_ERR_OOM, "workspace allocation failed");
+    }
+    if (cudaMemset(ctx->ws, 0, sizeof(Workspace)) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_CUDA, "workspace init failed");
   }
-  size_t bytes = std::max<size_t>(need, 1 << 16);
-  if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_OOM, "workspace allocation failed");
-  if (cudaMemset(ctx->ws, 0, sizeof(Workspace)) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_CUDA, "workspace init failed");
-  ctx->ws_bytes = bytes;
+  if (item_bytes <= ctx->items_bytes) return G4N_OK;
+  const size_t bytes = std::max<size_t>({item_bytes, 2 * ctx->items_bytes, size_t(1) << 16});
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_OOM, "item table allocation failed");
+  if (ctx->items) ctx->retired.push_back(ctx->items);
+  ctx->items = p;
+  ctx->items_bytes = bytes;
   return G4N_OK;
 }
 
@@ -1176,7 +1207,7 @@ int g4n_compute_step(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, c
   if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<grid_for(ctx, n, 128), 128, smem, (cudaStream_t)stream>>>(ctx->d_geoms, geom, n, pos, dir, depth, path,
                                                                     proposed, out_step, out_safety, out_limiter,
-                                                                    &ws->status, g4n_mlp_image(ctx));
+                                                                    &ws->status, g4n_mlp_image(ctx), ctx->walk_cap);
   return launch_error(ctx, "compute_step launch");
 }
 
@@ -1206,7 +1237,7 @@ static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_ede
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   Workspace *ws = (Workspace *)ctx->ws;
-  DItem *d_items = (DItem *)((char *)ctx->ws + sizeof(Workspace));
+  DItem *d_items = (DItem *)ctx->items;
   if (cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(DItem), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(&ws->q_head, 0, sizeof(unsigned long long), st) != cudaSuccess)
     return g4n_fail(ctx, G4N_ERR_CUDA, "transport: item upload failed");
@@ -1230,6 +1261,8 @@ static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_ede
   P.interact_min = inter;
   P.walk_budget = budget;
   P.regroup = regroup;
+  P.walk_cap = ctx->walk_cap;
+  P.trial_cap = ctx->trial_cap;
   P.log = logging ? &ws->log : nullptr;
   return launch_transport(ctx, b, P, block, st);
 }
@@ -1247,12 +1280,13 @@ int g4n_transport_batch_host(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_
   const size_t need = e_bytes + c_bytes + h_bytes + l_bytes + 4 * 256;
   cudaSetDevice(ctx->device);
   if (ctx->d_stage_bytes < need) {
-    cudaDeviceSynchronize();
-    cudaFree(ctx->d_stage);
-    ctx->d_stage = nullptr;
-    ctx->d_stage_bytes = 0;
-    if (cudaMalloc(&ctx->d_stage, need) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_OOM, "transport_host: staging allocation failed");
-    ctx->d_stage_bytes = need;
+    // grow by doubling; the outgrown buffer is retired, not freed (no device-wide synchronization)
+    const size_t bytes = std::max(need, 2 * ctx->d_stage_bytes);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return g4n_fail(ctx, G4N_ERR_OOM, "transport_host: staging allocation failed");
+    if (ctx->d_stage) ctx->retired.push_back(ctx->d_stage);
+    ctx->d_stage = p;
+    ctx->d_stage_bytes = bytes;
   }
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   char *base = (char *)ctx->d_stage;
@@ -1346,6 +1380,7 @@ int g4n_free_path(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, cons
   P.q_head = &ws->q_head;
   P.status = &ws->status;
   P.max_steps = max_steps > 0 ? max_steps : 1000000;
+  P.walk_cap = ctx->walk_cap;
   P.mlp_w = g4n_mlp_image(ctx);
   const FreePathKernel kern = free_path_kernel(mode, (flags & G4N_FLAG_DIAGNOSTICS) && out_counters);
   const int block = 128;
@@ -1357,6 +1392,14 @@ int g4n_free_path(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, cons
   grid = std::max<int64_t>(1, std::min<int64_t>(grid, (n + block - 1) / block));
   kern<<<(int)grid, block, smem, st>>>(P);
   return launch_error(ctx, "free_path launch");
+}
+
+int g4n_set_loop_caps(g4n_ctx *ctx, int32_t max_walk_nodes, int32_t max_sampler_trials) {
+  if (!ctx) return G4N_ERR_ARG;
+  if (max_walk_nodes < 0 || max_sampler_trials < 0) return g4n_fail(ctx, G4N_ERR_ARG, "loop caps must be >= 0");
+  ctx->walk_cap = max_walk_nodes > 0 ? max_walk_nodes : kDefaultWalkCap;
+  ctx->trial_cap = max_sampler_trials > 0 ? max_sampler_trials : kDefaultTrialCap;
+  return G4N_OK;
 }
 
 int g4n_sync(g4n_ctx *ctx, g4n_stream stream) {
@@ -1498,6 +1541,8 @@ extern "C" int g4n_transport_batch_noalloc(g4n_ctx *ctx, const g4n_batch_desc *b
     P.interact_min = inter;
     P.walk_budget = budget;
     P.regroup = regroup;
+    P.walk_cap = ctx->walk_cap;
+    P.trial_cap = ctx->trial_cap;
     P.log = nullptr;
     rc = launch_transport(ctx, b, P, block, st);
     if (rc) return rc;
@@ -1578,6 +1623,8 @@ int g4n_graph_create(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_edep, ui
   P.interact_min = inter;
   P.walk_budget = budget;
   P.regroup = regroup;
+  P.walk_cap = ctx->walk_cap;
+  P.trial_cap = ctx->trial_cap;
   P.log = nullptr;
   P.mlp_w = g4n_mlp_image(ctx);
   const TransportKernel kern = transport_kernel(b->mode, b->flags & G4N_FLAG_DIAGNOSTICS, P.walk_budget < kNeverYield, P.regroup > 0);

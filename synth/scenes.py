@@ -514,3 +514,20 @@ def modular_calorimeter(n_mod: int = 2, n_tower: int = 4, n_pairs: int = 10):
                                          -n_mod * mod_half + mod_half * (2 * j + 1), tower_hz))
                   for i in range(n_mod) for j in range(n_mod)]
     return base, logicals, placements
+
+
+# Query workloads (locate / compute_step benchmarks): points uniform in a box that holds the detector
+# and some of the world around it, directions isotropic.
+QUERY_BOXES = {"calorimeter": ((-600.0, -600.0, -50.0), (600.0, 600.0, 425.0)),
+               "barrel": ((-1600.0, -1600.0, -1600.0), (1600.0, 1600.0, 1600.0))}
+
+
+def query_points(scene: str, n: int, seed: int):
+    """(pos, dir) as (3, n) float64 arrays (structure of arrays): pos uniform in QUERY_BOXES[scene], dir
+    isotropic (normalised Gaussian triples)."""
+    lo, hi = (np.asarray(b) for b in QUERY_BOXES[scene])
+    rng = np.random.default_rng(seed)
+    p = lo[:, None] + (hi - lo)[:, None] * rng.random((3, n))
+    v = rng.standard_normal((3, n))
+    v /= np.sqrt((v * v).sum(axis=0))[None, :]
+    return np.ascontiguousarray(p), np.ascontiguousarray(v)

@@ -214,3 +214,85 @@ def test_logical_volume_errors(g4):
         assert e.value.code == -2
     finally:
         g4.g4n_destroy(ctx)
+
+
+class _FakeCuda:
+    """A CPU tensor posing as a CUDA tensor on device `index` (for the binding's argument checks only:
+    the checks raise before any library call, so no pointer is ever used)."""
+
+    def __init__(self, t, index=0):
+        self.t, self.is_cuda = t, True
+        self.device = type("D", (), {"index": index})()
+
+    dtype = property(lambda self: self.t.dtype)
+    shape = property(lambda self: self.t.shape)
+
+    def is_contiguous(self):
+        return self.t.is_contiguous()
+
+    def numel(self):
+        return self.t.numel()
+
+    def dim(self):
+        return self.t.dim()
+
+    def data_ptr(self):
+        return self.t.data_ptr()
+
+
+@pytest.mark.parametrize("case", ["counters_short", "hash_short", "len_short", "edep_rows", "wrong_device"])
+def test_binding_refuses_undersized_or_misplaced_outputs(g4, case):
+    """The transport kernels write G4N_N_COUNTERS counters and one hash / length per track: the binding
+    refuses smaller tensors, and tensors on another device than the context's, before calling the library."""
+    import torch
+    items = g4.make_items([(0, 1000, 0, synth.scenes.tiny_source(), 0), (0, 24, 5000, synth.scenes.tiny_source(), 0)])
+    ctx = ctypes_ctx = type("C", (), {"value": 0x1234})()
+    g4.binding._CTX_DEVICE[ctypes_ctx.value] = 0
+    try:
+        edep = _FakeCuda(torch.zeros((100, 13), dtype=torch.float64))
+        cnt = _FakeCuda(torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64))
+        h = _FakeCuda(torch.zeros(1024, dtype=torch.int64))
+        ln = _FakeCuda(torch.zeros(1024, dtype=torch.float64))
+        if case == "counters_short":
+            cnt = _FakeCuda(torch.zeros(g4.G4N_N_COUNTERS - 1, dtype=torch.int64))
+        elif case == "hash_short":
+            h = _FakeCuda(torch.zeros(1023, dtype=torch.int64))
+        elif case == "len_short":
+            ln = _FakeCuda(torch.zeros(1000, dtype=torch.float64))
+        elif case == "edep_rows":
+            edep = _FakeCuda(torch.zeros((99, 13), dtype=torch.float64))
+        else:
+            h = _FakeCuda(torch.zeros(1024, dtype=torch.int64), index=1)
+        for call in (g4.g4n_transport_batch, g4.g4n_transport_batch_noalloc, g4.g4n_graph_create):
+            with pytest.raises(ValueError):
+                call(ctx, items, 1, edep, cnt, h, ln)
+        # the same arguments at the right sizes pass the checks
+        ok = g4.binding._transport_ptrs(ctx, items, _FakeCuda(torch.zeros((100, 13), dtype=torch.float64)),
+                                        _FakeCuda(torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64)),
+                                        _FakeCuda(torch.zeros(1024, dtype=torch.int64)),
+                                        _FakeCuda(torch.zeros(1024, dtype=torch.float64)), 100)
+        assert len(ok) == 4 and all(p is not None for p in ok)
+    finally:
+        g4.binding._CTX_DEVICE.pop(ctypes_ctx.value, None)
+
+
+def test_binding_checks_query_shapes(g4):
+    """locate / compute_step / free_path: (3, n) positions and directions, per-query arrays of n."""
+    import torch
+    ctx = type("C", (), {"value": 0x4321})()
+    g4.binding._CTX_DEVICE[ctx.value] = 0
+    try:
+        pos = _FakeCuda(torch.zeros((3, 10), dtype=torch.float64))
+        with pytest.raises(ValueError):
+            g4.g4n_locate(ctx, 0, pos, _FakeCuda(torch.zeros((3, 9), dtype=torch.float64)))
+        with pytest.raises(ValueError):
+            g4.g4n_locate(ctx, 0, pos, pos, out_depth=_FakeCuda(torch.zeros(9, dtype=torch.int32)),
+                          out_path=_FakeCuda(torch.zeros((g4.G4N_DMAX, 10), dtype=torch.int32)))
+        with pytest.raises(ValueError):
+            g4.g4n_free_path(ctx, 0, pos, pos, _FakeCuda(torch.zeros(9, dtype=torch.float64)), 1.0,
+                             out_T=_FakeCuda(torch.zeros(10, dtype=torch.float64)),
+                             out_steps=_FakeCuda(torch.zeros(10, dtype=torch.int32)))
+        with pytest.raises(ValueError):
+            g4.g4n_locate(ctx, 0, _FakeCuda(torch.zeros((10, 3), dtype=torch.float64)), pos)
+    finally:
+        g4.binding._CTX_DEVICE.pop(ctx.value, None)
