@@ -50,12 +50,12 @@ FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_transport launch of the default workload:
-# a single-pass ncu capture of the first timed launch (after the 256 MB L2 flush, whose dirty lines are written back
-# during the launch), summarised in profiles/k_transport_fp64_calorimeter_full.md.  It is reported only while the
-# CUDA sources hash to the value they had when the capture was taken (else the kernel has changed since).
-NCU_TRAFFIC = {"sources_sha256": "f5b74612af8e56fc1b5b7f15d7be3aee93e6e3a602aff8ff4f7502fce686035d",
-               "bytes_per_launch": 2223104 + 41046016}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_transport launch, per workload and mode, from
+# a single-pass ncu capture of the bench's first timed launch (after the 256 MB L2 flush, whose dirty lines are
+# written back during the launch) and of a launch of the same kernel after the same flush with no track to carry
+# (the flush's own write-back): summaries in profiles/.  Reported only while the CUDA sources hash to the value they
+# had when the captures were taken (else the kernel has changed since).
+NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": {}}
 
 
 def cuda_sources_sha256() -> str:
@@ -70,10 +70,12 @@ def cuda_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
-    if NCU_TRAFFIC["bytes_per_launch"] is None or NCU_TRAFFIC["sources_sha256"] != cuda_sources_sha256():
+def measured_traffic(workload: str, mode: str):
+    """The captured DRAM bytes of one launch of (workload, mode), or None (not captured, or sources changed)."""
+    per = NCU_TRAFFIC["bytes_per_launch"] or {}
+    if NCU_TRAFFIC["sources_sha256"] != cuda_sources_sha256():
         return None
-    return NCU_TRAFFIC["bytes_per_launch"]
+    return per.get(f"{workload}/{mode}")
 
 
 def algorithmic_flops(c: dict) -> float:
@@ -184,36 +186,43 @@ def calorimeter(voxel: str = "default"):
     return sc, synth.scenes.calorimeter_source(), synth.scenes.CONFIG_SEEDS[1][1]
 
 
-def cpu_baseline(sc, src, seed, target_s: float = 12.0) -> dict:
-    """The FP64 oracle (brute-force navigation), as it stands, on all host cores; a bounded sample."""
-    import oracle
-    og = oracle.Geometry(sc)
-    threads = os.cpu_count() or 1
-    n, n2, dt, steps, tid = 4096, 0, 0.0, 0, 10_000_000
-    while dt < target_s and n2 < 50_000_000:
+def _oracle_rate(og, src, seed, threads: int, target_s: float, tid: int, n0: int) -> dict:
+    """Steps/s and tracks/s of oracle transports of growing batches of the following track ids, until
+    target_s of wall time."""
+    n, n_done, dt, steps = n0, 0, 0.0, 0
+    used = threads
+    while dt < target_s and n_done < 50_000_000:
         t0 = time.perf_counter()
         r = og.transport(src, seed, n, tid0=tid, want_hash=False, want_len=False, threads=threads)
         dt += time.perf_counter() - t0
         steps += int(r["counters"][1])
+        used = int(r["threads"])
         tid += n
-        n2 += n
+        n_done += n
         n *= 2
-    out = {"value": steps / dt, "unit": "steps/s", "cores": int(r["threads"]), "kind": "oracle",
-           "tracks_per_s": n2 / dt, "seconds": dt,
-           "sample": f"{n2} histories (track ids from 10^7) of the same workload, brute-force FP64 oracle, "
-                     f"OpenMP over tracks"}
-    # one thread as well (the paper's 1-thread rows): a smaller sample of the following track ids
-    n, n1, dt1, steps1 = 256, 0, 0.0, 0
-    while dt1 < target_s / 4 and n1 < 10_000_000:
-        t0 = time.perf_counter()
-        r = og.transport(src, seed, n, tid0=tid, want_hash=False, want_len=False, threads=1)
-        dt1 += time.perf_counter() - t0
-        steps1 += int(r["counters"][1])
-        tid += n
-        n1 += n
-        n *= 2
-    out["single_thread"] = {"value": steps1 / dt1, "unit": "steps/s", "cores": int(r["threads"]),
-                            "tracks_per_s": n1 / dt1, "seconds": dt1, "sample": f"{n1} histories, one thread"}
+    return {"value": steps / dt, "unit": "steps/s", "cores": used, "tracks_per_s": n_done / dt, "seconds": dt,
+            "histories": n_done, "next_tid": tid}
+
+
+def cpu_baseline(sc, src, seed, target_s: float = 12.0) -> dict:
+    """The FP64 oracle on the host cores, on bounded samples of the same workload: its uniform-grid timing
+    mode (results identical to its brute-force search) on all cores and on one thread, and the brute-force
+    search itself on all cores beside it."""
+    import oracle
+    threads = os.cpu_count() or 1
+    og = oracle.Geometry(sc)
+    og.use_grids(True)
+    main = _oracle_rate(og, src, seed, threads, target_s, 10_000_000, 4096)
+    one = _oracle_rate(og, src, seed, 1, target_s / 4, main["next_tid"], 256)
+    brute = _oracle_rate(oracle.Geometry(sc), src, seed, threads, target_s / 3, one["next_tid"], 4096)
+    out = {"value": main["value"], "unit": "steps/s", "cores": main["cores"], "kind": "oracle",
+           "tracks_per_s": main["tracks_per_s"], "seconds": main["seconds"],
+           "sample": f"{main['histories']} histories (track ids from 10^7) of the same workload, FP64 oracle in its "
+                     f"uniform-grid timing mode (histories identical to its brute-force search), OpenMP over tracks"}
+    out["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "tracks_per_s", "seconds")}
+    out["single_thread"]["sample"] = f"{one['histories']} histories, one thread, timing mode"
+    out["brute_force"] = {k: brute[k] for k in ("value", "unit", "cores", "tracks_per_s", "seconds")}
+    out["brute_force"]["sample"] = f"{brute['histories']} histories, all cores, brute-force search (every daughter)"
     return out
 
 
@@ -229,6 +238,7 @@ def cpu_baseline_batched(target_s: float = 12.0) -> dict:
         if dt >= target_s:
             break
         og = oracle.Geometry(s2)
+        og.use_grids(True)
         n = min(nt, 2000)
         t0 = time.perf_counter()
         r = og.transport(src, seed, n, tid0=n_tracks, want_hash=False, want_len=False, threads=threads)
@@ -238,16 +248,39 @@ def cpu_baseline_batched(target_s: float = 12.0) -> dict:
         n_geo += 1
     return {"value": steps / dt, "unit": "steps/s", "cores": threads, "kind": "oracle", "tracks_per_s": n_tracks / dt,
             "seconds": dt, "sample": f"up to 2000 tracks of each of the first {n_geo} of the 256 worlds ({n_tracks} "
-                                     f"histories), brute-force FP64 oracle, OpenMP over tracks"}
+                                     f"histories), FP64 oracle in its uniform-grid timing mode, OpenMP over tracks"}
+
+
+def reference_workload(args):
+    """(scene, source, seed, description) of the transport workload the reference arm times."""
+    import synth
+    w = args.workload
+    if w == "calorimeter":
+        sc, src, seed = calorimeter(args.voxel)
+        return sc, src, seed, WORKLOAD
+    if w == "tiny":
+        return (synth.scenes.tiny_scene(), synth.scenes.tiny_source(), synth.scenes.CONFIG_SEEDS[0][1],
+                WORKLOADS["tiny"])
+    if w in ("barrel", "barrel_learned", "barrel_nested"):
+        sc = synth.scenes.nested_barrel_scene() if w == "barrel_nested" else synth.scenes.barrel_scene()
+        return (sc, synth.scenes.barrel_source(), synth.scenes.CONFIG_SEEDS[4 if w == "barrel_learned" else 3][1],
+                WORKLOADS[w])
+    return None
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc, src, seed = calorimeter()
+    ref = reference_workload(args)
+    if ref is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"the reference arm times transport workloads; "
+                                                              f"{args.workload} is not one"}))
+        return
+    sc, src, seed, workload = ref
     import oracle
     og = oracle.Geometry(sc)
+    og.use_grids(True)
     threads = os.cpu_count() or 1
     n = max(64, args.ref_tracks)
     times, steps = [], []
@@ -263,7 +296,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tracks_per_step": n, "mode": "fp64 brute-force oracle"},
+            "config": {"workload": workload, "tracks_per_step": n,
+                       "mode": "FP64 oracle, uniform-grid timing mode (histories identical to its brute-force search)"},
             "tracks_per_s": n * args.steps / tot,
             "cpu_baseline": {"value": val, "unit": "steps/s", "cores": threads, "kind": "oracle",
                              "sample": f"{n} histories per step of the same workload"},
@@ -286,7 +320,8 @@ def time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream,
         barrier()
     t_wall = time.perf_counter()
     for k in range(args.steps):
-        flush.fill_(float(k))
+        if not getattr(args, "no_flush", False):
+            flush.fill_(float(k))
         ev[k][0].record(stream)
         g4.g4n_transport_batch(ctx, items, seed + k, edep, cnt, n_batches=edep.shape[0], mode=mode, stream=stream,
                                **launch)
@@ -484,7 +519,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload, "tracks_per_gpu": n, "mode": chosen,
-                   "l2": "flushed between timed steps (256 MB write)", "launch": launch[chosen],
+                   "l2": ("not flushed (DRAM-traffic capture run)" if args.no_flush
+                          else "flushed between timed steps (256 MB write)"), "launch": launch[chosen],
                    "autotuned": bool(args.autotune), "voxel": args.voxel if args.workload == "calorimeter" else "smart"},
         "tracks_per_s": R["tracks_per_s"],
         "steps_per_track": R["steps_per_track"],
@@ -495,7 +531,7 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": measured_traffic() if args.workload == "calorimeter" else None,
+                     "traffic": measured_traffic(args.workload, chosen),
                      "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (recipe nominal 1.25 TFLOP/s)",
                      "kernel": "k_transport", "flops_per_launch": flops},
         "hbm": {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / t_launch / 1e9,
@@ -851,6 +887,9 @@ def main():
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tune-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-flush", action="store_true",
+                    help="no L2 flush between timed launches: only for the DRAM-traffic capture of a launch in the "
+                         "steady state (the flush's dirty lines would otherwise be written back during the launch)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 10 if args.workload.startswith("barrel") else 20

@@ -90,6 +90,7 @@ def lib():
             "o_transport_trace": (i, [i, vp, u64, i64, d, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                       vp, vp]),
             "o_rotate": (None, [vp, d, d, d, vp]),
+            "o_use_grids": (None, [i, i]),
             "o_compute_step_many": (None, [i, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -138,6 +139,10 @@ class Geometry:
         if rc != 0:
             raise ValueError(f"oracle: finalize failed ({rc})")
         self.n_volumes = L.o_n_volumes(self.gid)
+
+    def use_grids(self, on: bool = True) -> None:
+        """Timing mode: uniform grids over the daughters of every mother with 8 or more (results unchanged)."""
+        lib().o_use_grids(self.gid, 1 if on else 0)
 
     # -- solids (local frame) -------------------------------------------------
     def solid_inside(self, solid: int, p, v) -> bool:
@@ -207,13 +212,13 @@ class Geometry:
         nd = lib().o_relocate(self.gid, _p(path), int(depth), _p(_f64(p)), _p(_f64(v)))
         return nd, path
 
-    def compute_step(self, depth: int, path, p, v, proposed: float = np.inf):
+    def compute_step(self, depth: int, path, p, v, proposed: float = np.inf, safety: bool = True):
         path = np.ascontiguousarray(np.asarray(path, dtype=np.int32))
         step = np.zeros(1)
         lim = np.zeros(1, dtype=np.int32)
         saf = np.zeros(1)
         rc = lib().o_compute_step(self.gid, int(depth), _p(path), _p(_f64(p)), _p(_f64(v)), float(proposed),
-                                  _p(step), _p(lim), _p(saf))
+                                  _p(step), _p(lim), _p(saf) if safety else None)
         if rc != 0:
             raise ValueError("oracle: compute_step outside the world")
         return float(step[0]), int(lim[0]), float(saf[0])

@@ -79,12 +79,24 @@ typedef struct {
   double *E, *muC, *muP;
 } OMat;
 
+/* Uniform grid over a mother's bounding box (its own frame): cell (i, j, k) lists, in placement
+ * order, the daughters whose bounding box grown by O_GRID_PAD overlaps it (see "uniform-grid
+ * acceleration" below). */
+typedef struct {
+  int n[3];
+  double lo[3], w[3];
+  int *off;                  /* n0 n1 n2 + 1 offsets into lst */
+  int *lst;
+} OGrid;
+
 typedef struct {
   OSolid *sol; int nsol, capsol;
   OVol *vol; int nvol, capvol;
   OMat *mat; int nmat, capmat;
   int *dau;                  /* daughter ids grouped by mother, in placement order */
   int finalized;
+  OGrid **grid;              /* per volume: NULL or its daughters' grid (timing mode) */
+  int use_grid;
 } OGeom;
 
 static OGeom *G[O_MAXG];
@@ -107,6 +119,11 @@ void o_free_all(void) {
     OGeom *g = G[i];
     if (!g) continue;
     for (int m = 0; m < g->nmat; ++m) { free(g->mat[m].E); free(g->mat[m].muC); free(g->mat[m].muP); }
+    if (g->grid) {
+      for (int v = 0; v < g->nvol; ++v)
+        if (g->grid[v]) { free(g->grid[v]->off); free(g->grid[v]->lst); free(g->grid[v]); }
+      free(g->grid);
+    }
     free(g->mat); free(g->sol); free(g->vol); free(g->dau); free(g);
     G[i] = NULL;
   }
@@ -682,6 +699,122 @@ static void frame_of(const OGeom *g, const int *path, int depth, const double *p
   memcpy(vl, va, sizeof(va));
 }
 
+/* ------------------------------------------------------------------ uniform-grid acceleration
+ * Timing mode only (the CPU baseline of the benchmark): the plain definitions above search every
+ * daughter; with o_build_grids() a mother with at least O_GRID_MIN daughters gets a uniform grid over
+ * its bounding box, and
+ *  - locate tests only the daughters listed in the point's cell, in placement order (a daughter that
+ *    contains the point, band included, overlaps the cell: lists are built from bounding boxes grown
+ *    by O_GRID_PAD, far above the tolerance band and every rounding error of the cell lookup);
+ *  - the step visits the cells along the ray (3-D DDA) from the point's cell until the next cell
+ *    begins beyond the best distance found, evaluating each listed daughter once; a daughter entered
+ *    at t <= best has its entry point in a cell that begins at or before t, so it is evaluated; among
+ *    equal distances the lower placement index wins, as in the brute-force loop.
+ * The results are those of the brute-force search (tests compare histories on subsets of every
+ * workload).  Written independently of the library's voxels. */
+#define O_GRID_MIN 8
+#define O_GRID_PAD 1e-6
+#define O_GRID_MAXN 128
+#define O_GRID_SEEN 512
+
+/* Half-extents of a solid's bounding box in its own frame (tubes and cones: the full cylinder). */
+static void solid_half(const OSolid *s, double *h) {
+  if (s->kind == O_BOX) { h[0] = s->a; h[1] = s->b; h[2] = s->c; }
+  else if (s->kind == O_ORB) { h[0] = h[1] = h[2] = s->a; }
+  else if (s->kind == O_TUBE) { h[0] = h[1] = s->b; h[2] = s->c; }
+  else {
+    double r = fmax(fabs(s->ko * s->c + s->co), fabs(-s->ko * s->c + s->co));
+    h[0] = h[1] = r; h[2] = s->c;
+  }
+}
+
+static void build_grid(OGeom *g, int m) {
+  const OVol *mv = &g->vol[m];
+  double H[3];
+  solid_half(&g->sol[mv->solid], H);
+  double dlo[3], dhi[3], mean[3] = {0, 0, 0};
+  double (*bl)[3] = (double (*)[3])malloc((size_t)mv->ndau * sizeof(double[3]));
+  double (*bh)[3] = (double (*)[3])malloc((size_t)mv->ndau * sizeof(double[3]));
+  for (int k = 0; k < mv->ndau; ++k) {
+    const OVol *d = &g->vol[g->dau[mv->first + k]];
+    double h[3];
+    solid_half(&g->sol[d->solid], h);
+    const double ex = fabs(d->c) * h[0] + fabs(d->s) * h[1], ey = fabs(d->s) * h[0] + fabs(d->c) * h[1];
+    const double e[3] = {ex, ey, h[2]};
+    for (int a = 0; a < 3; ++a) {
+      bl[k][a] = d->t[a] - e[a] - O_GRID_PAD;
+      bh[k][a] = d->t[a] + e[a] + O_GRID_PAD;
+      mean[a] += 2.0 * e[a] / mv->ndau;
+    }
+  }
+  OGrid *gr = (OGrid *)calloc(1, sizeof(OGrid));
+  long ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    dlo[a] = -H[a];
+    dhi[a] = H[a];
+    int n = (int)ceil(2.0 * H[a] / fmax(mean[a], 1e-9));
+    n = n < 1 ? 1 : (n > O_GRID_MAXN ? O_GRID_MAXN : n);
+    gr->n[a] = n;
+    gr->lo[a] = dlo[a];
+    gr->w[a] = (dhi[a] - dlo[a]) / n;
+    ncell *= n;
+  }
+  /* counting pass, then fill (daughters in placement order) */
+  gr->off = (int *)calloc((size_t)ncell + 1, sizeof(int));
+  int lo3[3], hi3[3];
+  for (int pass = 0; pass < 2; ++pass) {
+    int *fill = pass ? (int *)calloc((size_t)ncell, sizeof(int)) : NULL;
+    for (int k = 0; k < mv->ndau; ++k) {
+      for (int a = 0; a < 3; ++a) {
+        lo3[a] = (int)floor((bl[k][a] - gr->lo[a]) / gr->w[a]);
+        hi3[a] = (int)floor((bh[k][a] - gr->lo[a]) / gr->w[a]);
+        lo3[a] = lo3[a] < 0 ? 0 : (lo3[a] >= gr->n[a] ? gr->n[a] - 1 : lo3[a]);
+        hi3[a] = hi3[a] < 0 ? 0 : (hi3[a] >= gr->n[a] ? gr->n[a] - 1 : hi3[a]);
+      }
+      for (int i = lo3[0]; i <= hi3[0]; ++i)
+        for (int j = lo3[1]; j <= hi3[1]; ++j)
+          for (int l = lo3[2]; l <= hi3[2]; ++l) {
+            const long c = ((long)i * gr->n[1] + j) * gr->n[2] + l;
+            if (pass == 0) gr->off[c + 1]++;
+            else gr->lst[gr->off[c] + fill[c]++] = g->dau[mv->first + k];
+          }
+    }
+    if (pass == 0) {
+      for (long c = 0; c < ncell; ++c) gr->off[c + 1] += gr->off[c];
+      gr->lst = (int *)malloc((size_t)(gr->off[ncell] > 0 ? gr->off[ncell] : 1) * sizeof(int));
+    } else {
+      free(fill);
+    }
+  }
+  free(bl);
+  free(bh);
+  g->grid[m] = gr;
+}
+
+/* Build the grids of every mother with at least O_GRID_MIN daughters and switch the timing mode on
+ * (on = 0 switches it off again; the grids are kept). */
+void o_use_grids(int gi, int on) {
+  OGeom *g = G[gi];
+  if (on && !g->grid) {
+    g->grid = (OGrid **)calloc((size_t)g->nvol, sizeof(OGrid *));
+    for (int m = 0; m < g->nvol; ++m)
+      if (g->vol[m].ndau >= O_GRID_MIN) build_grid(g, m);
+  }
+  g->use_grid = on;
+}
+
+static int grid_cell(const OGrid *gr, const double *p, int *c) {
+  for (int a = 0; a < 3; ++a) {
+    int k = (int)floor((p[a] - gr->lo[a]) / gr->w[a]);
+    c[a] = k < 0 ? 0 : (k >= gr->n[a] ? gr->n[a] - 1 : k);
+  }
+  return (c[0] * gr->n[1] + c[1]) * gr->n[2] + c[2];
+}
+
+static const OGrid *grid_of(const OGeom *g, int m) {
+  return (g->use_grid && g->grid) ? g->grid[m] : NULL;
+}
+
 static uint64_t *g_cnt_inside = NULL;   /* optional per-call counter of Inside tests */
 
 /* Enter, repeatedly, the first daughter in placement order whose solid contains the point. */
@@ -690,8 +823,18 @@ static void descend(const OGeom *g, int *path, int *depth, double *pl, double *v
     const OVol *m = &g->vol[path[*depth - 1]];
     int found = -1;
     double dl[3], dv[3];
-    for (int k = 0; k < m->ndau; ++k) {
-      int d = g->dau[m->first + k];
+    /* the daughters to test, in placement order: all of them, or those of the point's grid cell */
+    const int *ds = g->dau + m->first;
+    int nd = m->ndau;
+    const OGrid *gr = grid_of(g, path[*depth - 1]);
+    if (gr) {
+      int c[3];
+      const int cell = grid_cell(gr, pl, c);
+      ds = gr->lst + gr->off[cell];
+      nd = gr->off[cell + 1] - gr->off[cell];
+    }
+    for (int k = 0; k < nd; ++k) {
+      int d = ds[k];
       to_local(&g->vol[d], pl, vl, dl, dv);
       if (cnt) cnt[C_INSIDE]++;
       if (s_inside(&g->sol[g->vol[d].solid], dl, dv)) { found = d; break; }
@@ -745,6 +888,58 @@ int o_relocate(int gi, int *path, int depth, const double *p, const double *v) {
  * daughter's DistanceToIn (limiter = daughter id).  Ties: a daughter beats the
  * mother; between daughters the lower placement index wins.  Brute-force
  * isotropic safety.  Returns the geometric step. */
+/* The step of the timing mode: the cells along the ray, each listed daughter once (see above).
+ * Returns 0 when more daughters were met than it can remember (the caller then searches them all). */
+static int grid_step(const OGeom *g, const OGrid *gr, const double *pl, const double *vl, double *best_io,
+                     int *lim_io, uint64_t *cnt) {
+  int c[3], st[3];
+  double tmax[3], tdel[3];
+  grid_cell(gr, pl, c);
+  for (int a = 0; a < 3; ++a) {
+    if (vl[a] > 0.0) {
+      st[a] = 1;
+      tmax[a] = (gr->lo[a] + (c[a] + 1) * gr->w[a] - pl[a]) / vl[a];
+      tdel[a] = gr->w[a] / vl[a];
+    } else if (vl[a] < 0.0) {
+      st[a] = -1;
+      tmax[a] = (gr->lo[a] + c[a] * gr->w[a] - pl[a]) / vl[a];
+      tdel[a] = -gr->w[a] / vl[a];
+    } else {
+      st[a] = 0;
+      tmax[a] = O_INF;
+      tdel[a] = O_INF;
+    }
+  }
+  int seen[O_GRID_SEEN], nseen = 0;
+  double best = *best_io;
+  int lim = *lim_io;
+  for (;;) {
+    const int cell = (c[0] * gr->n[1] + c[1]) * gr->n[2] + c[2];
+    for (int k = gr->off[cell]; k < gr->off[cell + 1]; ++k) {
+      const int d = gr->lst[k];
+      int dup = 0;
+      for (int q = 0; q < nseen; ++q)
+        if (seen[q] == d) { dup = 1; break; }
+      if (dup) continue;
+      if (nseen == O_GRID_SEEN) return 0;
+      seen[nseen++] = d;
+      double dl[3], dv[3];
+      to_local(&g->vol[d], pl, vl, dl, dv);
+      if (cnt) cnt[C_DIST_IN]++;
+      const double t = s_dist_in(&g->sol[g->vol[d].solid], dl, dv);
+      if (t < O_INF && (t < best || (t == best && (lim == LIM_MOTHER || d < lim)))) { best = t; lim = d; }
+    }
+    const int a = tmax[0] <= tmax[1] ? (tmax[0] <= tmax[2] ? 0 : 2) : (tmax[1] <= tmax[2] ? 1 : 2);
+    if (!(tmax[a] <= best)) break;   /* the next cell begins beyond the best distance */
+    c[a] += st[a];
+    if (st[a] == 0 || c[a] < 0 || c[a] >= gr->n[a]) break;
+    tmax[a] += tdel[a];
+  }
+  *best_io = best;
+  *lim_io = lim;
+  return 1;
+}
+
 static double geom_step(const OGeom *g, const int *path, int depth, const double *p, const double *v,
                         int *limiter, double *safety, uint64_t *cnt) {
   double pl[3], vl[3];
@@ -753,6 +948,15 @@ static double geom_step(const OGeom *g, const int *path, int depth, const double
   const OSolid *ms = &g->sol[m->solid];
   double best = s_dist_out(ms, pl, vl);
   int lim = LIM_MOTHER;
+  const OGrid *gr = safety ? NULL : grid_of(g, path[depth - 1]);
+  if (gr) {
+    double b = best;
+    int l = lim;
+    if (grid_step(g, gr, pl, vl, &b, &l, cnt)) {
+      *limiter = l;
+      return b;
+    }
+  }
   double saf = safety ? s_safety_out(ms, pl) : 0.0;
   for (int k = 0; k < m->ndau; ++k) {
     int d = g->dau[m->first + k];
@@ -769,18 +973,19 @@ static double geom_step(const OGeom *g, const int *path, int depth, const double
   return best;
 }
 
-/* compute_step with a proposed physics step: the physics step wins only if strictly shorter. */
+/* compute_step with a proposed physics step: the physics step wins only if strictly shorter.
+ * out_safety may be NULL (no safety: the timing mode's grids may then serve the step). */
 int o_compute_step(int gi, int depth, const int *path, const double *p, const double *v, double proposed,
                    double *out_step, int *out_limiter, double *out_safety) {
   const OGeom *g = G[gi];
   if (depth <= 0) return -1;
   int lim;
-  double saf;
-  double s = geom_step(g, path, depth, p, v, &lim, &saf, NULL);
+  double saf = 0.0;
+  double s = geom_step(g, path, depth, p, v, &lim, out_safety ? &saf : NULL, NULL);
   if (proposed < s) { s = proposed; lim = LIM_PHYS; }
   *out_step = s;
   *out_limiter = lim;
-  *out_safety = saf;
+  if (out_safety) *out_safety = saf;
   return 0;
 }
 

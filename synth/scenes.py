@@ -531,3 +531,20 @@ def query_points(scene: str, n: int, seed: int):
     v = rng.standard_normal((3, n))
     v /= np.sqrt((v * v).sum(axis=0))[None, :]
     return np.ascontiguousarray(p), np.ascontiguousarray(v)
+
+
+def reversed_stack_scene(n_plates: int = 24, pitch: float = 40.0) -> Scene:
+    """A 200 x 200 x 1000 mm vacuum box holding n_plates aluminium-like plates (80 x 80 x 5 mm) stacked along z,
+    placed (hence numbered) from the top down, without voxels: one candidate list in id order, which puts the
+    plates farthest along an upward ray first -- the order a learned proposal can improve on."""
+    mats, mi = _std_materials()
+    solids = [Solid(BOX, (100.0, 100.0, 500.0)), Solid(BOX, (40.0, 40.0, 2.5))]
+    places = [Placement(-1, 0, mi["vacuum"], (0.0, 0.0, 0.0))]
+    for k in range(n_plates):
+        places.append(Placement(0, 1, mi["al"], (0.0, 0.0, 450.0 - pitch * k)))
+    return Scene("reversed_stack", mats, solids, places, VoxelSpec(mode="none"))
+
+
+def reversed_stack_source() -> Source:
+    return Source(pos=(0.0, 0.0, -495.0), spot_sigma=15.0, isotropic=False, direction=(0.0, 0.0, 1.0),
+                  e_kind="loguniform", e0=0.1, e1=3.0)

@@ -31,13 +31,12 @@ def test_clock_summary_without_samples():
 def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
     sha = bench.cuda_sources_sha256()
     monkeypatch.setitem(bench.NCU_TRAFFIC, "sources_sha256", sha)
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "bytes_per_launch", 1234)
-    assert bench.measured_traffic() == 1234
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "bytes_per_launch", {"barrel/fp64": 1234})
+    assert bench.measured_traffic("barrel", "fp64") == 1234
+    assert bench.measured_traffic("barrel", "fp32_recheck") is None
+    assert bench.measured_traffic("calorimeter", "fp64") is None
     monkeypatch.setitem(bench.NCU_TRAFFIC, "sources_sha256", "0" * 64)
-    assert bench.measured_traffic() is None
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "sources_sha256", sha)
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "bytes_per_launch", None)
-    assert bench.measured_traffic() is None
+    assert bench.measured_traffic("barrel", "fp64") is None
 
 
 def test_algorithmic_flops_weights_each_counted_event():

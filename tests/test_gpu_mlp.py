@@ -123,9 +123,10 @@ def test_learned_transport_identical(env, name):
 
 
 def test_trained_proposal_saves_exact_evaluations(env):
-    """What the trained network gains, at identical histories: the plain navigator evaluates every
-    listed candidate in FP64; the learned mode evaluates the proposal first and prunes the rest by
-    the rigorous FP32 bounds.  Against the FP32 bounds alone it must never cost more evaluations."""
+    """What the trained network gains, at identical histories, on random worlds (voxel lists in id order,
+    the first-hit daughter already first in most nodes): the plain navigator evaluates every listed
+    candidate in FP64; the learned mode evaluates the proposal first and prunes the rest by the rigorous
+    FP32 bounds, as many evaluations as the FP32 bounds alone or fewer."""
     g4, torch, ctx = env
     sc = mixed_scene(seed=13, n=1500, half=400.0)
     gid = g4.build_scene(ctx, sc)
@@ -134,7 +135,18 @@ def test_trained_proposal_saves_exact_evaluations(env):
                                         sc.n_volumes + 2)
     g4.g4n_mlp_load(ctx, mlp_init(14))
     g4.g4n_mlp_train(ctx, feat, label, ncand, epochs=6, batch=2048, lr=2e-3, seed=4)
-    n, seed = 200000, 99
+    res = _evaluations(env, gid, sc, src, 200000, 99)
+    plain_evals = sum(res[0][1][k] for k in ("cand_box", "cand_tube", "cand_orb"))
+    fp32_evals = res[1][1]["rechecks"]
+    learned_evals = res[2][1]["rechecks"]
+    print(f"FP64 candidate evaluations: plain {plain_evals}, fp32 bounds {fp32_evals}, learned {learned_evals}, "
+          f"proposals {res[2][1]['proposals']}, pruned {res[2][1]['pruned']}")
+    assert learned_evals <= fp32_evals
+    assert learned_evals < 0.25 * plain_evals
+
+
+def _evaluations(env, gid, sc, src, n, seed):
+    g4, torch, ctx = env
     res = {}
     for mode in (0, 1, 2):
         edep = torch.zeros((100, sc.n_volumes + 2), dtype=torch.float64, device="cuda")
@@ -144,10 +156,65 @@ def test_trained_proposal_saves_exact_evaluations(env):
         g4.g4n_sync(ctx)
         res[mode] = (h.cpu().numpy(), g4.counters_dict(cnt))
     assert np.array_equal(res[0][0], res[2][0]) and np.array_equal(res[1][0], res[2][0])
-    plain_evals = sum(res[0][1][k] for k in ("cand_box", "cand_tube", "cand_orb"))
+    return res
+
+
+def test_trained_proposal_gains_where_list_order_misleads(env):
+    """The gain of the trained network over the method without it (the FP32-bounded navigator), at
+    identical histories and against the oracle: in a stack of plates numbered from the far end, the
+    candidate list puts the plates an upward ray reaches last first, so the bounds alone evaluate every
+    plate ahead of the ray in FP64, farthest first; the trained proposal names the next plate, whose
+    exact distance then prunes the rest."""
+    g4, torch, ctx = env
+    sc = synth.scenes.reversed_stack_scene()
+    src = synth.scenes.reversed_stack_source()
+    gid = g4.build_scene(ctx, sc)
+    feat, label, ncand = g4.g4n_mlp_log(ctx, _items(g4, gid, 100000, src, tid0=20_000_000), 7, 1_000_000,
+                                        sc.n_volumes + 2)
+    assert feat.shape[0] > 100000
+    g4.g4n_mlp_load(ctx, mlp_init(15))
+    losses = g4.g4n_mlp_train(ctx, feat, label, ncand, epochs=4, batch=2048, lr=2e-3, seed=6)
+    n, seed = 50000, 77
+    res = _evaluations(env, gid, sc, src, n, seed)
+    r = oracle.Geometry(sc).transport(src, seed, n)
+    assert np.array_equal(res[2][0].view(np.uint64), r["hashes"])
     fp32_evals = res[1][1]["rechecks"]
     learned_evals = res[2][1]["rechecks"]
-    print(f"FP64 candidate evaluations: plain {plain_evals}, fp32 bounds {fp32_evals}, learned {learned_evals}, "
-          f"proposals {res[2][1]['proposals']}, pruned {res[2][1]['pruned']}")
-    assert learned_evals <= fp32_evals
-    assert learned_evals < 0.25 * plain_evals
+    print(f"losses {losses.tolist()}; FP64 candidate evaluations: fp32 bounds {fp32_evals}, learned {learned_evals}, "
+          f"proposals {res[2][1]['proposals']}, pruned {res[2][1]['pruned']}, steps {res[2][1]['steps']}")
+    assert learned_evals < 0.5 * fp32_evals
+
+
+def test_trained_learned_barrel_full_size_sampled(env):
+    """The learned mode with a trained network on the barrel at full size (10^7 tracks): identical
+    histories to the plain FP64 navigator, and 300 sampled histories replayed one by one by the oracle."""
+    g4, torch, ctx = env
+    sc = synth.scenes.barrel_scene()
+    src = synth.scenes.barrel_source()
+    gid = g4.build_scene(ctx, sc)
+    feat, label, ncand = g4.g4n_mlp_log(ctx, _items(g4, gid, 500000, src, tid0=50_000_000), 3, 2_000_000,
+                                        sc.n_volumes + 2)
+    g4.g4n_mlp_load(ctx, mlp_init(41))
+    losses = g4.g4n_mlp_train(ctx, feat, label, ncand, epochs=2, batch=4096, lr=2e-3, seed=5)
+    assert losses[-1] < losses[0]
+    del feat, label, ncand
+    n, seed = 10_000_000, synth.scenes.CONFIG_SEEDS[4][1]
+    hashes = {}
+    for mode in (0, 2):
+        edep = torch.zeros((100, sc.n_volumes + 2), dtype=torch.float64, device="cuda")
+        cnt = torch.zeros(32, dtype=torch.int64, device="cuda")
+        h = torch.zeros(n, dtype=torch.int64, device="cuda")
+        g4.g4n_transport_batch(ctx, _items(g4, gid, n, src), seed, edep, cnt, h, mode=mode, diagnostics=(mode == 2))
+        g4.g4n_sync(ctx)
+        hashes[mode] = h.cpu().numpy().view(np.uint64)
+        c = g4.counters_dict(cnt)
+        assert c["tracks"] == n and c["steps"] == c["geom_steps"] + c["phys_steps"]
+        if mode == 2:
+            assert c["proposals"] > 0
+        del edep, cnt, h
+    bad = np.nonzero(hashes[0] != hashes[2])[0]
+    assert bad.size == 0, f"{bad.size} histories differ between the plain and the learned mode"
+    og = oracle.Geometry(sc)
+    for i in np.unique(np.random.default_rng(8).integers(0, n, 300)):
+        r = og.transport(src, seed, 1, tid0=int(i), threads=1)
+        assert hashes[2][i] == r["hashes"][0], i

@@ -48,6 +48,7 @@ SCENES = {
 BOX_HALF = {"barrel": (1600.0, 1600.0, 1600.0), "nested_barrel": (1600.0, 1600.0, 1600.0), "calorimeter": (600.0, 600.0, 400.0), "nested_core": (12.0, 12.0, 12.0),
             "segments": (360.0, 360.0, 90.0)}
 AIM = {"segments": 0.8, "mixed_smart": 0.3, "mixed_fixed": 0.3, "mixed_none": 0.3, "cones": 0.6}
+EXACT_SAFETY = ("tiny", "calorimeter", "spheres")   # boxes aligned with their mother, orbs
 
 
 def _build(env, name):
@@ -208,8 +209,13 @@ def test_compute_step_parity(env, name, mode):
     assert np.all(np.abs(s - s_ref) <= STEP_TOL), np.max(np.abs(s - s_ref))
     # isotropic safety: non-negative, never beyond the step, and the ball it defines stays in the volume
     assert np.all(saf >= 0.0)
-    s_geo, _, _ = og.compute_step_many(p, v, d_ref, path_ref, None)
+    s_geo, _, s_ref_saf = og.compute_step_many(p, v, d_ref, path_ref, None)
     assert np.all(saf <= s_geo + STEP_TOL)
+    if name in EXACT_SAFETY:
+        # every solid here is an orb or a box aligned with its mother, whose brute-force safety the oracle
+        # computes from all daughters: the device's (from the node's candidates and slab faces) is no larger
+        bad = np.nonzero(saf > s_ref_saf + STEP_TOL)[0]
+        assert bad.size == 0, (bad.size, p[bad[0]], saf[bad[0]], s_ref_saf[bad[0]])
     idx = np.nonzero(saf > 1e-6)[0][:300]
     dirs = rng.normal(size=(16, 3))
     dirs /= np.linalg.norm(dirs, axis=1)[:, None]
@@ -467,14 +473,14 @@ def test_logical_volume_scene_parity(env, mode):
     assert g4.counters_dict(cnt)["geom_steps"] > 5 * n   # the tracks cross many cells
 
 
-def _full_size_sampled(env, entries_fn, seed, n_sample=300):
-    """Both modes over a full-size launch: identical histories across modes, and a random sample
-    of them replayed one by one by the oracle."""
+def _full_size_sampled(env, entries_fn, seed, n_sample=300, modes=(0, 1, 2)):
+    """Every mode over a full-size launch: identical histories across modes, and a random sample of
+    each mode's histories replayed one by one by the oracle."""
     g4, torch, ctx = env
     entries, stride, total, geoms = entries_fn(g4, ctx)
     items = g4.make_items(entries)
     hashes = {}
-    for mode in (0, 1):
+    for mode in modes:
         edep = torch.zeros((100, stride), dtype=torch.float64, device="cuda")
         cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
         h = torch.zeros(total, dtype=torch.int64, device="cuda")
@@ -483,15 +489,17 @@ def _full_size_sampled(env, entries_fn, seed, n_sample=300):
         hashes[mode] = h.cpu().numpy().view(np.uint64)
         c = g4.counters_dict(cnt)
         assert c["tracks"] == total and c["steps"] == c["geom_steps"] + c["phys_steps"]
-    bad = np.nonzero(hashes[0] != hashes[1])[0]
-    assert bad.size == 0, f"{bad.size} histories differ between modes, first global index {bad[:5]}"
+    for mode in modes[1:]:
+        bad = np.nonzero(hashes[modes[0]] != hashes[mode])[0]
+        assert bad.size == 0, f"{bad.size} histories differ between modes {modes[0]} and {mode}, first {bad[:5]}"
     rng = np.random.default_rng(seed)
     starts = np.cumsum([0] + [e[1] for e in entries])
     for gidx in np.unique(rng.integers(0, total, n_sample)):
         k = int(np.searchsorted(starts, gidx, side="right") - 1)
         gid, nt, tid0, src, off = entries[k]
         r = geoms[k].transport(src, seed, 1, tid0=int(tid0 + gidx - starts[k]), threads=1)
-        assert hashes[0][gidx] == r["hashes"][0], (gidx, k)
+        for mode in modes:
+            assert hashes[mode][gidx] == r["hashes"][0], (mode, gidx, k)
 
 
 def test_batched_full_size_sampled(env):
