@@ -40,13 +40,16 @@ WORKLOAD = ("sampling calorimeter: 50 alternating 5 mm lead-like / 10 mm scintil
             "gamma energy U(0.1, 10) MeV along +z, Gaussian spot sigma 10 mm; Compton (Kahn) + photoabsorption, "
             "10 keV cutoff; per-cell energy deposit in 100 batches")
 
-# Algorithmic FP64 work per counted event (flops: add/sub/mul/compare/min/max = 1, fma = 2, div/sqrt = 1).
-# An Inside test of a world-aligned box answered by exact coordinate keys (key_inside) counts as the FP64
-# box test whose answer it gives, and a relocation answered by a face record (face_reloc) as the two Inside
-# tests (mother, entered volume) the method needs at least: the work the method defines, not the
-# instructions the kernel executes.
+# Algorithmic FP64 work per counted event (flops: add/sub/mul/compare/min/max = 1, fma = 2, div/sqrt = 1), from the
+# formulas of each test.  An Inside test of a world-aligned box answered by exact coordinate keys (key_inside) counts
+# as the FP64 box test whose answer it gives, and a relocation answered by a face record (face_reloc) as the two
+# Inside tests (mother, entered volume) the method needs at least: the work the method defines, not the instructions
+# the kernel executes.  DistanceToOut and Inside of tubes and cones (the *_curved counts, also included in dist_out
+# and inside) add their surplus over the box's: a tube segment's exit takes ~163 (z plane ~30, the two cylinders'
+# quadratics with their range tests ~69 with the shared a, b, r^2, the two phi planes ~64), its Inside ~40.
 FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube": 90, "cand_cone": 100, "inside": 24,
-         "key_inside": 24, "face_reloc": 48, "vox_nodes": 14, "phys_steps": 60}
+         "key_inside": 24, "face_reloc": 48, "vox_nodes": 14, "phys_steps": 60, "dist_out_curved": 151,
+         "inside_curved": 16}
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
 
 
@@ -152,6 +155,9 @@ WORKLOADS = {
               "voxels; 10^7 gamma log-uniform 0.02-20 MeV isotropic from points on the axis",
     "barrel_learned": "barrel scene with the learned candidate proposal (MLP trained on steps logged by the plain "
                       "navigator); 10^7 gamma",
+    "stack": "24 aluminium-like plates (80 x 80 x 5 mm, pitch 40 mm) in a 200 x 200 x 1000 mm vacuum box, numbered from "
+             "the far end, no voxels; 10^6 gamma 0.1-3 MeV log-uniform along +z from below, 15 mm spot; learned proposal "
+             "trained on steps logged by the plain navigator",
     "barrel_nested": "barrel with deep nesting: 30 full tubes each inside the previous (the shells' annuli tiled by "
                      "64 phi segments inside each), 2000 lead-like orbs in the segments, hierarchy depth 32, smart "
                      "voxels; 10^7 gamma log-uniform 0.02-20 MeV isotropic from points on the axis",
@@ -369,6 +375,21 @@ def setup_workload(g4, ctx, args, rank):
         gid = g4.build_scene(ctx, sc)
         n = args.tracks
         return g4.make_items([(gid, n, rank * n, src, 0)]), sc.n_volumes + 2, seed, n, WORKLOAD, ["fp64", "fp32_recheck"]
+    if w == "stack":
+        # where list order misleads: the learned proposal against the FP32 bounds alone
+        from synth.mlp_init import mlp_init
+        sc, src = synth.scenes.reversed_stack_scene(), synth.scenes.reversed_stack_source()
+        gid = g4.build_scene(ctx, sc)
+        n = args.tracks
+        log_items = g4.make_items([(gid, 100_000, 50_000_000, src, 0)])
+        seed = 0x7A0C0020
+        feat, label, ncand = g4.g4n_mlp_log(ctx, log_items, seed + 7, 2_000_000, sc.n_volumes + 2)
+        g4.g4n_mlp_load(ctx, mlp_init(15))
+        args.train_losses = g4.g4n_mlp_train(ctx, feat, label, ncand, epochs=4, batch=2048, lr=2e-3, seed=6).tolist()
+        args.train_samples = int(feat.shape[0])
+        del feat, label, ncand
+        return (g4.make_items([(gid, n, rank * n, src, 0)]), sc.n_volumes + 2, seed, n, WORKLOADS["stack"],
+                ["fp64", "fp32_recheck", "learned"])
     if w == "tiny":
         sc = synth.scenes.tiny_scene()
         gid = g4.build_scene(ctx, sc)
@@ -540,8 +561,9 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
         "counters": {k: cdiag[k] for k in ("steps", "geom_steps", "phys_steps", "safety_skips", "cand_box",
-                                           "cand_tube", "cand_orb", "inside", "key_inside", "face_reloc", "vox_nodes",
-                                           "dist_out", "rechecks", "proposals", "pruned")},
+                                           "cand_tube", "cand_orb", "inside", "inside_curved", "key_inside",
+                                           "face_reloc", "vox_nodes", "dist_out", "dist_out_curved", "rechecks",
+                                           "proposals", "pruned")},
     }
     if getattr(args, "train_losses", None):
         line["learned"] = {"train_samples": args.train_samples, "epoch_losses": args.train_losses}
@@ -554,6 +576,9 @@ def run_gpu(args):
         elif args.workload.startswith("barrel"):
             sc = synth.scenes.nested_barrel_scene() if args.workload == "barrel_nested" else synth.scenes.barrel_scene()
             line["cpu_baseline"] = cpu_baseline(sc, synth.scenes.barrel_source(), seed)
+        elif args.workload == "stack":
+            line["cpu_baseline"] = cpu_baseline(synth.scenes.reversed_stack_scene(),
+                                                synth.scenes.reversed_stack_source(), seed)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -879,7 +904,7 @@ def main():
     ap.add_argument("--mode", default="auto", choices=["auto", "fp64", "fp32_recheck"])
     ap.add_argument("--voxel", default="smart")
     ap.add_argument("--workload", default="barrel_learned",
-                    choices=["calorimeter", "tiny", "batched", "barrel", "barrel_learned", "barrel_nested",
+                    choices=["calorimeter", "tiny", "batched", "barrel", "barrel_learned", "barrel_nested", "stack",
                              "spheres_regular", "spheres_random", "locate", "compute_step"])
     ap.add_argument("--scene", default="calorimeter", choices=["calorimeter", "barrel"],
                     help="locate / compute_step workloads: the scene queried")

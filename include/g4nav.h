@@ -74,6 +74,8 @@ enum {
   G4N_C_CUTOFF, G4N_C_PUSHES, G4N_C_STEP_LIMIT,
   G4N_C_WALK_YIELDS = 10,    /* boundary searches that used their node budget and went on in a later round */
   G4N_C_CAND_CONE = 11,      /* DistanceToIn evaluations of cones */
+  G4N_C_DIST_OUT_CURVED = 12, /* of G4N_C_DIST_OUT: those of tubes and cones */
+  G4N_C_INSIDE_CURVED = 13,  /* of G4N_C_INSIDE: those of tubes and cones */
   G4N_C_FACE_RELOC = 14,     /* relocations answered by a box face's precomputed record */
   G4N_C_KEY_INSIDE = 15,     /* Inside tests of world-aligned boxes answered by exact coordinate thresholds */
   G4N_C_SAFETY_SKIPS = 16,   /* steps that skipped the boundary search because safety exceeded the physics step */
@@ -281,7 +283,7 @@ typedef struct {
  * searches take their next steps meanwhile; default 16, values >= 65536 never yield and select a
  * kernel without that code), regroup_period (0 = off: every that many rounds each thread block
  * sorts its tracks by phase and solid kind of the leaf and deals them out again, so that each
- * warp runs one kind of work; FP64 and FP32_RECHECK modes without diagnostics).  flags:
+ * warp runs one kind of work; every mode without diagnostics).  flags:
  * G4N_FLAG_DIAGNOSTICS also fills the diagnostic counters (G4N_C_WALK_YIELDS and above; the
  * counters below it are always filled).  Results
  * never depend on the launch shape. */
@@ -337,7 +339,9 @@ int g4n_graph_destroy(g4n_graph *graph);
 
 /* A small network proposes which candidate daughter of the current voxel node the ray enters
  * first; in G4N_MODE_LEARNED that candidate is evaluated exactly before the others, and its
- * distance prunes every candidate whose rigorous FP32 lower bound exceeds it.  The exact
+ * distance prunes every candidate whose rigorous FP32 lower bound exceeds it.  The network is
+ * asked only where two or more of the node's candidates pass the FP32 bounds (elsewhere the
+ * bounds alone leave at most one exact evaluation).  The exact
  * navigator stays the judge: results are identical in every mode.  (No counterpart in the
  * paper; part of the method's learned-proposal extension.)
  *

@@ -30,7 +30,8 @@ G4N_NOALLOC_MAX_ITEMS = 256
 G4N_MLP_N_PARAMS = 6880
 G4N_NOALLOC_STATUS_SLOT = G4N_N_COUNTERS - 1
 COUNTER_NAMES = {0: "tracks", 1: "steps", 2: "geom_steps", 3: "phys_steps", 4: "photo", 5: "compton", 6: "escaped",
-                 7: "cutoff", 8: "pushes", 9: "step_limit", 10: "walk_yields", 11: "cand_cone", 14: "face_reloc", 15: "key_inside", 16: "safety_skips", 17: "cand_box", 18: "cand_tube",
+                 7: "cutoff", 8: "pushes", 9: "step_limit", 10: "walk_yields", 11: "cand_cone", 12: "dist_out_curved",
+                 13: "inside_curved", 14: "face_reloc", 15: "key_inside", 16: "safety_skips", 17: "cand_box", 18: "cand_tube",
                  19: "cand_orb", 20: "dist_out", 21: "inside", 22: "vox_nodes", 23: "rechecks", 24: "proposals",
                  25: "pruned", 26: "cyc_refill", 27: "cyc_interact", 28: "cyc_step", 29: "step_lanes",
                  30: "step_phases"}

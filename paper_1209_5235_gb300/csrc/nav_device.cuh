@@ -58,6 +58,16 @@ __device__ __forceinline__ void diag_kind(Counters &c, int kind) {
   }
 }
 
+// An FP64 DistanceToOut or Inside test of solid `kind`: tubes and cones are also counted apart (their
+// formulas have several times the box's arithmetic).
+template <bool COUNT>
+__device__ __forceinline__ void diag_test(Counters &c, int which, int curved_which, int kind) {
+  if (COUNT) {
+    c.c[which]++;
+    if (kind == kTube || kind == kCone) c.c[curved_which]++;
+  }
+}
+
 // key(x): a double's bits as a signed integer with the negative half reflected, so that
 // x < y <=> key(x) < key(y) for all non-NaN doubles (-0 < +0).
 __device__ __forceinline__ long long dkey(double x) {
@@ -284,57 +294,60 @@ __device__ __noinline__ bool tube_inside(const double *q, int flags, const V3 &p
   return true;
 }
 
+// The crossings tube_cross takes the first of, one helper per surface: each returns its crossing
+// parameter t when t lies in (tmin, best) and the crossing passes the surface's range tests, else
+// +inf.
+// z plane the ray enters (enter) or leaves (exit) through
+__device__ __forceinline__ double tube_z_cand(const double *q, int flags, const V3 &p, const V3 &v, double half,
+                                              bool enter, double tmin) {
+  if (v.z == 0.0) return kInf;
+  const double sg = ((v.z < 0.0) == enter) ? 1.0 : -1.0;
+  const double t = (sg * q[2] - p.z) / v.z;
+  if (!(t > tmin)) return kInf;
+  const double qx = p.x + t * v.x, qy = p.y + t * v.y;
+  return (tube_r_ok(q, flags, qx, qy, half) && tube_phi_ok(q, flags, qx, qy, half)) ? t : kInf;
+}
+
+// cylinder of radius R (outer: the root that enters / leaves the solid through rmax; inner: through rmin)
+__device__ __forceinline__ double tube_cyl_cand(const double *q, int flags, const V3 &p, const V3 &v, double half,
+                                                bool enter, double tmin, double best, bool outer) {
+  const double a = v.x * v.x + v.y * v.y;
+  if (!(a > 0.0)) return kInf;
+  const double b = p.x * v.x + p.y * v.y;
+  const double r2 = p.x * p.x + p.y * p.y;
+  const double R = outer ? q[1] : q[0];
+  double lo, hi;
+  if (!quad_roots(a, b, r2 - R * R, lo, hi)) return kInf;
+  const double t = (enter == outer) ? lo : hi;
+  if (t > tmin && t < best && fabs(p.z + t * v.z) <= q[2] + half &&
+      tube_phi_ok(q, flags, p.x + t * v.x, p.y + t * v.y, half))
+    return t;
+  return kInf;
+}
+
+// phi half-plane at the start (start = true) or end of the segment
+__device__ __forceinline__ double tube_phi_cand(const double *q, int flags, const V3 &p, const V3 &v, double half,
+                                                bool enter, double tmin, double best, bool start) {
+  // v . outward normal of the plane, the signed distance to its line (positive on the solid's side)
+  const double dn = start ? q[4] * v.x - q[3] * v.y : q[5] * v.y - q[6] * v.x;
+  if (!(dn != 0.0 && ((dn < 0.0) == enter))) return kInf;
+  const double t = (start ? q[3] * p.y - q[4] * p.x : q[6] * p.x - q[5] * p.y) / dn;
+  if (!(t > tmin && t < best)) return kInf;
+  const double qx = p.x + t * v.x, qy = p.y + t * v.y;
+  const double along = start ? q[3] * qx + q[4] * qy : q[5] * qx + q[6] * qy;
+  return (along >= -half && tube_r_ok(q, flags, qx, qy, half) && fabs(p.z + t * v.z) <= q[2] + half) ? t : kInf;
+}
+
 // enter = true: first entering crossing with t > half (DistanceToIn);
 // enter = false: first exiting crossing with t > -half (DistanceToOut, clamped by the caller).
 __device__ __noinline__ double tube_cross(const double *q, int flags, const V3 &p, const V3 &v, double half, bool enter) {
   const double tmin = enter ? half : -half;
-  double best = kInf;
-  if (v.z != 0.0) {
-    // the z plane this ray can enter (enter) or leave (exit) through
-    const double sg = ((v.z < 0.0) == enter) ? 1.0 : -1.0;
-    const double t = (sg * q[2] - p.z) / v.z;
-    if (t > tmin) {
-      const double qx = p.x + t * v.x, qy = p.y + t * v.y;
-      if (tube_r_ok(q, flags, qx, qy, half) && tube_phi_ok(q, flags, qx, qy, half)) best = t;
-    }
-  }
-  const double a = v.x * v.x + v.y * v.y;
-  if (a > 0.0) {
-    const double b = p.x * v.x + p.y * v.y;
-    const double r2 = p.x * p.x + p.y * p.y;
-    double lo, hi;
-    if (quad_roots(a, b, r2 - q[1] * q[1], lo, hi)) {
-      const double t = enter ? lo : hi;
-      if (t > tmin && t < best && fabs(p.z + t * v.z) <= q[2] + half &&
-          tube_phi_ok(q, flags, p.x + t * v.x, p.y + t * v.y, half))
-        best = t;
-    }
-    if ((flags & kHasRmin) && quad_roots(a, b, r2 - q[0] * q[0], lo, hi)) {
-      const double t = enter ? hi : lo;
-      if (t > tmin && t < best && fabs(p.z + t * v.z) <= q[2] + half &&
-          tube_phi_ok(q, flags, p.x + t * v.x, p.y + t * v.y, half))
-        best = t;
-    }
-  }
+  double best = tube_z_cand(q, flags, p, v, half, enter, tmin);
+  best = fmin(best, tube_cyl_cand(q, flags, p, v, half, enter, tmin, best, true));
+  if (flags & kHasRmin) best = fmin(best, tube_cyl_cand(q, flags, p, v, half, enter, tmin, best, false));
   if (flags & kSeg) {
-    const double dn = q[4] * v.x - q[3] * v.y;  // v . outward normal of the start plane
-    if (dn != 0.0 && ((dn < 0.0) == enter)) {
-      const double t = (q[3] * p.y - q[4] * p.x) / dn;
-      if (t > tmin && t < best) {
-        const double qx = p.x + t * v.x, qy = p.y + t * v.y;
-        if (q[3] * qx + q[4] * qy >= -half && tube_r_ok(q, flags, qx, qy, half) && fabs(p.z + t * v.z) <= q[2] + half)
-          best = t;
-      }
-    }
-    const double de = q[5] * v.y - q[6] * v.x;  // end plane
-    if (de != 0.0 && ((de < 0.0) == enter)) {
-      const double t = (q[6] * p.x - q[5] * p.y) / de;
-      if (t > tmin && t < best) {
-        const double qx = p.x + t * v.x, qy = p.y + t * v.y;
-        if (q[5] * qx + q[6] * qy >= -half && tube_r_ok(q, flags, qx, qy, half) && fabs(p.z + t * v.z) <= q[2] + half)
-          best = t;
-      }
-    }
+    best = fmin(best, tube_phi_cand(q, flags, p, v, half, enter, tmin, best, true));
+    best = fmin(best, tube_phi_cand(q, flags, p, v, half, enter, tmin, best, false));
   }
   return best;
 }
@@ -965,7 +978,7 @@ __device__ __forceinline__ int descend_body(const DGeom &G, bool active, int m, 
         const DVol &D = G.vol[d];
         V3 dp, dv;
         to_local(D, p, v, dp, dv);
-        diag<COUNT>(cnt, G4N_C_INSIDE);
+        diag_test<COUNT>(cnt, G4N_C_INSIDE, G4N_C_INSIDE_CURVED, D.kind);
         if (vol_inside(D, dp, dv, G.half)) {
           found = d;
           fp = dp;
@@ -1020,7 +1033,7 @@ __device__ __forceinline__ int locate_world_warp(const DGeom &G, bool active, co
     } else {
       world_to_local(G.wxf[0], G.vol[0].flags & kWorldAligned, x, u, p, v);
       have_p = true;
-      diag<COUNT>(cnt, G4N_C_INSIDE);
+      diag_test<COUNT>(cnt, G4N_C_INSIDE, G4N_C_INSIDE_CURVED, G.vol[0].kind);
       in = vol_inside(G.vol[0], p, v, G.half);
     }
   }
@@ -1061,7 +1074,7 @@ __device__ __forceinline__ int relocate_warp(const DGeom &G, bool active, int le
         have_p = true;
         if (MODE != kFP64) ok = certainly_inside32(L, make_ray32(p, v), (float)(4.0 * G.half) + 1e-30f);
         if (!ok) {
-          diag<COUNT>(cnt, G4N_C_INSIDE);
+          diag_test<COUNT>(cnt, G4N_C_INSIDE, G4N_C_INSIDE_CURVED, L.kind);
           ok = vol_inside(L, p, v, G.half);
         }
       }
@@ -1428,7 +1441,7 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       saf_f = resume ? (float)from.safety : saf32;
       stop = fmin(limit, (double)out_hi);
     } else {
-      diag<COUNT>(cnt, G4N_C_DIST_OUT);
+      diag_test<COUNT>(cnt, G4N_C_DIST_OUT, G4N_C_DIST_OUT_CURVED, V.kind);
       tout = vol_dist_out(V, p, v, iv, half, &oface);
       R.safety = resume ? from.safety : (want_safety ? vol_safety_out(V, p) : 0.0);
       stop = fmin(limit, tout);
@@ -1447,8 +1460,23 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       walking = true;
       diag<COUNT>(cnt, G4N_C_VOX_NODES);
       if (!resume && (MODE == kLearned || mc.log) && L.count >= 2 && L.count <= mlp::kOut) {
-        node_features(G, V, ch, p, v, mc.loge, L.count, feat);
-        have_feat = true;
+        // learned mode: a proposal can only save work when two or more of the node's candidates pass
+        // the FP32 bounds (with one or none the bounds alone leave a single FP64 evaluation at most)
+        int open = 2;
+        if (MODE == kLearned) {
+          open = 0;
+#pragma unroll 1
+          for (int k = 0; k < L.count && open < 2; ++k) {
+            const int c = __ldg(&G.cand[L.offset + k]);
+            const DBox32 B = G.box[c];
+            const float iso = iso_lb32(G.v32[c], r.plo[0], r.plo[1], r.plo[2]) - (float)(2.0 * G.half);
+            if (fmaxf(box_entry_lb(B.lo, B.hi, r, nullptr), iso) <= bound_f) ++open;
+          }
+        }
+        if (open >= 2) {
+          node_features(G, V, ch, p, v, mc.loge, L.count, feat);
+          have_feat = true;
+        }
       }
     }
   }
@@ -1587,7 +1615,7 @@ __device__ __forceinline__ StepResult geom_step_warp(const DGeom &G, bool active
       R.physics = true;
       return R;
     }
-    diag<COUNT>(cnt, G4N_C_DIST_OUT);
+    diag_test<COUNT>(cnt, G4N_C_DIST_OUT, G4N_C_DIST_OUT_CURVED, G.vol[leaf].kind);
     tout = vol_dist_out(G.vol[leaf], p, v, iv, half, &oface);
   }
   // a daughter wins a tie with the mother; `best` already holds the lowest id among tied daughters

@@ -175,6 +175,11 @@ __global__ void __launch_bounds__(128) k_compute_step(const DGeom *__restrict__ 
 
 // ---------------------------------------------------------------- transport
 
+// Shared memory of the learned mode's weights and per-warp scratch (16-byte multiple).
+__host__ __device__ __forceinline__ size_t mlp_block_bytes(unsigned block) {
+  return (sizeof(mlp::SmemWeights) + (size_t)(block / 32) * sizeof(mlp::SmemWarp) + 15) & ~size_t(15);
+}
+
 enum Phase : int { kEmpty = 0, kStep = 1, kInteract = 2, kWalk = 3 };  // kWalk: a yielded boundary search
 
 // Voxel nodes a boundary search walks per round before it yields (walk_budget = 0); budgets
@@ -793,7 +798,9 @@ __global__ void __launch_bounds__(128, (MODE == kFP32 && YIELD) ? 3 : 4) k_trans
       if (round > 0 && round % P.regroup == 0) {
         if (!__syncthreads_or(phase != kEmpty || !drained)) break;
         extern __shared__ __align__(16) unsigned char smem_rg[];
-        regroup_block(P, t, phase, wch, reinterpret_cast<uint32_t *>(smem_rg));
+        // the learned mode keeps its weights and per-warp scratch first; the regroup buffer follows them
+        const size_t off = MODE == kLearned ? mlp_block_bytes(blockDim.x) : 0;
+        regroup_block(P, t, phase, wch, reinterpret_cast<uint32_t *>(smem_rg + off));
       }
       ++round;
     }
@@ -1034,7 +1041,8 @@ TransportKernel transport_kernel(int mode, bool count, bool yield, bool regroup)
   if (mode == G4N_MODE_FP64) return count ? k_transport<kFP64, true, true, false> : plain_kernel<kFP64>(yield, regroup);
   if (mode == G4N_MODE_FP32_RECHECK)
     return count ? k_transport<kFP32, true, true, false> : plain_kernel<kFP32>(yield, regroup);
-  return count ? k_transport<kLearned, true, false, false> : k_transport<kLearned, false, false, false>;
+  if (count) return k_transport<kLearned, true, false, false>;
+  return regroup ? k_transport<kLearned, false, false, true> : k_transport<kLearned, false, false, false>;
 }
 
 // Dynamic shared memory of a launch: the MLP weights and one scratch tile per warp (learned mode).
@@ -1042,13 +1050,10 @@ TransportKernel transport_kernel(int mode, bool count, bool yield, bool regroup)
 // regroup buffer (regrouping kernels).
 size_t transport_smem_bytes(int mode, int block, int regroup);
 
-size_t mlp_smem_bytes(int mode, int block) {
-  return mode == G4N_MODE_LEARNED ? sizeof(mlp::SmemWeights) + (size_t)(block / 32) * sizeof(mlp::SmemWarp) : 0;
-}
+size_t mlp_smem_bytes(int mode, int block) { return mode == G4N_MODE_LEARNED ? mlp_block_bytes(block) : 0; }
 
 size_t transport_smem_bytes(int mode, int block, int regroup) {
-  if (mode == G4N_MODE_LEARNED) return mlp_smem_bytes(mode, block);
-  return regroup > 0 ? (size_t)kTrackWords * block * sizeof(uint32_t) : 0;
+  return mlp_smem_bytes(mode, block) + (regroup > 0 ? (size_t)kTrackWords * block * sizeof(uint32_t) : 0);
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -1093,7 +1098,7 @@ int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refi
                     int *regroup) {
   *block = b->block_size > 0 ? b->block_size : 128;
   if (b->regroup_period < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: regroup_period must be >= 0");
-  *regroup = b->mode == G4N_MODE_LEARNED ? 0 : std::min(b->regroup_period, 1 << 20);
+  *regroup = std::min(b->regroup_period, 1 << 20);
   if (b->walk_budget < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: walk_budget must be >= 0");
   *budget = b->walk_budget > 0 ? std::min(b->walk_budget, 1 << 20) : kDefaultWalkBudget;
   if (*block % 32 || *block > 128) return g4n_fail(ctx, G4N_ERR_ARG, "transport: block_size must be a multiple of 32, <= 128");
