@@ -58,7 +58,10 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flop
 # written back during the launch) and of a launch of the same kernel after the same flush with no track to carry
 # (the flush's own write-back): summaries in profiles/.  Reported only while the CUDA sources hash to the value they
 # had when the captures were taken (else the kernel has changed since).
-NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": {}}
+NCU_TRAFFIC = {"sources_sha256": "5098c7b7adf1d0acb68beb75ebaf3653787306807c554b7e89f887a2f75d37a3",
+               # barrel: the capture ran the configs[3] seed; the configs[4] line runs the same kernel on the same scene
+               "bytes_per_launch": {"barrel/fp64": 8324352 + 993821184, "barrel_learned/fp64": 8324352 + 993821184,
+                                    "calorimeter/fp64": 2443776 + 41151232}}
 
 
 def cuda_sources_sha256() -> str:
@@ -288,7 +291,9 @@ def run_reference(args):
     og = oracle.Geometry(sc)
     og.use_grids(True)
     threads = os.cpu_count() or 1
-    n = max(64, args.ref_tracks)
+    n = args.ref_tracks or {"barrel": 1_000_000, "barrel_learned": 1_000_000, "barrel_nested": 500_000,
+                            "calorimeter": 200_000, "tiny": 20_000}.get(args.workload, 100_000)
+    n = max(64, n)
     times, steps = [], []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -413,9 +418,10 @@ def setup_workload(g4, ctx, args, rank):
     seed = synth.scenes.CONFIG_SEEDS[4 if w == "barrel_learned" else 3][1]
     modes = ["fp64", "fp32_recheck"]
     if w == "barrel_learned":
-        # the proposal network: 10^7 steps logged by the plain navigator, trained by the library's kernels
+        # the proposal network: 10^7 steps logged by the plain navigator (10^7 histories give a little more; the
+        # log keeps the first 10^7), trained by the library's kernels
         from synth.mlp_init import mlp_init
-        log_items = g4.make_items([(gid, 3_000_000, 50_000_000, synth.scenes.barrel_source(), 0)])
+        log_items = g4.make_items([(gid, 10_000_000, 50_000_000, synth.scenes.barrel_source(), 0)])
         feat, label, ncand = g4.g4n_mlp_log(ctx, log_items, seed + 7, 10_000_000, sc.n_volumes + 2)
         g4.g4n_mlp_load(ctx, mlp_init(41))
         args.train_losses = g4.g4n_mlp_train(ctx, feat, label, ncand, epochs=2, batch=4096, lr=2e-3, seed=5).tolist()
@@ -712,17 +718,23 @@ def run_free_path(args):
     if not args.no_cpu_baseline and world == 1:
         import oracle
         og = oracle.Geometry(sc)
+        og.use_grids(True)          # the oracle's timing mode: free paths identical to its brute-force search
         t0 = time.perf_counter()
         _, _, used = og.free_path_many(p, v, E, Y)
         dt_all = time.perf_counter() - t0
-        m1 = 2000
         t0 = time.perf_counter()
-        og.free_path_many(p[:m1], v[:m1], E, Y[:m1], threads=1)
+        og.free_path_many(p, v, E, Y, threads=1)
         dt_1 = time.perf_counter() - t0
+        ob = oracle.Geometry(sc)    # brute force: every step tests all 8000 balls
+        m1 = 20000
+        t0 = time.perf_counter()
+        ob.free_path_many(p[:m1], v[:m1], E, Y[:m1])
+        dt_b = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": n / dt_all, "unit": "rays/s", "cores": int(used), "kind": "oracle",
-                                "single_thread_rays_per_s": m1 / dt_1,
-                                "sample": f"all {n} rays on {used} threads; the first {m1} rays on 1 thread; "
-                                          f"brute-force FP64 oracle (every step tests all 8000 balls)"}
+                                "single_thread_rays_per_s": n / dt_1, "brute_force_rays_per_s": m1 / dt_b,
+                                "sample": f"all {n} rays on {used} threads and on 1 thread, FP64 oracle in its "
+                                          f"uniform-grid timing mode; the first {m1} rays by its brute-force search "
+                                          f"on {used} threads"}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -750,7 +762,7 @@ def run_queries(args):
     b.build()
     ctx = g4.g4n_create(local)
     scene = args.scene
-    sc = synth.scenes.calorimeter_scene() if scene == "calorimeter" else synth.scenes.barrel_scene()
+    sc = calorimeter(args.voxel)[0] if scene == "calorimeter" else synth.scenes.barrel_scene()   # smart voxels
     gid = g4.build_scene(ctx, sc)
     n = args.queries
     p, v = synth.scenes.query_points(scene, n, seed=0x7A0C0010 + rank)
@@ -894,7 +906,8 @@ def main():
     ap.add_argument("--tracks", type=int, default=1_000_000)
     ap.add_argument("--track-scale", type=float, default=1.0,
                     help="batched / barrel workloads: fraction of their track counts (profiling a smaller case)")
-    ap.add_argument("--ref-tracks", type=int, default=4000)
+    ap.add_argument("--ref-tracks", type=int, default=0,
+                    help="reference arm: histories per step (default: about a second of the oracle on 16 cores)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--refill-min", type=int, default=0)
