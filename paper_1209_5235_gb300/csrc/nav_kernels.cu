@@ -466,10 +466,10 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     lazy = MODE == kFP64 && mu_pos && !mc.log;
     if (!lazy) sphys = mu_pos ? t.Y / t.mu : kInf;
     // a zero safety (after every boundary crossing) always needs the boundary search.  Lazy form: the
-    // search is skipped only when Y < safety mu by more than the rounding of the product, so that
+    // search is skipped only when Y - safety mu (one rounding, by the fma) lies below -2^-49 Y, so that
     // fl(Y / mu) < safety holds as well (the comparison the oracle makes)
     need_geo = resume || !nonzero_bits(t.safety) ||
-               (lazy ? !(t.Y < t.safety * t.mu * (1.0 - 0x1p-50)) : !(sphys < t.safety));
+               (lazy ? !(fma(-t.safety, t.mu, t.Y) < -0x1p-49 * t.Y) : !(sphys < t.safety));
     want_saf = !(MODE == kFP64 && L.vox < 0);
     if (!need_geo) {
       diag<COUNT>(cnt, G4N_C_SAFETY_SKIPS);
@@ -506,17 +506,15 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
     if (timeout) flag(P.status, kStTimeout);
     if (need_geo) {
       t.safety = R.safety;
-      // geometry wins iff step <= fl(Y / mu).  Lazy form: the product step mu decides when it lies
-      // outside Y (1 +- 2^-50), a margin that covers the rounding of both forms; a near-tie takes
+      // geometry wins iff step <= fl(Y / mu).  Lazy form: Y - step mu (one rounding, by the fma) decides
+      // when it lies outside +-2^-49 Y, a margin far above the rounding of either form; a near-tie takes
       // the division itself
       bool geo_first;
       if (!lazy) {
         geo_first = R.step <= sphys;
       } else {
-        const double a = R.step * t.mu;
-        if (a < t.Y * (1.0 - 0x1p-50)) geo_first = true;
-        else if (a > t.Y * (1.0 + 0x1p-50)) geo_first = false;
-        else geo_first = R.step <= t.Y / t.mu;
+        const double d = fma(-R.step, t.mu, t.Y), m = 0x1p-49 * t.Y;
+        geo_first = d > m || (!(d < -m) && R.step <= t.Y / t.mu);
       }
       if (!R.physics && geo_first) {
         geo = true;
