@@ -54,14 +54,14 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flop
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_transport launch, per workload and mode, from
-# a single-pass ncu capture of the bench's first timed launch (after the 256 MB L2 flush, whose dirty lines are
-# written back during the launch) and of a launch of the same kernel after the same flush with no track to carry
-# (the flush's own write-back): summaries in profiles/.  Reported only while the CUDA sources hash to the value they
-# had when the captures were taken (else the kernel has changed since).
-NCU_TRAFFIC = {"sources_sha256": "5098c7b7adf1d0acb68beb75ebaf3653787306807c554b7e89f887a2f75d37a3",
-               # barrel: the capture ran the configs[3] seed; the configs[4] line runs the same kernel on the same scene
-               "bytes_per_launch": {"barrel/fp64": 8324352 + 993821184, "barrel_learned/fp64": 8324352 + 993821184,
-                                    "calorimeter/fp64": 2443776 + 41151232}}
+# a single-pass ncu capture of the bench's first timed launch run without the L2 flush before it (--no-flush; the
+# flush changes the figure by < 1 %): summaries in profiles/.  Reported only while the CUDA sources hash to the value
+# they had when the captures were taken (else the kernel has changed since).
+NCU_TRAFFIC = {"sources_sha256": "516237c420ba22056c5c6ad79e7558b5ff06635345fe4eb9d0d6e159e38dba73",
+               # barrel: captured on the plain barrel workload (same scene and 10^7 tracks, another seed); the learned
+               # workload's line times the same FP64 kernel
+               "bytes_per_launch": {"barrel/fp64": 8518400 + 997785600, "barrel_learned/fp64": 8518400 + 997785600,
+                                    "calorimeter/fp64": 2280192 + 40204288}}
 
 
 def cuda_sources_sha256() -> str:
