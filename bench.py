@@ -50,6 +50,9 @@ WORKLOAD = ("sampling calorimeter: 50 alternating 5 mm lead-like / 10 mm scintil
 FLOPS = {"steps": 40, "dist_out": 12, "cand_box": 56, "cand_orb": 40, "cand_tube": 90, "cand_cone": 100, "inside": 24,
          "key_inside": 24, "face_reloc": 48, "vox_nodes": 14, "phys_steps": 60, "dist_out_curved": 151,
          "inside_curved": 16}
+SCHEDULES = {0: "persistent", 1: "staged"}
+# bytes of one track's state in the staged schedule's queues (16 doubles, hash, id, 6 ints)
+STAGED_STATE_BYTES = 168
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
 
 
@@ -76,12 +79,13 @@ def cuda_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(workload: str, mode: str):
-    """The captured DRAM bytes of one launch of (workload, mode), or None (not captured, or sources changed)."""
+def measured_traffic(workload: str, mode: str, schedule: str = "persistent"):
+    """The captured DRAM bytes of one launch of (workload, mode, schedule), or None (not captured, or sources
+    changed)."""
     per = NCU_TRAFFIC["bytes_per_launch"] or {}
     if NCU_TRAFFIC["sources_sha256"] != cuda_sources_sha256():
         return None
-    return per.get(f"{workload}/{mode}")
+    return per.get(f"{workload}/{mode}" + ("/staged" if schedule == "staged" else ""))
 
 
 def algorithmic_flops(c: dict) -> float:
@@ -329,6 +333,7 @@ def time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream,
     torch.cuda.synchronize()
     if barrier:
         barrier()
+    launches0 = g4.g4n_kernel_launches(ctx)
     t_wall = time.perf_counter()
     for k in range(args.steps):
         if not getattr(args, "no_flush", False):
@@ -341,9 +346,10 @@ def time_mode(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream,
     if barrier:
         barrier()
     t_wall = time.perf_counter() - t_wall
+    launches = g4.g4n_kernel_launches(ctx) - launches0
     g4.g4n_sync(ctx, stream)
     ms = [a.elapsed_time(b) for a, b in ev]
-    return ms, g4.counters_dict(cnt), t_wall
+    return ms, g4.counters_dict(cnt), t_wall, launches
 
 
 def time_graph(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream, launch):
@@ -463,7 +469,9 @@ def run_gpu(args):
         for m in mode_names:
             tuned[m] = tune["per_mode"][code[m]]["cfg"]
     manual = dict(block_size=args.block, blocks_per_sm=args.blocks_per_sm, refill_min=args.refill_min,
-                  interact_min=args.interact_min, walk_budget=args.walk_budget, regroup_period=args.regroup)
+                  interact_min=args.interact_min, walk_budget=args.walk_budget, regroup_period=args.regroup,
+                  schedule=g4.G4N_SCHEDULE_STAGED if args.schedule == "staged" else g4.G4N_SCHEDULE_PERSISTENT,
+                  pool_tracks=args.pool, drain_tracks=args.drain)
     launch = {m: tuned.get(m, manual) for m in mode_names}
     # matched results: the same histories, bit for bit, in every mode (one launch with hashes each)
     ref_h = None
@@ -485,8 +493,8 @@ def run_gpu(args):
         dist.barrier()
     with ClockSampler(local) as clk:
         for m in mode_names:
-            ms, c, t_wall = time_mode(g4, torch, ctx, items, seed, code[m], args, edep, cnt, flush, stream, launch[m],
-                                      barrier=dist.barrier if dist else None)
+            ms, c, t_wall, launches = time_mode(g4, torch, ctx, items, seed, code[m], args, edep, cnt, flush, stream,
+                                                launch[m], barrier=dist.barrier if dist else None)
             t_dev = sum(ms) / 1e3
             steps_total, tracks_total = c["steps"], c["tracks"]
             if dist:
@@ -498,7 +506,9 @@ def run_gpu(args):
                 steps_total, tracks_total = int(st[0].item()), int(st[1].item())
             results[m] = {"steps_per_s": steps_total / t_dev, "tracks_per_s": tracks_total / t_dev,
                           "ms_per_step": 1e3 * t_dev / args.steps, "ms_launch_mean": float(np.mean(ms)),
-                          "steps_per_track": steps_total / max(tracks_total, 1), "launch": launch[m]}
+                          "steps_per_track": steps_total / max(tracks_total, 1), "launch": launch[m],
+                          "schedule": SCHEDULES[launch[m].get("schedule", 0)], "gpu_launches": launches,
+                          "interactions": c["photo"] + c["compton"]}
     chosen = max(results, key=lambda k: results[k]["steps_per_s"]) if matched else "fp64"
     mode = code[chosen]
     graph_value = time_graph(g4, torch, ctx, items, seed, mode, args, edep, cnt, flush, stream, launch[chosen])
@@ -541,11 +551,16 @@ def run_gpu(args):
     t_launch = R["ms_launch_mean"] / 1e3
     achieved = flops / t_launch / 1e12
     hbm_bytes = (nb * stride * 8) * 2              # tallies read + written once per launch; tables stay in L2
+    staged = R["schedule"] == "staged"
+    if staged:
+        # the queues: every step and every interaction reads a state and writes one back, every start writes one
+        hbm_bytes += STAGED_STATE_BYTES * (2 * cdiag["steps"] + 2 * (cdiag["photo"] + cdiag["compton"])
+                                           + cdiag["tracks"])
     line = {
         "metric": METRIC, "value": R["steps_per_s"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload, "tracks_per_gpu": n, "mode": chosen,
+        "config": {"workload": workload, "tracks_per_gpu": n, "mode": chosen, "schedule": R["schedule"],
                    "l2": ("not flushed (DRAM-traffic capture run)" if args.no_flush
                           else "flushed between timed steps (256 MB write)"), "launch": launch[chosen],
                    "autotuned": bool(args.autotune), "voxel": args.voxel if args.workload == "calorimeter" else "smart"},
@@ -555,12 +570,13 @@ def run_gpu(args):
         "matched_results": matched,
         "plain_fp64_steps_per_s": results.get("fp64", {}).get("steps_per_s"),
         "graph_replay_steps_per_s": graph_value,
-        "gpu_launches": args.steps,
+        "gpu_launches": R["gpu_launches"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": measured_traffic(args.workload, chosen),
+                     "traffic": measured_traffic(args.workload, chosen, R["schedule"]),
                      "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (recipe nominal 1.25 TFLOP/s)",
-                     "kernel": "k_transport", "flops_per_launch": flops},
+                     "kernel": ("k_staged_step + k_staged_finish + k_staged_drain (one transport batch)" if staged
+                                else "k_transport"), "flops_per_launch": flops},
         "hbm": {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / t_launch / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"),
                 "frac": (hbm_bytes / t_launch / 1e9) / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None},
@@ -922,6 +938,10 @@ def main():
     ap.add_argument("--scene", default="calorimeter", choices=["calorimeter", "barrel"],
                     help="locate / compute_step workloads: the scene queried")
     ap.add_argument("--queries", type=int, default=10_000_000)
+    ap.add_argument("--schedule", default="staged", choices=["staged", "persistent"],
+                    help="schedule of the transport when --autotune 0 (the tuner chooses it otherwise)")
+    ap.add_argument("--pool", type=int, default=0, help="staged schedule: tracks in flight (0 = default)")
+    ap.add_argument("--drain", type=int, default=0, help="staged schedule: drain point (0 = default, -1 = never)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tune-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -107,6 +107,11 @@ const char *g4n_last_error(const g4n_ctx *ctx);
 int g4n_set_tolerance_scale(g4n_ctx *ctx, double scale);
 /* Wait for `stream` and report any device-side error raised since the last sync. */
 int g4n_sync(g4n_ctx *ctx, g4n_stream stream);
+/* Kernels the context has launched so far on the device: the navigation queries, the free path,
+ * every kernel of a transport batch (one per persistent launch; two per iteration and the drain
+ * in the staged schedule) and one per graph replay.  A monotonic count, for measuring launch
+ * rates; -1 for a null context. */
+int64_t g4n_kernel_launches(const g4n_ctx *ctx);
 /* Caps of the context's device loops (failure detection; the paper has no counterpart).  Every
  * loop of the kernels that is not bounded by its input is capped: the voxel walk of one boundary
  * search (default 65536 nodes) and each rejection sampler -- Kahn's method, the disc azimuth, the
@@ -271,7 +276,7 @@ typedef struct {
 } g4n_work_item;
 
 /* A transport launch.  items: HOST array of n_items work items, processed from one device queue
- * by a persistent kernel.  Physics: Algorithm 1 free paths with Y = -log W (stream 1 of the
+ * (by the schedule below).  Physics: Algorithm 1 free paths with Y = -log W (stream 1 of the
  * track's generator), interactions Compton (Kahn's method) or photoabsorption chosen by
  * U mu_tot < mu_photo, energy below `cutoff` after a Compton scatter deposited on the spot.
  * Tally rows: track id mod n_tally_batches; tally_stride doubles per row.  max_steps: per-track
@@ -285,9 +290,28 @@ typedef struct {
  * sorts its tracks by phase and solid kind of the leaf and deals them out again, so that each
  * warp runs one kind of work; every mode without diagnostics).  flags:
  * G4N_FLAG_DIAGNOSTICS also fills the diagnostic counters (G4N_C_WALK_YIELDS and above; the
- * counters below it are always filled).  Results
- * never depend on the launch shape. */
+ * counters below it are always filled).
+ *
+ * schedule: G4N_SCHEDULE_PERSISTENT (0) runs the batch in the persistent kernel described above,
+ * asynchronously on the stream.  G4N_SCHEDULE_STAGED (1) keeps the tracks in flight in
+ * structure-of-arrays queues in device memory and advances them in iterations of two kernels (one
+ * step of every queued track, its next queue chosen by the solid kind of its leaf; then the
+ * interactions and the new tracks from the source), with the last tracks of the batch finished by
+ * one persistent kernel: each kernel's code is small and its warps run one kind of work.  The call
+ * then returns when the batch has ended (it waits on the stream for an end flag every few
+ * iterations); its device errors are reported by g4n_sync as for the persistent kernel.
+ * pool_tracks: tracks in flight at most (0 = min(tracks of the batch, 2^24)); the library keeps
+ * 5 x pool_tracks x 168 bytes of queues (8.4 GB for 10^7 tracks), grown on demand and freed by
+ * g4n_destroy.  drain_tracks: the persistent kernel takes over once every track has started and
+ * at most this many are in flight (0 = four per resident thread of that kernel, < 0 = never).
+ * The staged schedule ignores block_size (128), walk_budget (searches never yield) and
+ * regroup_period; blocks_per_sm (0 = as many as fit) applies to its kernels.  Launches with
+ * G4N_FLAG_DIAGNOSTICS, the sample log (g4n_mlp_log), the allocation-free entry point and CUDA
+ * graphs always use the persistent kernel.  Results never depend on the schedule or the launch
+ * shape. */
 #define G4N_FLAG_DIAGNOSTICS 1
+#define G4N_SCHEDULE_PERSISTENT 0
+#define G4N_SCHEDULE_STAGED 1
 typedef struct {
   int32_t n_items;
   const g4n_work_item *items;
@@ -304,6 +328,10 @@ typedef struct {
   int32_t flags;
   int32_t walk_budget;
   int32_t regroup_period;
+  int32_t schedule;
+  int32_t reserved;
+  int64_t pool_tracks;
+  int64_t drain_tracks;
 } g4n_batch_desc;
 
 /* Transport every track of the batch (Algorithm 2, phase 5).  out_edep: n_tally_batches x

@@ -1,12 +1,13 @@
-"""Launch-shape autotuner of the persistent transport kernel.
+"""Schedule and launch-shape autotuner of the transport.
 
-Results never depend on the launch shape (block size, blocks per SM, the warp
-refill and interaction thresholds, the voxel-walk budget per round, the period of
-block-wide regrouping) or on the precision mode, only speed does.
-The tuner times trial launches of the caller's batch with CUDA events and walks
-one parameter at a time from the defaults, keeping any value that is faster
-(coordinate descent), within a time budget.  It only calls the C ABI through the
-binding.
+Results never depend on the schedule (the persistent kernel or the staged
+queues), the launch shape (block size, blocks per SM, the warp refill and
+interaction thresholds, the voxel-walk budget per round, the period of
+block-wide regrouping, the staged schedule's drain point) or the precision mode,
+only speed does.  The tuner times trial launches of the caller's batch with CUDA
+events: a few staged shapes, then the persistent kernel's parameters one at a
+time from the defaults, keeping any value that is faster (coordinate descent),
+within a time budget.  It only calls the C ABI through the binding.
 """
 from __future__ import annotations
 
@@ -25,7 +26,10 @@ SPACE = {
     "interact_min": (4, 8, 12, 16, 20, 24),
 }
 DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8, "walk_budget": 16,
-           "regroup_period": 0}
+           "regroup_period": 0, "schedule": b.G4N_SCHEDULE_PERSISTENT, "pool_tracks": 0, "drain_tracks": 0}
+# staged shapes tried: the drain at its default point, never, or early; two grid sizes
+STAGED = ({"drain_tracks": 0, "blocks_per_sm": 0}, {"drain_tracks": 0, "blocks_per_sm": 8},
+          {"drain_tracks": -1, "blocks_per_sm": 0}, {"drain_tracks": 1 << 20, "blocks_per_sm": 0})
 
 
 def time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps=2, stream=None):
@@ -62,8 +66,9 @@ def subset_items(items, max_tracks):
 
 
 def autotune(ctx, items, stride, seed, modes=(b.G4N_MODE_FP64, b.G4N_MODE_FP32_RECHECK), n_batches=100, reps=2,
-             budget_s=30.0, space=None, stream=None, max_tracks=2_000_000):
-    """Best (mode, launch shape) for the batch; returns dict(mode, cfg, ms, per_mode, trials).
+             budget_s=30.0, space=None, stream=None, max_tracks=2_000_000,
+             schedules=(b.G4N_SCHEDULE_STAGED, b.G4N_SCHEDULE_PERSISTENT)):
+    """Best (mode, schedule and launch shape) for the batch; returns dict(mode, cfg, ms, per_mode, trials).
     Batches of more than `max_tracks` tracks are tuned on a proportional subset (shorter
     trials, so that the budget covers the whole search)."""
     import torch
@@ -76,16 +81,31 @@ def autotune(ctx, items, stride, seed, modes=(b.G4N_MODE_FP64, b.G4N_MODE_FP32_R
     for mode in modes:
         t_end = time.perf_counter() + budget_s / len(modes)   # each mode gets its share of the budget
         time_launch(ctx, items, seed, edep, cnt, mode, DEFAULT, reps=1, stream=stream)   # warm-up
-        cfg = dict(DEFAULT)
-        best = time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps, stream)
-        trials.append((mode, dict(cfg), best))
-        for key in space:
-            for val in space[key]:
-                if val == cfg[key] or time.perf_counter() > t_end:
-                    continue
-                trial = dict(cfg, **{key: val})
+        cfg, best = None, float("inf")
+        if b.G4N_SCHEDULE_STAGED in schedules:
+            for shape in STAGED:
+                trial = dict(DEFAULT, schedule=b.G4N_SCHEDULE_STAGED, **shape)
                 ms = time_launch(ctx, items, seed, edep, cnt, mode, trial, reps, stream)
                 trials.append((mode, dict(trial), ms))
+                if ms < best:
+                    best, cfg = ms, trial
+        if b.G4N_SCHEDULE_PERSISTENT not in schedules:
+            per_mode[mode] = {"cfg": cfg, "ms": best}
+            continue
+        pcfg = dict(DEFAULT)
+        pbest = time_launch(ctx, items, seed, edep, cnt, mode, pcfg, reps, stream)
+        trials.append((mode, dict(pcfg), pbest))
+        if pbest < best:
+            best, cfg = pbest, pcfg
+        for key in space:
+            for val in space[key]:
+                if val == pcfg[key] or time.perf_counter() > t_end:
+                    continue
+                trial = dict(pcfg, **{key: val})
+                ms = time_launch(ctx, items, seed, edep, cnt, mode, trial, reps, stream)
+                trials.append((mode, dict(trial), ms))
+                if ms < pbest:
+                    pbest, pcfg = ms, trial
                 if ms < best:
                     best, cfg = ms, trial
         per_mode[mode] = {"cfg": cfg, "ms": best}

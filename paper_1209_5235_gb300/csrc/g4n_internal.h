@@ -242,7 +242,14 @@ struct g4n_ctx {
   // device buffers outgrown while work may still read them: freed by g4n_destroy (growth by
   // doubling bounds them by the live size), so that growing never synchronizes the device
   std::vector<void *> retired;
+  // staged transport: its track-state queues behind a control block (grown by doubling, the
+  // outgrown ones retired), two pinned end flags and two events (cudaEvent_t) of the chunks in flight
+  void *stage_q = nullptr;
+  size_t stage_q_bytes = 0;
+  int *stage_flag = nullptr;
+  void *stage_ev[2] = {nullptr, nullptr};
   int sm_count = 0;
+  int64_t launches = 0;  // kernels launched (g4n_kernel_launches)
   // candidate-proposal MLP state (owned by mlp.cu)
   void *mlp = nullptr;
 };

@@ -599,8 +599,12 @@ int g4n_destroy(g4n_ctx *ctx) {
   cudaFree(ctx->ws);
   cudaFree(ctx->items);
   cudaFree(ctx->d_stage);
+  cudaFree(ctx->stage_q);
   for (void *p : ctx->retired) cudaFree(p);
   cudaFreeHost(ctx->h_stage);
+  cudaFreeHost(ctx->stage_flag);
+  for (void *e : ctx->stage_ev)
+    if (e) cudaEventDestroy((cudaEvent_t)e);
   delete ctx;
   return G4N_OK;
 }

@@ -1105,6 +1105,9 @@ int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refi
   if (*refill > 32 || *inter > 32) return g4n_fail(ctx, G4N_ERR_ARG, "transport: refill_min/interact_min must be 1..32");
   if (b->mode != G4N_MODE_FP64 && b->mode != G4N_MODE_FP32_RECHECK && b->mode != G4N_MODE_LEARNED)
     return g4n_fail(ctx, G4N_ERR_ARG, "transport: unknown mode");
+  if (b->schedule != G4N_SCHEDULE_PERSISTENT && b->schedule != G4N_SCHEDULE_STAGED)
+    return g4n_fail(ctx, G4N_ERR_ARG, "transport: unknown schedule");
+  if (b->pool_tracks < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: pool_tracks must be >= 0");
   if (b->mode == G4N_MODE_LEARNED && !g4n_mlp_image(ctx))
     return g4n_fail(ctx, G4N_ERR_STATE, "transport: learned mode needs MLP weights (g4n_mlp_load / g4n_mlp_train)");
   return G4N_OK;
@@ -1160,6 +1163,7 @@ int launch_transport(g4n_ctx *ctx, const g4n_batch_desc *b, TParams &P, int bloc
   const int64_t need = (P.total + block - 1) / block;
   grid = std::max<int64_t>(1, std::min(grid, need));
   kern<<<(int)grid, block, smem, st>>>(P);
+  ++ctx->launches;
   return launch_error(ctx, "transport launch");
 }
 
@@ -1170,6 +1174,8 @@ int grid_for(g4n_ctx *ctx, int64_t n, int block) {
 }
 
 }  // namespace
+
+#include "transport_staged.cuh"
 
 extern "C" {
 
@@ -1183,6 +1189,7 @@ int g4n_locate(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, const d
   if ((rc = ensure_ws(ctx, 0))) return rc;
   cudaSetDevice(ctx->device);
   Workspace *ws = (Workspace *)ctx->ws;
+  ++ctx->launches;
   k_locate<<<grid_for(ctx, n, 128), 128, 0, (cudaStream_t)stream>>>(ctx->d_geoms, geom, n, pos, dir, out_depth,
                                                                      out_path, &ws->status);
   return launch_error(ctx, "locate launch");
@@ -1208,6 +1215,7 @@ int g4n_compute_step(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, c
                                     : (mode == G4N_MODE_FP32_RECHECK ? k_compute_step<kFP32> : k_compute_step<kLearned>);
   const size_t smem = mlp_smem_bytes(mode, 128);
   if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ++ctx->launches;
   kern<<<grid_for(ctx, n, 128), 128, smem, (cudaStream_t)stream>>>(ctx->d_geoms, geom, n, pos, dir, depth, path,
                                                                     proposed, out_step, out_safety, out_limiter,
                                                                     &ws->status, g4n_mlp_image(ctx), ctx->walk_cap);
@@ -1267,6 +1275,8 @@ static int transport_impl(g4n_ctx *ctx, const g4n_batch_desc *b, double *out_ede
   P.walk_cap = ctx->walk_cap;
   P.trial_cap = ctx->trial_cap;
   P.log = logging ? &ws->log : nullptr;
+  if (b->schedule == G4N_SCHEDULE_STAGED && !logging && !(b->flags & G4N_FLAG_DIAGNOSTICS))
+    return staged_transport(ctx, b, P, st);
   return launch_transport(ctx, b, P, block, st);
 }
 
@@ -1394,6 +1404,7 @@ int g4n_free_path(g4n_ctx *ctx, int32_t geom, int64_t n, const double *pos, cons
   int64_t grid = (int64_t)ctx->sm_count * std::max(per_sm, 1);
   grid = std::max<int64_t>(1, std::min<int64_t>(grid, (n + block - 1) / block));
   kern<<<(int)grid, block, smem, st>>>(P);
+  ++ctx->launches;
   return launch_error(ctx, "free_path launch");
 }
 
@@ -1404,6 +1415,8 @@ int g4n_set_loop_caps(g4n_ctx *ctx, int32_t max_walk_nodes, int32_t max_sampler_
   ctx->trial_cap = max_sampler_trials > 0 ? max_sampler_trials : kDefaultTrialCap;
   return G4N_OK;
 }
+
+int64_t g4n_kernel_launches(const g4n_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
 int g4n_sync(g4n_ctx *ctx, g4n_stream stream) {
   if (!ctx) return G4N_ERR_ARG;
@@ -1680,6 +1693,7 @@ int g4n_graph_launch(g4n_graph *g, uint64_t seed, g4n_stream stream) {
   if (cudaGraphExecKernelNodeSetParams(g->exec, g->kernel_node, &g->kp) != cudaSuccess ||
       cudaGraphLaunch(g->exec, (cudaStream_t)stream) != cudaSuccess)
     return g4n_fail(g->ctx, G4N_ERR_CUDA, "graph_launch failed");
+  ++g->ctx->launches;
   return G4N_OK;
 }
 

@@ -31,8 +31,10 @@ def test_clock_summary_without_samples():
 def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
     sha = bench.cuda_sources_sha256()
     monkeypatch.setitem(bench.NCU_TRAFFIC, "sources_sha256", sha)
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "bytes_per_launch", {"barrel/fp64": 1234})
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "bytes_per_launch", {"barrel/fp64": 1234, "calorimeter/fp64/staged": 99})
     assert bench.measured_traffic("barrel", "fp64") == 1234
+    assert bench.measured_traffic("barrel", "fp64", "staged") is None      # each schedule has its own capture
+    assert bench.measured_traffic("calorimeter", "fp64", "staged") == 99
     assert bench.measured_traffic("barrel", "fp32_recheck") is None
     assert bench.measured_traffic("calorimeter", "fp64") is None
     monkeypatch.setitem(bench.NCU_TRAFFIC, "sources_sha256", "0" * 64)
@@ -90,6 +92,9 @@ class _FakeG4:
     def g4n_sync(self, ctx, stream=None):
         pass
 
+    def g4n_kernel_launches(self, ctx):
+        return 5 * len(self.launches)   # as if every batch launched five kernels
+
     def counters_dict(self, cnt):
         return {"steps": 7}
 
@@ -114,9 +119,10 @@ def test_timed_region_is_bracketed_by_synchronize_and_barrier():
     class A:
         warmup, steps = 3, 4
 
-    ms, c, _ = bench.time_mode(g4, _FakeTorch, None, None, 100, 0, A, _Arr(), _Arr(), _Arr(), None, {},
-                               barrier=barrier)
+    ms, c, _, launches = bench.time_mode(g4, _FakeTorch, None, None, 100, 0, A, _Arr(), _Arr(), _Arr(), None, {},
+                                         barrier=barrier)
     assert g4.launches == [1100, 1101, 1102, 100, 101, 102, 103]     # W warm-ups, then exactly K timed launches
+    assert launches == 5 * 4                                         # the kernels of the K timed batches only
     assert len(ms) == 4 and c == {"steps": 7}
     first_timed = _FakeTorch.log.index(("flush", 0.0))
     # a synchronize and a barrier right before the first timed launch and right after the last

@@ -44,35 +44,37 @@ def _expect(env, code, text):
     assert e.value.code == code and text in str(e.value), str(e.value)
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_walk_cap_reports_timeout_and_context_recovers(env, mode):
+def test_walk_cap_reports_timeout_and_context_recovers(env, mode, schedule):
     """A voxel walk capped at one node gives up on every search that crosses a node boundary; the device
     status reaches g4n_sync as G4N_ERR_TIMEOUT.  With the default cap restored the same context gives
     the oracle's histories again."""
     g4, torch, ctx, sc, gid = env
     g4.g4n_set_loop_caps(ctx, 1, 0)
     try:
-        _run(env, mode=mode)
+        _run(env, mode=mode, schedule=schedule)
         _expect(env, g4.G4N_ERR_TIMEOUT, "voxel walk")
     finally:
         g4.g4n_set_loop_caps(ctx, 0, 0)
-    edep, cnt, h = _run(env, n=3000, seed=12, mode=mode)
+    edep, cnt, h = _run(env, n=3000, seed=12, mode=mode, schedule=schedule)
     g4.g4n_sync(ctx)
     ref = oracle.Geometry(sc).transport(synth.scenes.tiny_source(), 12, 3000)
     assert np.array_equal(h.cpu().numpy().view(np.uint64), ref["hashes"])
 
 
-def test_sampler_cap_reports_timeout(env):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_sampler_cap_reports_timeout(env, schedule):
     """Kahn's method and the disc azimuth capped at one trial reject some draws outright: reported as
     G4N_ERR_TIMEOUT (a rejection sampler reached its trial cap)."""
     g4, torch, ctx, sc, gid = env
     g4.g4n_set_loop_caps(ctx, 0, 1)
     try:
-        _run(env)
+        _run(env, schedule=schedule)
         _expect(env, g4.G4N_ERR_TIMEOUT, "rejection sampler")
     finally:
         g4.g4n_set_loop_caps(ctx, 0, 0)
-    _run(env)
+    _run(env, schedule=schedule)
     g4.g4n_sync(ctx)
 
 

@@ -200,21 +200,24 @@ def test_trained_learned_barrel_full_size_sampled(env):
     del feat, label, ncand
     n, seed = 10_000_000, synth.scenes.CONFIG_SEEDS[4][1]
     hashes = {}
-    for mode in (0, 2):
+    # the plain navigator, the learned mode with its counters (persistent kernel), the learned mode staged
+    for mode, diag, sched in ((0, False, 0), (2, True, 0), (2, False, 1)):
         edep = torch.zeros((100, sc.n_volumes + 2), dtype=torch.float64, device="cuda")
         cnt = torch.zeros(32, dtype=torch.int64, device="cuda")
         h = torch.zeros(n, dtype=torch.int64, device="cuda")
-        g4.g4n_transport_batch(ctx, _items(g4, gid, n, src), seed, edep, cnt, h, mode=mode, diagnostics=(mode == 2))
+        g4.g4n_transport_batch(ctx, _items(g4, gid, n, src), seed, edep, cnt, h, mode=mode, diagnostics=diag,
+                               schedule=sched)
         g4.g4n_sync(ctx)
-        hashes[mode] = h.cpu().numpy().view(np.uint64)
+        hashes[mode, sched] = h.cpu().numpy().view(np.uint64)
         c = g4.counters_dict(cnt)
         assert c["tracks"] == n and c["steps"] == c["geom_steps"] + c["phys_steps"]
-        if mode == 2:
+        if diag:
             assert c["proposals"] > 0
         del edep, cnt, h
-    bad = np.nonzero(hashes[0] != hashes[2])[0]
-    assert bad.size == 0, f"{bad.size} histories differ between the plain and the learned mode"
+    for key in ((2, 0), (2, 1)):
+        bad = np.nonzero(hashes[0, 0] != hashes[key])[0]
+        assert bad.size == 0, f"{bad.size} histories differ between the plain navigator and {key}"
     og = oracle.Geometry(sc)
     for i in np.unique(np.random.default_rng(8).integers(0, n, 300)):
         r = og.transport(src, seed, 1, tid0=int(i), threads=1)
-        assert hashes[2][i] == r["hashes"][0], i
+        assert hashes[2, 1][i] == r["hashes"][0], i

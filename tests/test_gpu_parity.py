@@ -283,8 +283,9 @@ def test_transport_parity(env, name, n, mode):
     _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("mode", MODES)
-def test_transport_calorimeter_full_size_sampled(env, mode):
+def test_transport_calorimeter_full_size_sampled(env, mode, schedule):
     """The benchmark workload (10^6 tracks, default launch shape): sampled histories replayed one by one
     by the oracle must match bit for bit; whole-run invariants hold at full size."""
     g4, torch, ctx = env
@@ -292,7 +293,7 @@ def test_transport_calorimeter_full_size_sampled(env, mode):
     src = synth.scenes.calorimeter_source()
     seed = synth.scenes.CONFIG_SEEDS[1][1]
     n = 1_000_000
-    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode)
+    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, schedule=schedule)
     g4.g4n_sync(ctx)
     hashes = h.cpu().numpy().view(np.uint64)
     lens = ln.cpu().numpy()
@@ -473,33 +474,35 @@ def test_logical_volume_scene_parity(env, mode):
     assert g4.counters_dict(cnt)["geom_steps"] > 5 * n   # the tracks cross many cells
 
 
-def _full_size_sampled(env, entries_fn, seed, n_sample=300, modes=(0, 1, 2)):
-    """Every mode over a full-size launch: identical histories across modes, and a random sample of
-    each mode's histories replayed one by one by the oracle."""
+def _full_size_sampled(env, entries_fn, seed, n_sample=300, modes=(0, 1, 2), schedules=(0, 1)):
+    """Every mode and schedule over a full-size launch: identical histories across them, and a random
+    sample of the histories replayed one by one by the oracle."""
     g4, torch, ctx = env
     entries, stride, total, geoms = entries_fn(g4, ctx)
     items = g4.make_items(entries)
     hashes = {}
     for mode in modes:
-        edep = torch.zeros((100, stride), dtype=torch.float64, device="cuda")
-        cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
-        h = torch.zeros(total, dtype=torch.int64, device="cuda")
-        g4.g4n_transport_batch(ctx, items, seed, edep, cnt, h, mode=mode)
-        g4.g4n_sync(ctx)
-        hashes[mode] = h.cpu().numpy().view(np.uint64)
-        c = g4.counters_dict(cnt)
-        assert c["tracks"] == total and c["steps"] == c["geom_steps"] + c["phys_steps"]
-    for mode in modes[1:]:
-        bad = np.nonzero(hashes[modes[0]] != hashes[mode])[0]
-        assert bad.size == 0, f"{bad.size} histories differ between modes {modes[0]} and {mode}, first {bad[:5]}"
+        for sched in schedules:
+            edep = torch.zeros((100, stride), dtype=torch.float64, device="cuda")
+            cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
+            h = torch.zeros(total, dtype=torch.int64, device="cuda")
+            g4.g4n_transport_batch(ctx, items, seed, edep, cnt, h, mode=mode, schedule=sched)
+            g4.g4n_sync(ctx)
+            hashes[mode, sched] = h.cpu().numpy().view(np.uint64)
+            c = g4.counters_dict(cnt)
+            assert c["tracks"] == total and c["steps"] == c["geom_steps"] + c["phys_steps"]
+    keys = list(hashes)
+    for k in keys[1:]:
+        bad = np.nonzero(hashes[keys[0]] != hashes[k])[0]
+        assert bad.size == 0, f"{bad.size} histories differ between (mode, schedule) {keys[0]} and {k}, first {bad[:5]}"
     rng = np.random.default_rng(seed)
     starts = np.cumsum([0] + [e[1] for e in entries])
     for gidx in np.unique(rng.integers(0, total, n_sample)):
         k = int(np.searchsorted(starts, gidx, side="right") - 1)
         gid, nt, tid0, src, off = entries[k]
         r = geoms[k].transport(src, seed, 1, tid0=int(tid0 + gidx - starts[k]), threads=1)
-        for mode in modes:
-            assert hashes[mode][gidx] == r["hashes"][0], (mode, gidx, k)
+        for key in keys:
+            assert hashes[key][gidx] == r["hashes"][0], (key, gidx, k)
 
 
 def test_batched_full_size_sampled(env):
