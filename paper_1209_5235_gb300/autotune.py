@@ -27,9 +27,11 @@ SPACE = {
 }
 DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8, "walk_budget": 16,
            "regroup_period": 0, "schedule": b.G4N_SCHEDULE_PERSISTENT, "pool_tracks": 0, "drain_tracks": 0}
-# staged shapes tried: the drain at its default point, never, or early; two grid sizes
+# staged shapes tried: the drain at its default point, never, or early; grids of one, two and four
+# waves of the blocks that fit
 STAGED = ({"drain_tracks": 0, "blocks_per_sm": 0}, {"drain_tracks": 0, "blocks_per_sm": 8},
-          {"drain_tracks": -1, "blocks_per_sm": 0}, {"drain_tracks": 1 << 20, "blocks_per_sm": 0})
+          {"drain_tracks": 0, "blocks_per_sm": 16}, {"drain_tracks": -1, "blocks_per_sm": 0},
+          {"drain_tracks": 1 << 20, "blocks_per_sm": 0})
 
 
 def time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps=2, stream=None):

@@ -2,12 +2,16 @@
 // compute_step and the persistent transport kernel (Algorithm 1 with Compton
 // scattering, photoabsorption and energy deposits), plus g4n_sync.
 //
-// Transport design: one persistent grid sized to fill every SM; each lane
-// carries one track in registers for its whole history (SoA state never
-// round-trips through HBM).  A warp refills its idle lanes from one global
-// queue head with a single atomicAdd per refill (__ballot_sync/__popc), so
-// uneven history lengths and uneven geometries share one launch (the
-// periodic compaction/refill of Sec. 5, done per step in-warp).
+// Transport design, two schedules over the same per-track device functions:
+//  - persistent: one grid sized to fill every SM; each lane carries one track in
+//    registers for its whole history.  A warp refills its idle lanes from one
+//    global queue head with a single atomicAdd per refill (__ballot_sync/__popc),
+//    so uneven history lengths and uneven geometries share one launch (the
+//    periodic compaction/refill of Sec. 5, done per step in-warp).
+//  - staged (transport_staged.cuh): the tracks in flight live in SoA queues in
+//    HBM and advance in iterations of a step kernel and an interaction/source
+//    kernel, each track queued by the solid kind of its leaf (the compaction of
+//    Sec. 5 done every step, globally, by the queues themselves).
 #include <cuda_runtime.h>
 
 #include <algorithm>
