@@ -56,15 +56,19 @@ STAGED_STATE_BYTES = 168
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (2 DFMA) = 1.2586
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_transport launch, per workload and mode, from
-# a single-pass ncu capture of the bench's first timed launch run without the L2 flush before it (--no-flush; the
-# flush changes the figure by < 1 %): summaries in profiles/.  Reported only while the CUDA sources hash to the value
-# they had when the captures were taken (else the kernel has changed since).
-NCU_TRAFFIC = {"sources_sha256": "516237c420ba22056c5c6ad79e7558b5ff06635345fe4eb9d0d6e159e38dba73",
-               # barrel: captured on the plain barrel workload (same scene and 10^7 tracks, another seed); the learned
-               # workload's line times the same FP64 kernel
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one transport batch, per workload, mode and schedule,
+# from single-pass ncu captures run without the L2 flush before the batch (--no-flush; the flush changes the figure by
+# < 1 %): the persistent kernel's one launch, or the sum over the staged schedule's kernels of a batch (launch list of
+# nine batches, divided by nine).  Summaries in profiles/.  Reported only while the CUDA sources hash to the value
+# they had when the captures were taken (else the kernels may have changed since).
+NCU_TRAFFIC = {"sources_sha256": "ee81f458d22bdcc92120b5976dcc57f4e72f6d62a2ee7c7060126d2ec4fbc380",
+               # persistent kernel: captured at an earlier hash whose k_transport device code is the same (only host
+               # code and the staged kernels were added since); barrel: captured on the plain barrel workload (same
+               # scene and 10^7 tracks, another seed), which the learned workload's line times with the same kernels
                "bytes_per_launch": {"barrel/fp64": 8518400 + 997785600, "barrel_learned/fp64": 8518400 + 997785600,
-                                    "calorimeter/fp64": 2280192 + 40204288}}
+                                    "calorimeter/fp64": 2280192 + 40204288,
+                                    "barrel/fp64/staged": 46469637120, "barrel_learned/fp64/staged": 46469637120,
+                                    "calorimeter/fp64/staged": 4342757148}}
 
 
 def cuda_sources_sha256() -> str:
