@@ -300,9 +300,10 @@ typedef struct {
  * one persistent kernel: each kernel's code is small and its warps run one kind of work.  The call
  * then returns when the batch has ended (it waits on the stream for an end flag every few
  * iterations); its device errors are reported by g4n_sync as for the persistent kernel.
- * pool_tracks: tracks in flight at most (0 = min(tracks of the batch, 2^24)); the library keeps
- * 5 x pool_tracks x 168 bytes of queues (8.4 GB for 10^7 tracks), grown on demand and freed by
- * g4n_destroy.  drain_tracks: the persistent kernel takes over once every track has started and
+ * pool_tracks: tracks in flight at most (0 = min(tracks of the batch, 2^24), halved while its queues
+ * do not fit the free device memory); the library keeps 5 x pool_tracks x 168 bytes of queues
+ * (8.4 GB for 10^7 tracks), grown on demand and freed by g4n_destroy; G4N_ERR_OOM if an explicit
+ * pool's queues cannot be allocated.  drain_tracks: the persistent kernel takes over once every track has started and
  * at most this many are in flight (0 = four per resident thread of that kernel, < 0 = never).
  * The staged schedule ignores block_size (128), walk_budget (searches never yield) and
  * regroup_period; blocks_per_sm (0 = as many as fit) applies to its kernels.  Launches with

@@ -396,20 +396,38 @@ int sg_grid(g4n_ctx *ctx, const g4n_batch_desc *b, K kern, size_t smem) {
 template <int MODE>
 int staged_run(g4n_ctx *ctx, const g4n_batch_desc *b, TParams &P, cudaStream_t st) {
   if (b->pool_tracks < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: pool_tracks must be >= 0");
-  const int64_t pool = std::max<int64_t>(1, std::min<int64_t>(b->pool_tracks > 0 ? b->pool_tracks : kSgDefaultPool,
-                                                              P.total));
+  int64_t pool = std::max<int64_t>(1, std::min<int64_t>(b->pool_tracks > 0 ? b->pool_tracks : kSgDefaultPool, P.total));
   const size_t ctrl_bytes = 1024;
-  const size_t need = ctrl_bytes + (size_t)kSgArrays * (size_t)pool * kSgEntryBytes;
-  if (ctx->stage_q_bytes < need) {
-    const size_t bytes = std::max(need, 2 * ctx->stage_q_bytes);
+  auto queue_bytes = [&](int64_t n) { return ctrl_bytes + (size_t)kSgArrays * (size_t)n * kSgEntryBytes; };
+  if (ctx->stage_q_bytes < queue_bytes(pool)) {
+    // grow by up to half again (batches of slowly growing size do not reallocate every call); the default pool
+    // halves until its queues fit the free device memory, an explicit pool does not
     void *p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    size_t got = 0;
+    for (;;) {
+      const size_t need = queue_bytes(pool);
+      const size_t want = std::max(need, std::min(2 * ctx->stage_q_bytes, need + need / 2));
+      if (cudaMalloc(&p, want) == cudaSuccess) {
+        got = want;
+        break;
+      }
       cudaGetLastError();
-      return g4n_fail(ctx, G4N_ERR_OOM, "transport: staged queue allocation failed (lower pool_tracks)");
+      if (want > need && cudaMalloc(&p, need) == cudaSuccess) {
+        got = need;
+        break;
+      }
+      cudaGetLastError();
+      p = nullptr;
+      if (b->pool_tracks > 0 || pool <= (int64_t(1) << 16))
+        return g4n_fail(ctx, G4N_ERR_OOM, "transport: staged queue allocation failed (lower pool_tracks)");
+      pool /= 2;
+      if (ctx->stage_q_bytes >= queue_bytes(pool)) break;  // the queues held already suffice
     }
-    if (ctx->stage_q) ctx->retired.push_back(ctx->stage_q);
-    ctx->stage_q = p;
-    ctx->stage_q_bytes = bytes;
+    if (p) {
+      if (ctx->stage_q) ctx->retired.push_back(ctx->stage_q);
+      ctx->stage_q = p;
+      ctx->stage_q_bytes = got;
+    }
   }
   if (!ctx->stage_flag) {
     if (cudaMallocHost(&ctx->stage_flag, 2 * sizeof(int)) != cudaSuccess) {
