@@ -125,6 +125,30 @@ __device__ __forceinline__ void sg_push(const SgQueues &Q, SgCtrl *C, bool want,
   if (want) sg_store(Q, sg_entry(Q, q, (long long)base + __popc(peers & ((1u << lane) - 1u))), t);
 }
 
+// Block-wide append (every thread of the block calls it, with the block's warps converged): the warps count
+// their lanes per queue in shared memory, one thread per queue reserves the block's slots with one global
+// atomic, and every lane stores at its slot.  The step kernel appends this way: one global atomic per queue
+// per block of 128 tracks instead of per warp, and its loop over the queue runs in block-sized strides.
+__shared__ unsigned s_qcount[kSgQueues];
+__shared__ unsigned long long s_qbase[kSgQueues];
+
+__device__ __forceinline__ void sg_push_block(const SgQueues &Q, SgCtrl *C, bool want, int q, const Track &t) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned peers = __match_any_sync(kFull, want ? q : -1);
+  const int leader = __ffs(peers) - 1;
+  unsigned woff = 0;
+  if (want && (int)lane == leader) woff = atomicAdd(&s_qcount[q], (unsigned)__popc(peers));
+  woff = __shfl_sync(kFull, woff, leader);
+  __syncthreads();
+  if (threadIdx.x < kSgQueues) {
+    const unsigned c = s_qcount[threadIdx.x];
+    s_qbase[threadIdx.x] = c ? atomicAdd(&C->cnt[threadIdx.x], (unsigned long long)c) : 0ull;
+    s_qcount[threadIdx.x] = 0;  // ready for the next call (the barrier below orders it before any new count)
+  }
+  __syncthreads();
+  if (want) sg_store(Q, sg_entry(Q, q, (long long)(s_qbase[q] + woff + __popc(peers & ((1u << lane) - 1u)))), t);
+}
+
 // Step queue of bank b for the track's leaf.
 __device__ __forceinline__ int sg_queue_of(const TParams &P, const Track &t, int b) {
   return b * kSgKinds + P.geoms[P.items[t.item].geom].vol[t.leaf].kind;
@@ -155,6 +179,7 @@ __device__ __forceinline__ void sg_begin(Counters &cnt) {
 #pragma unroll
   for (int k = 0; k < G4N_N_COUNTERS; ++k) cnt.c[k] = 0;
   for (int k = threadIdx.x; k < G4N_N_COUNTERS; k += blockDim.x) s_events[k] = 0;
+  if (threadIdx.x < kSgQueues) s_qcount[threadIdx.x] = 0;
   __syncthreads();
 }
 
@@ -216,10 +241,10 @@ __global__ void __launch_bounds__(128, 4) k_staged_step(const TParams P, const S
   const long long total = sg_prefix(C, ib, pref);
   const int ob = ib ^ 1;
   const bool want_slot = P.out_hash || P.out_len;
-  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  // block-sized strides: the loop condition is the same for every thread of the block (sg_push_block's barriers)
 #pragma unroll 1
-  for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < total; w += nw) {
-    const long long i = w * 32 + (threadIdx.x & 31u);
+  for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < total; b0 += (long long)gridDim.x * blockDim.x) {
+    const long long i = b0 + threadIdx.x;
     Track t;
     t.item = 0;
     t.leaf = 0;
@@ -236,7 +261,7 @@ __global__ void __launch_bounds__(128, 4) k_staged_step(const TParams P, const S
     const int next = step_warp<MODE, false, false, true>(P, t, phase, cnt, mc, ch);
     const bool was = phase == kStep;
     const bool keep = was && next != kEmpty;
-    sg_push(Q, C, keep, !keep ? 0 : next == kStep ? sg_queue_of(P, t, ob) : kSgInteract, t);
+    sg_push_block(Q, C, keep, !keep ? 0 : next == kStep ? sg_queue_of(P, t, ob) : kSgInteract, t);
     sg_retire(C, was && next == kEmpty);
   }
   sg_flush(P, cnt);
