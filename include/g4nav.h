@@ -97,7 +97,8 @@ enum {
 
 /* Create a context on CUDA device `device` (>= 0), or a host-only context (device = -1) that builds,
  * validates and voxelizes geometry without touching a GPU (its queries return G4N_ERR_STATE).
- * *ctx is set to NULL on failure. */
+ * *ctx is set to NULL on failure.  The setup that precedes the paper's benchmark program
+ * (Algorithm 2); no counterpart in the paper. */
 int g4n_create(g4n_ctx **ctx, int device);
 /* Free every device and host resource of the context.  NULL is accepted. */
 int g4n_destroy(g4n_ctx *ctx);
@@ -150,7 +151,10 @@ int g4n_solid_cone(g4n_ctx *ctx, double rmin1, double rmax1, double rmin2, doubl
 int g4n_place(g4n_ctx *ctx, int32_t mother, int32_t solid, int32_t mat, const double *t, const double *rot,
               int32_t *out_vol);
 
-/* Smart-voxel request for the geometry being built.  mode 0 = smart heuristic (per mother, per
+/* Smart-voxel request for the geometry being built.  The paper does not describe its candidate search
+ * (its port runs the isolated Geant4 navigation code, Sec. 3.3); these voxels are this library's own
+ * acceleration structure, in the manner of Geant4's smart voxels, for the candidate search of the two
+ * navigation problems of Sec. 3.2.  mode 0 = smart heuristic (per mother, per
  * level: slices = clamp(smartless x daughters, 1, max_slices) on the axis with the fewest
  * candidates per node, equal neighbouring nodes merged, nodes with more than refine_above
  * candidates refined on a further axis, up to 3 levels); mode 1 = fixed (n_levels levels with the
@@ -186,8 +190,9 @@ int g4n_place_logical(g4n_ctx *ctx, int32_t mother_vol, int32_t lv, const double
                       int32_t *out_first_vol, int32_t *out_n_vols);
 
 /* Validate the volumes placed since the last finalize (every daughter inside its mother,
- * siblings not overlapping, depth <= G4N_DMAX), build the voxels and upload the tables.
- * Returns the geometry id in *out_geom. */
+ * siblings not overlapping, depth <= G4N_DMAX), build the voxels and upload the tables:
+ * Algorithm 2 phase 1 (load the geometry and transfer it to GPU memory).  Returns the geometry id
+ * in *out_geom. */
 int g4n_geom_finalize(g4n_ctx *ctx, int32_t *out_geom);
 
 /* Table sizes of a finalized geometry (HOST array of 8): n_volumes, n_voxel_headers,

@@ -51,7 +51,7 @@ EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_sc
 __all__ = EXPORTED + ["G4N_FLAG_DIAGNOSTICS", "G4N_SCHEDULE_PERSISTENT", "G4N_SCHEDULE_STAGED", "G4NError", "load", "lib_path", "build_scene", "build_logical_scene", "make_items", "counters_dict", "voxel_params",
                       "COUNTER_NAMES", "PARITY_COUNTERS", "G4N_DMAX", "G4N_N_COUNTERS", "G4N_MODE_FP64",
                       "G4N_MODE_FP32_RECHECK", "G4N_MODE_LEARNED", "G4N_LIM_PHYSICS", "G4N_LIM_MOTHER",
-                      "G4N_ERR_ARG", "G4N_ERR_GEOM", "G4N_ERR_STEP_LIMIT", "G4N_ERR_TIMEOUT", "G4N_ERR_STATE",
+                      "G4N_ERR_ARG", "G4N_ERR_GEOM", "G4N_ERR_OOM", "G4N_ERR_CUDA", "G4N_ERR_STEP_LIMIT", "G4N_ERR_TIMEOUT", "G4N_ERR_STATE",
                       "G4N_NOALLOC_MAX_ITEMS", "G4N_NOALLOC_STATUS_SLOT", "G4N_MLP_N_PARAMS",
                       "g4n_voxel_params", "g4n_source", "g4n_work_item", "g4n_batch_desc"]
 

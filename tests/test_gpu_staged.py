@@ -194,3 +194,39 @@ def test_staged_matches_persistent_and_reuses_queues(env):
     for h, c in outs[1:]:
         assert np.array_equal(h, outs[0][0])
         assert np.array_equal(c[:10], outs[0][1][:10])
+
+
+def test_staged_explicit_pool_out_of_memory(env):
+    """An explicit pool whose queues cannot be allocated is refused with G4N_ERR_OOM before any kernel runs (a
+    batch of 10^10 tracks asks for 8.4 TB of queues); the context then runs the next batch as usual."""
+    g4, torch, ctx = env
+    sc, src, n, og, gid, r = _scene(env, "tiny")
+    items = g4.make_items([(gid, 10 ** 10, 0, src, 0)])
+    edep = torch.zeros((100, sc.n_volumes + 2), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
+    with pytest.raises(g4.G4NError) as e:
+        g4.g4n_transport_batch(ctx, items, SEED, edep, cnt, schedule=STAGED, pool_tracks=10 ** 10)
+    assert e.value.code == g4.G4N_ERR_OOM and "pool_tracks" in str(e.value)
+    assert cnt.abs().sum().item() == 0
+    out = _run(env, gid, sc, src, SEED, n, pool_tracks=2000)
+    g4.g4n_sync(ctx)
+    _compare(g4, r, *out, sc.n_volumes)
+
+
+def test_allocation_free_entry_point_keeps_the_persistent_kernel(env):
+    """The allocation-free entry point runs the persistent kernel whatever the batch's schedule (the staged
+    queues are allocated memory): the same histories as the oracle, no queue memory taken."""
+    g4, torch, ctx = env
+    sc, src, n, og, gid, r = _scene(env, "calorimeter")
+    items = g4.make_items([(gid, n, 0, src, 0)])
+    edep = torch.zeros((100, sc.n_volumes + 2), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
+    h = torch.zeros(n, dtype=torch.int64, device="cuda")
+    ln = torch.zeros(n, dtype=torch.float64, device="cuda")
+    launches = g4.g4n_kernel_launches(ctx)
+    g4.g4n_transport_batch_noalloc(ctx, items, SEED, edep, cnt, h, ln, schedule=STAGED)
+    torch.cuda.synchronize()
+    assert int(cnt[g4.G4N_NOALLOC_STATUS_SLOT].item()) == 0
+    assert g4.g4n_kernel_launches(ctx) - launches == 1    # one persistent launch
+    cnt[g4.G4N_NOALLOC_STATUS_SLOT] = 0
+    _compare(g4, r, edep, cnt, h, ln, sc.n_volumes)
