@@ -61,9 +61,9 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flop
 # < 1 %): the persistent kernel's one launch, or the sum over the staged schedule's kernels of a batch (launch list of
 # nine batches, divided by nine).  Summaries in profiles/.  Reported only while the CUDA sources hash to the value
 # they had when the captures were taken (else the kernels may have changed since).
-NCU_TRAFFIC = {"sources_sha256": "2214188635b891eba96ce704dc861f56355988f5f3d5f5dbeb014b3bbc19b75e",
-               # staged: captured at commit 04de76f, whose CUDA sources differ from these only in the comments of
-               # g4nav.h; persistent kernel: captured at an earlier hash whose k_transport device code is the same (only
+NCU_TRAFFIC = {"sources_sha256": "7442afa4330e317c30072e4a7cacb4ce8355323a69cb88fdfbe0647c62d1c6b7",
+               # staged: captured at commit 04de76f, whose CUDA sources differ from these only in comments and in the
+               # launch bounds of k_locate (a query kernel, not part of a transport batch); persistent kernel: captured at an earlier hash whose k_transport device code is the same (only
                # host code and the staged kernels were added since); barrel: captured on the plain barrel workload (same
                # scene and 10^7 tracks, another seed), which the learned workload's line times with the same kernels
                "bytes_per_launch": {"barrel/fp64": 8518400 + 997785600, "barrel_learned/fp64": 8518400 + 997785600,
