@@ -297,3 +297,36 @@ def test_binding_checks_query_shapes(g4):
             g4.g4n_locate(ctx, 0, _FakeCuda(torch.zeros((10, 3), dtype=torch.float64)), pos)
     finally:
         g4.binding._CTX_DEVICE.pop(ctx.value, None)
+
+
+def test_ctypes_structures_match_the_header_layout(tmp_path):
+    """The binding's ctypes mirrors of the ABI structures have the C compiler's size and field offsets (a C
+    program built from include/g4nav.h prints them), so that no field of a batch description or work item is
+    read from the wrong place."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    from paper_1209_5235_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"g4n_batch_desc": binding.g4n_batch_desc, "g4n_work_item": binding.g4n_work_item,
+               "g4n_source": binding.g4n_source, "g4n_voxel_params": binding.g4n_voxel_params}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "g4nav.h"', "int main(void) {"]
+    for name, st in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, st in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert got[(name, field)] == getattr(st, field).offset, (name, field)
