@@ -93,7 +93,7 @@ def measured_traffic(workload: str, mode: str, schedule: str = "persistent"):
     per = NCU_TRAFFIC["bytes_per_launch"] or {}
     if NCU_TRAFFIC["sources_sha256"] != cuda_sources_sha256():
         return None
-    return per.get(f"{workload}/{mode}" + ("/staged" if schedule == "staged" else ""))
+    return per.get(f"{workload}/{mode}" + ("" if schedule == "persistent" else "/" + schedule))
 
 
 def algorithmic_flops(c: dict) -> float:
@@ -479,7 +479,8 @@ def run_gpu(args):
     manual = dict(block_size=args.block, blocks_per_sm=args.blocks_per_sm, refill_min=args.refill_min,
                   interact_min=args.interact_min, walk_budget=args.walk_budget, regroup_period=args.regroup,
                   schedule=g4.G4N_SCHEDULE_STAGED if args.schedule == "staged" else g4.G4N_SCHEDULE_PERSISTENT,
-                  pool_tracks=args.pool, drain_tracks=args.drain)
+                  pool_tracks=args.pool, drain_tracks=args.drain,
+                  staged_flags=g4.G4N_STAGED_RELOCATION_KERNEL if args.reloc_kernel else 0)
     launch = {m: tuned.get(m, manual) for m in mode_names}
     # matched results: the same histories, bit for bit, in every mode (one launch with hashes each)
     ref_h = None
@@ -560,15 +561,20 @@ def run_gpu(args):
     achieved = flops / t_launch / 1e12
     hbm_bytes = (nb * stride * 8) * 2              # tallies read + written once per launch; tables stay in L2
     staged = R["schedule"] == "staged"
+    reloc_kernel = staged and bool(R["launch"].get("staged_flags", 0) & g4.G4N_STAGED_RELOCATION_KERNEL)
     if staged:
-        # the queues: every step and every interaction reads a state and writes one back, every start writes one
+        # the queues: every step and every interaction reads a state and writes one back, every start writes one;
+        # with the relocation kernel every relocation search (a crossing no face record answers) one more of each
         hbm_bytes += STAGED_STATE_BYTES * (2 * cdiag["steps"] + 2 * (cdiag["photo"] + cdiag["compton"])
                                            + cdiag["tracks"])
+        if reloc_kernel:
+            hbm_bytes += (STAGED_STATE_BYTES + 4) * 2 * (cdiag["geom_steps"] - cdiag["face_reloc"])
     line = {
         "metric": METRIC, "value": R["steps_per_s"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload, "tracks_per_gpu": n, "mode": chosen, "schedule": R["schedule"],
+        "config": {"workload": workload, "tracks_per_gpu": n, "mode": chosen,
+                   "schedule": R["schedule"] + (" + relocation kernel" if reloc_kernel else ""),
                    "l2": ("not flushed (DRAM-traffic capture run)" if args.no_flush
                           else "flushed between timed steps (256 MB write)"), "launch": launch[chosen],
                    "autotuned": bool(args.autotune), "voxel": args.voxel if args.workload == "calorimeter" else "smart"},
@@ -581,10 +587,12 @@ def run_gpu(args):
         "gpu_launches": R["gpu_launches"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": measured_traffic(args.workload, chosen, R["schedule"]),
+                     "traffic": measured_traffic(args.workload, chosen,
+                                                 R["schedule"] + ("+reloc" if reloc_kernel else "")),
                      "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flops/clk/SM (recipe nominal 1.25 TFLOP/s)",
-                     "kernel": ("k_staged_step + k_staged_finish + k_staged_drain (one transport batch)" if staged
-                                else "k_transport"), "flops_per_launch": flops},
+                     "kernel": (("k_staged_step + k_staged_reloc + k_staged_finish + k_staged_drain" if reloc_kernel
+                                 else "k_staged_step + k_staged_finish + k_staged_drain") + " (one transport batch)"
+                                if staged else "k_transport"), "flops_per_launch": flops},
         "hbm": {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / t_launch / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"),
                 "frac": (hbm_bytes / t_launch / 1e9) / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None},
@@ -950,6 +958,8 @@ def main():
                     help="schedule of the transport when --autotune 0 (the tuner chooses it otherwise)")
     ap.add_argument("--pool", type=int, default=0, help="staged schedule: tracks in flight (0 = default)")
     ap.add_argument("--drain", type=int, default=0, help="staged schedule: drain point (0 = default, -1 = never)")
+    ap.add_argument("--reloc-kernel", type=int, default=0,
+                    help="staged schedule: relocation searches in a kernel of their own (1) or in the step kernel (0)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tune-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -306,9 +306,12 @@ typedef struct {
  * then returns when the batch has ended (it waits on the stream for an end flag every few
  * iterations); its device errors are reported by g4n_sync as for the persistent kernel.
  * pool_tracks: tracks in flight at most (0 = min(tracks of the batch, 2^24), halved while its queues
- * do not fit the free device memory); the library keeps 5 x pool_tracks x 168 bytes of queues
- * (8.4 GB for 10^7 tracks), grown on demand and freed by g4n_destroy; G4N_ERR_OOM if an explicit
- * pool's queues cannot be allocated.  drain_tracks: the persistent kernel takes over once every track has started and
+ * do not fit the free device memory); the library keeps 6 x pool_tracks x 172 bytes of queues
+ * (10.3 GB for 10^7 tracks), grown on demand and freed by g4n_destroy; G4N_ERR_OOM if an explicit
+ * pool's queues cannot be allocated.  staged_flags: G4N_STAGED_RELOCATION_KERNEL runs the relocation
+ * searches after geometry-limited steps in a kernel of their own, in full warps of searching lanes
+ * (it pays where most relocations need a search, as in tube segments, and costs a launch per
+ * iteration where face records answer most of them, as in box cells).  drain_tracks: the persistent kernel takes over once every track has started and
  * at most this many are in flight (0 = four per resident thread of that kernel, < 0 = never).
  * The staged schedule ignores block_size (128), walk_budget (searches never yield) and
  * regroup_period; blocks_per_sm (0 = as many as fit) applies to its kernels.  Launches with
@@ -318,6 +321,7 @@ typedef struct {
 #define G4N_FLAG_DIAGNOSTICS 1
 #define G4N_SCHEDULE_PERSISTENT 0
 #define G4N_SCHEDULE_STAGED 1
+#define G4N_STAGED_RELOCATION_KERNEL 1
 typedef struct {
   int32_t n_items;
   const g4n_work_item *items;
@@ -335,7 +339,7 @@ typedef struct {
   int32_t walk_budget;
   int32_t regroup_period;
   int32_t schedule;
-  int32_t reserved;
+  int32_t staged_flags;
   int64_t pool_tracks;
   int64_t drain_tracks;
 } g4n_batch_desc;

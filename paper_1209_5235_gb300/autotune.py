@@ -26,12 +26,14 @@ SPACE = {
     "interact_min": (4, 8, 12, 16, 20, 24),
 }
 DEFAULT = {"block_size": 128, "blocks_per_sm": 0, "refill_min": 8, "interact_min": 8, "walk_budget": 16,
-           "regroup_period": 0, "schedule": b.G4N_SCHEDULE_PERSISTENT, "pool_tracks": 0, "drain_tracks": 0}
-# staged shapes tried: the drain at its default point, never, or early; grids of one, two and four
-# waves of the blocks that fit
-STAGED = ({"drain_tracks": 0, "blocks_per_sm": 0}, {"drain_tracks": 0, "blocks_per_sm": 8},
-          {"drain_tracks": 0, "blocks_per_sm": 16}, {"drain_tracks": -1, "blocks_per_sm": 0},
-          {"drain_tracks": 1 << 20, "blocks_per_sm": 0})
+           "regroup_period": 0, "schedule": b.G4N_SCHEDULE_PERSISTENT, "pool_tracks": 0, "drain_tracks": 0,
+           "staged_flags": 0}
+# staged shapes tried: grids of one, two and four waves of the blocks that fit, with and without the separate
+# relocation kernel; the drain at its default point, never, or early
+STAGED = tuple({"drain_tracks": 0, "blocks_per_sm": bps, "staged_flags": fl}
+               for fl in (0, b.G4N_STAGED_RELOCATION_KERNEL) for bps in (0, 8, 16)) + \
+    ({"drain_tracks": -1, "blocks_per_sm": 0, "staged_flags": 0},
+     {"drain_tracks": 1 << 20, "blocks_per_sm": 0, "staged_flags": 0})
 
 
 def time_launch(ctx, items, seed, edep, cnt, mode, cfg, reps=2, stream=None):

@@ -27,6 +27,7 @@ G4N_DMAX = 32
 G4N_N_COUNTERS = 32
 G4N_FLAG_DIAGNOSTICS = 1
 G4N_SCHEDULE_PERSISTENT, G4N_SCHEDULE_STAGED = 0, 1
+G4N_STAGED_RELOCATION_KERNEL = 1
 G4N_NOALLOC_MAX_ITEMS = 256
 G4N_MLP_N_PARAMS = 6880
 G4N_NOALLOC_STATUS_SLOT = G4N_N_COUNTERS - 1
@@ -48,7 +49,7 @@ EXPORTED = ["g4n_create", "g4n_destroy", "g4n_last_error", "g4n_set_tolerance_sc
             "g4n_transport_batch_noalloc", "g4n_mlp_load", "g4n_mlp_get", "g4n_mlp_log", "g4n_mlp_train",
             "g4n_mlp_grad", "g4n_mlp_predict", "g4n_graph_create", "g4n_graph_launch", "g4n_graph_destroy"]
 
-__all__ = EXPORTED + ["G4N_FLAG_DIAGNOSTICS", "G4N_SCHEDULE_PERSISTENT", "G4N_SCHEDULE_STAGED", "G4NError", "load", "lib_path", "build_scene", "build_logical_scene", "make_items", "counters_dict", "voxel_params",
+__all__ = EXPORTED + ["G4N_FLAG_DIAGNOSTICS", "G4N_SCHEDULE_PERSISTENT", "G4N_SCHEDULE_STAGED", "G4N_STAGED_RELOCATION_KERNEL", "G4NError", "load", "lib_path", "build_scene", "build_logical_scene", "make_items", "counters_dict", "voxel_params",
                       "COUNTER_NAMES", "PARITY_COUNTERS", "G4N_DMAX", "G4N_N_COUNTERS", "G4N_MODE_FP64",
                       "G4N_MODE_FP32_RECHECK", "G4N_MODE_LEARNED", "G4N_LIM_PHYSICS", "G4N_LIM_MOTHER",
                       "G4N_ERR_ARG", "G4N_ERR_GEOM", "G4N_ERR_OOM", "G4N_ERR_CUDA", "G4N_ERR_STEP_LIMIT", "G4N_ERR_TIMEOUT", "G4N_ERR_STATE",
@@ -86,7 +87,7 @@ class g4n_batch_desc(ctypes.Structure):
                 ("tally_stride", ctypes.c_int64), ("max_steps", ctypes.c_int64), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("refill_min", ctypes.c_int32), ("interact_min", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("walk_budget", ctypes.c_int32), ("regroup_period", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32), ("pool_tracks", ctypes.c_int64),
+                ("schedule", ctypes.c_int32), ("staged_flags", ctypes.c_int32), ("pool_tracks", ctypes.c_int64),
                 ("drain_tracks", ctypes.c_int64)]
 
 
@@ -480,7 +481,7 @@ def make_items(entries) -> "ctypes.Array":
 
 def _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, refill_min=0,
           interact_min=0, diagnostics=False, walk_budget=0, regroup_period=0, schedule=0, pool_tracks=0,
-          drain_tracks=0):
+          drain_tracks=0, staged_flags=0):
     d = g4n_batch_desc()
     d.n_items = len(items)
     d.items = ctypes.cast(items, ctypes.POINTER(g4n_work_item))
@@ -498,6 +499,7 @@ def _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, b
     d.schedule = int(schedule)
     d.pool_tracks = int(pool_tracks)
     d.drain_tracks = int(drain_tracks)
+    d.staged_flags = int(staged_flags)
     return d
 
 
@@ -505,12 +507,13 @@ def g4n_transport_batch(ctx, items, seed: int, edep, counters, track_hash=None, 
                         mode: int = G4N_MODE_FP64, n_batches: int = 100, max_steps: int = 0, block_size: int = 0,
                         blocks_per_sm: int = 0, refill_min: int = 0, interact_min: int = 0,
                         diagnostics: bool = False, stream=None, walk_budget: int = 0, regroup_period: int = 0,
-        schedule: int = 0, pool_tracks: int = 0, drain_tracks: int = 0) -> None:
+        schedule: int = 0, pool_tracks: int = 0, drain_tracks: int = 0,
+        staged_flags: int = 0) -> None:
     """Device outputs (accumulated): edep (n_batches, stride) f64, counters (32,) int64 (as uint64 bits)."""
     ptrs = _transport_ptrs(ctx, items, edep, counters, track_hash, track_len, n_batches)
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
               interact_min, diagnostics, walk_budget, regroup_period, schedule, pool_tracks,
-              drain_tracks)
+              drain_tracks, staged_flags)
     _check(ctx, load().g4n_transport_batch(ctx, ctypes.byref(d), *ptrs, _stream(stream)))
 
 
@@ -519,7 +522,8 @@ def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_has
                                 max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0, refill_min: int = 0,
                                 interact_min: int = 0, diagnostics: bool = False, stream=None,
                                 walk_budget: int = 0, regroup_period: int = 0,
-        schedule: int = 0, pool_tracks: int = 0, drain_tracks: int = 0) -> None:
+        schedule: int = 0, pool_tracks: int = 0, drain_tracks: int = 0,
+        staged_flags: int = 0) -> None:
     """The allocation-free variant of g4n_transport_batch (at most G4N_NOALLOC_MAX_ITEMS items).
 
     For callers that must not allocate device memory while running: the library keeps this call's
@@ -529,7 +533,7 @@ def g4n_transport_batch_noalloc(ctx, items, seed: int, edep, counters, track_has
     ptrs = _transport_ptrs(ctx, items, edep, counters, track_hash, track_len, n_batches)
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
               interact_min, diagnostics, walk_budget, regroup_period, schedule, pool_tracks,
-              drain_tracks)
+              drain_tracks, staged_flags)
     _check(ctx, load().g4n_transport_batch_noalloc(ctx, ctypes.byref(d), *ptrs, _stream(stream)))
 
 
@@ -538,11 +542,12 @@ def g4n_transport_batch_host(ctx, items, seed: int, stride: int, n_tracks: int =
                              n_batches: int = 100, max_steps: int = 0, block_size: int = 0, blocks_per_sm: int = 0,
                              refill_min: int = 0, interact_min: int = 0, diagnostics: bool = False, stream=None,
                              out=None, walk_budget: int = 0, regroup_period: int = 0,
-        schedule: int = 0, pool_tracks: int = 0, drain_tracks: int = 0):
+        schedule: int = 0, pool_tracks: int = 0, drain_tracks: int = 0,
+        staged_flags: int = 0):
     """Host-buffer variant: returns dict of numpy arrays (edep, counters, hashes, lengths)."""
     d = _desc(items, seed, cutoff, mode, n_batches, stride, max_steps, block_size, blocks_per_sm, refill_min,
               interact_min, diagnostics, walk_budget, regroup_period, schedule, pool_tracks,
-              drain_tracks)
+              drain_tracks, staged_flags)
     if out is None:
         out = {"edep": np.zeros((n_batches, stride)), "counters": np.zeros(G4N_N_COUNTERS, dtype=np.uint64),
                "hashes": np.zeros(n_tracks, dtype=np.uint64) if want_hash else None,
@@ -632,12 +637,13 @@ def g4n_graph_create(ctx, items, seed: int, edep, counters, track_hash=None, tra
                      mode: int = G4N_MODE_FP64, n_batches: int = 100, max_steps: int = 0, block_size: int = 0,
                      blocks_per_sm: int = 0, refill_min: int = 0, interact_min: int = 0, diagnostics: bool = False,
                      walk_budget: int = 0, regroup_period: int = 0,
-        schedule: int = 0, pool_tracks: int = 0, drain_tracks: int = 0):
+        schedule: int = 0, pool_tracks: int = 0, drain_tracks: int = 0,
+        staged_flags: int = 0):
     """Record the batch as a CUDA graph writing into the given device outputs; returns the handle."""
     ptrs = _transport_ptrs(ctx, items, edep, counters, track_hash, track_len, n_batches)
     d = _desc(items, seed, cutoff, mode, n_batches, edep.shape[1], max_steps, block_size, blocks_per_sm, refill_min,
               interact_min, diagnostics, walk_budget, regroup_period, schedule, pool_tracks,
-              drain_tracks)
+              drain_tracks, staged_flags)
     h = ctypes.c_void_p()
     _check(ctx, load().g4n_graph_create(ctx, ctypes.byref(d), *ptrs, ctypes.byref(h)))
     return (ctx, h)

@@ -444,8 +444,60 @@ __device__ __forceinline__ V3 deflect(const V3 &u, double ct, double cph, double
 // (warp-collective): the free path (Eq. 7) races the geometric step; a boundary
 // crossing relocates, a physics end point waits for the interaction phase.
 // Returns the lane's next phase.
-template <int MODE, bool COUNT, bool YIELD, bool EV>
-__device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, MlpCtx mc, Chain &wch) {
+constexpr int kReloc = 4;  // staged schedule: the step is done, its relocation search is deferred (aux: limiter, left)
+
+// The relocation after a geometric step (from the current leaf; `need`: the lanes that search, `leaf` the
+// answer of the others), the push after ten zero steps, and the step record: the tail of step_warp, shared
+// with the staged schedule's relocation kernel (update_nzero false there: the step kernel counted it).
+template <int MODE, bool COUNT, bool EV>
+__device__ __forceinline__ int reloc_tail(const TParams &P, const DGeom &G, Track &t, bool geo, bool need, int leaf,
+                                          bool from_left, double s, int lim, bool update_nzero, Counters &cnt,
+                                          int next) {
+  bool pushing = false;
+  int from = t.leaf;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int found = relocate_warp<MODE, COUNT>(G, need, need ? from : 0, t.x, t.u, from_left, cnt);
+    if (need) leaf = found;
+    need = false;
+    if (pass == 0 && geo) {
+      if (update_nzero) t.nzero = (dkey(s) <= dkey(G.half)) ? t.nzero + 1 : 0;
+      if (leaf >= 0 && t.nzero >= 10) {
+        const double push = 100.0 * G.tol;
+        t.x.x += push * t.u.x;
+        t.x.y += push * t.u.y;
+        t.x.z += push * t.u.z;
+        if (P.out_len) t.len += push;
+        event<EV>(cnt, G4N_C_PUSHES);
+        t.nzero = 0;
+        pushing = need = true;
+        from = leaf;
+        from_left = false;
+      }
+    }
+    if (!__any_sync(kFull, need)) break;
+  }
+  if (pushing && P.out_hash) t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
+  if (geo) {
+    if (leaf < 0) {
+      event<EV>(cnt, G4N_C_ESCAPED);
+      tally(P, t, G.n_vol, t.E);
+      if (P.out_hash) t.h = hash_step(t.h, -1, lim, kEvEscape);
+      finish(P, t);
+      next = kEmpty;
+    } else {
+      t.leaf = leaf;
+      if (P.out_hash) t.h = hash_step(t.h, leaf, lim, kEvNone);
+      update_mu(G, t);
+      next = kStep;
+    }
+  }
+  return next;
+}
+
+template <int MODE, bool COUNT, bool YIELD, bool EV, bool DEFER = false>
+__device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, MlpCtx mc, Chain &wch,
+                         int *aux = nullptr) {
   const bool resume = YIELD && phase == kWalk;  // continue the step's yielded boundary search
   bool act = phase == kStep || resume;
   const DGeom &G = P.geoms[P.items[act ? t.item : 0].geom];
@@ -555,47 +607,17 @@ __device__ int step_warp(const TParams &P, Track &t, int phase, Counters &cnt, M
   const bool fast = left && face_relocate(G, t.leaf, R.face, t.x, t.u, &leaf);
   if (fast) diag<COUNT>(cnt, G4N_C_FACE_RELOC);
   // relocation search, then (after 10 zero steps) the push and its relocation: one copy of
-  // the relocation code serves both passes
-  bool need = geo && !fast, from_left = left, pushing = false;
-  int from = t.leaf;
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const int found = relocate_warp<MODE, COUNT>(G, need, need ? from : 0, t.x, t.u, from_left, cnt);
-    if (need) leaf = found;
-    need = false;
-    if (pass == 0 && geo) {
-      t.nzero = (dkey(s) <= dkey(G.half)) ? t.nzero + 1 : 0;
-      if (leaf >= 0 && t.nzero >= 10) {
-        const double push = 100.0 * G.tol;
-        t.x.x += push * t.u.x;
-        t.x.y += push * t.u.y;
-        t.x.z += push * t.u.z;
-        if (P.out_len) t.len += push;
-        event<EV>(cnt, G4N_C_PUSHES);
-        t.nzero = 0;
-        pushing = need = true;
-        from = leaf;
-        from_left = false;
-      }
-    }
-    if (!__any_sync(kFull, need)) break;
+  // the relocation code serves both passes.  DEFER: a lane that needs the search stops here (its
+  // zero-step count updated) and goes to the relocation queue with its limiter and exit flag.
+  bool defer = false;
+  if (DEFER && geo && !fast) {
+    defer = true;
+    t.nzero = (dkey(s) <= dkey(G.half)) ? t.nzero + 1 : 0;
+    *aux = (lim << 1) | (left ? 1 : 0);
   }
-  if (pushing && P.out_hash) t.h = hash_step(t.h, leaf, kLimPush, kEvPush);
-  if (geo) {
-    if (leaf < 0) {
-      event<EV>(cnt, G4N_C_ESCAPED);
-      tally(P, t, G.n_vol, t.E);
-      if (P.out_hash) t.h = hash_step(t.h, -1, lim, kEvEscape);
-      finish(P, t);
-      next = kEmpty;
-    } else {
-      t.leaf = leaf;
-      if (P.out_hash) t.h = hash_step(t.h, leaf, lim, kEvNone);
-      update_mu(G, t);
-      next = kStep;
-    }
-  }
-  return next;
+  next = reloc_tail<MODE, COUNT, EV>(P, G, t, geo && !defer, !DEFER && geo && !fast, leaf, left, s, lim, true, cnt,
+                                     next);
+  return defer ? kReloc : next;
 }
 
 // The interaction at the end of a free path: photoabsorption if U mu_tot < mu_photo,
@@ -1115,6 +1137,7 @@ int transport_shape(g4n_ctx *ctx, const g4n_batch_desc *b, int *block, int *refi
   if (b->schedule != G4N_SCHEDULE_PERSISTENT && b->schedule != G4N_SCHEDULE_STAGED)
     return g4n_fail(ctx, G4N_ERR_ARG, "transport: unknown schedule");
   if (b->pool_tracks < 0) return g4n_fail(ctx, G4N_ERR_ARG, "transport: pool_tracks must be >= 0");
+  if (b->staged_flags & ~G4N_STAGED_RELOCATION_KERNEL) return g4n_fail(ctx, G4N_ERR_ARG, "transport: unknown staged_flags");
   if (b->mode == G4N_MODE_LEARNED && !g4n_mlp_image(ctx))
     return g4n_fail(ctx, G4N_ERR_STATE, "transport: learned mode needs MLP weights (g4n_mlp_load / g4n_mlp_train)");
   return G4N_OK;

@@ -18,9 +18,13 @@
 //
 // Each kernel is small enough for the instruction caches and its warps are full (the queues are
 // compact); the cost is one load and one store of a track's state (168 B) per step and per
-// interaction, from HBM/L2 at full coalescing.  Every history is the same as in the persistent
+// interaction (and per deferred relocation), from HBM/L2 at full coalescing.  Every history is the same as in the persistent
 // kernel (the same device functions advance a track; the order of steps within a history is
 // fixed), so results do not depend on the schedule.
+//
+// With G4N_STAGED_RELOCATION_KERNEL a third kernel runs between the two: the step kernel queues the steps
+// whose relocation needs a search (not answered by a face record), and the relocation kernel runs those
+// searches in full warps.
 //
 // The last tracks of a batch (fewer than drain_tracks in flight, no new ones left) are finished
 // by one persistent kernel that takes them from the queue: an iteration costs at least the
@@ -35,10 +39,11 @@
 namespace {
 
 constexpr int kSgKinds = 4;                 // solid kinds (box, tube, orb, cone)
-constexpr int kSgQueues = 2 * kSgKinds + 1; // step queues of two banks, then the interaction queue
+constexpr int kSgQueues = 2 * kSgKinds + 2; // step queues of two banks, the interaction and the relocation queue
 constexpr int kSgInteract = 2 * kSgKinds;
-constexpr int kSgArrays = 5;                // queue arrays of `pool` entries (see sg_entry)
-constexpr int kSgDoubles = 16, kSgInts = 6;
+constexpr int kSgReloc = 2 * kSgKinds + 1;
+constexpr int kSgArrays = 6;                // queue arrays of `pool` entries (see sg_entry)
+constexpr int kSgDoubles = 16, kSgInts = 7; // the seventh int: a deferred relocation's limiter and exit flag
 constexpr int kSgChunk = 8;                 // iterations launched between reads of the end flag
 
 // Track-state queues, structure of arrays: field f of entry e at base_f[e].
@@ -46,7 +51,7 @@ struct SgQueues {
   double *d;       // kSgDoubles fields x n: x, u, 1/u, E, Y, len, safety, mu, mu_photo, bin fraction
   uint64_t *h;     // history hash
   int64_t *tid;    // track id
-  int32_t *iw;     // kSgInts fields x n: leaf, item, steps, zero steps, energy bin, draw counter
+  int32_t *iw;     // kSgInts fields x n: leaf, item, steps, zero steps, energy bin, draw counter, relocation aux
   int64_t n;       // entries per field (kSgArrays x pool)
   int64_t pool;    // tracks in flight at most
 };
@@ -59,7 +64,7 @@ struct SgCtrl {
   unsigned long long q_head;          // next track of the batch to start
   long long active;                   // tracks in flight
   long long n_new, base;              // admission of the current iteration: tracks [base, base + n_new)
-  unsigned int fin[3];                // blocks finished per kernel (step, finish, drain)
+  unsigned int fin[4];                // blocks finished per kernel (step, finish, drain, relocation)
   int done;                           // every track has ended
   int drain_now, drain_bank;          // the drain kernel takes the tracks of this bank
   long long iterations;               // iterations run (a runaway guard for the host)
@@ -72,6 +77,7 @@ struct SgCtrl {
 // the tracks of a bank are never more than `pool`, so no two queues of an array can meet.
 __device__ __forceinline__ int64_t sg_entry(const SgQueues &Q, int q, long long j) {
   if (q == kSgInteract) return 4 * Q.pool + j;
+  if (q == kSgReloc) return 5 * Q.pool + j;
   const int64_t a = (int64_t)(q >> 1) * Q.pool;  // bank b, kind k: array 2b + (k >> 1)
   return (q & 1) ? a + Q.pool - 1 - j : a + j;
 }
@@ -132,7 +138,7 @@ __device__ __forceinline__ void sg_push(const SgQueues &Q, SgCtrl *C, bool want,
 __shared__ unsigned s_qcount[kSgQueues];
 __shared__ unsigned long long s_qbase[kSgQueues];
 
-__device__ __forceinline__ void sg_push_block(const SgQueues &Q, SgCtrl *C, bool want, int q, const Track &t) {
+__device__ __forceinline__ int64_t sg_push_block(const SgQueues &Q, SgCtrl *C, bool want, int q, const Track &t) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned peers = __match_any_sync(kFull, want ? q : -1);
   const int leader = __ffs(peers) - 1;
@@ -146,7 +152,12 @@ __device__ __forceinline__ void sg_push_block(const SgQueues &Q, SgCtrl *C, bool
     s_qcount[threadIdx.x] = 0;  // ready for the next call (the barrier below orders it before any new count)
   }
   __syncthreads();
-  if (want) sg_store(Q, sg_entry(Q, q, (long long)(s_qbase[q] + woff + __popc(peers & ((1u << lane) - 1u)))), t);
+  int64_t e = -1;
+  if (want) {
+    e = sg_entry(Q, q, (long long)(s_qbase[q] + woff + __popc(peers & ((1u << lane) - 1u))));
+    sg_store(Q, e, t);
+  }
+  return e;  // the lane's queue entry (-1: none)
 }
 
 // Step queue of bank b for the track's leaf.
@@ -231,7 +242,9 @@ __device__ __forceinline__ long long sg_prefix(const SgCtrl *C, int b, long long
 
 // Step kernel of iteration (ib: the bank read, the other bank written).  Its last block admits
 // the next tracks of the batch: as many as the tracks in flight leave room for in the pool.
-template <int MODE>
+// RELOC_KERNEL: a step that needs a relocation search (not answered by a face record) is queued for the
+// relocation kernel instead of searching here, with its limiter and exit flag in the entry's aux int.
+template <int MODE, bool RELOC_KERNEL>
 __global__ void __launch_bounds__(128, 4) k_staged_step(const TParams P, const SgQueues Q, SgCtrl *C, int ib) {
   if (((const volatile SgCtrl *)C)->drain_now || ((const volatile SgCtrl *)C)->done) return;
   Counters cnt;
@@ -258,10 +271,13 @@ __global__ void __launch_bounds__(128, 4) k_staged_step(const TParams P, const S
       phase = kStep;
     }
     Chain ch;
-    const int next = step_warp<MODE, false, false, true>(P, t, phase, cnt, mc, ch);
+    int aux = 0;
+    const int next = step_warp<MODE, false, false, true, RELOC_KERNEL>(P, t, phase, cnt, mc, ch, &aux);
     const bool was = phase == kStep;
     const bool keep = was && next != kEmpty;
-    sg_push_block(Q, C, keep, !keep ? 0 : next == kStep ? sg_queue_of(P, t, ob) : kSgInteract, t);
+    const int q = !keep ? 0 : next == kStep ? sg_queue_of(P, t, ob) : next == kReloc ? kSgReloc : kSgInteract;
+    const int64_t e = sg_push_block(Q, C, keep, q, t);
+    if (RELOC_KERNEL && keep && next == kReloc) Q.iw[6 * Q.n + e] = aux;
     sg_retire(C, was && next == kEmpty);
   }
   sg_flush(P, cnt);
@@ -275,6 +291,50 @@ __global__ void __launch_bounds__(128, 4) k_staged_step(const TParams P, const S
     V->n_new = n_new;
     V->q_head = V->q_head + (unsigned long long)n_new;
     V->active = active + n_new;
+    __threadfence();
+  }
+}
+
+// Relocation kernel of the iteration (the option G4N_STAGED_RELOCATION_KERNEL): the steps whose relocation
+// search the step kernel deferred, in full warps of searching lanes (in the step kernel a warp's lanes limited
+// by physics or answered by a face record wait while the others search); then the push after ten zero
+// steps and the step record, as the step kernel would have done them, and the tracks go on to bank ob.  Its
+// last block empties the queue.
+template <int MODE>
+__global__ void __launch_bounds__(128, 4) k_staged_reloc(const TParams P, const SgQueues Q, SgCtrl *C, int ib) {
+  const volatile SgCtrl *V0 = C;
+  if (V0->drain_now || V0->done) return;
+  Counters cnt;
+  sg_begin(cnt);
+  const long long total = (long long)V0->cnt[kSgReloc];
+  const int ob = ib ^ 1;
+  const bool want_slot = P.out_hash || P.out_len;
+  // block-sized strides: the loop condition is the same for every thread of the block (sg_push_block's barriers)
+#pragma unroll 1
+  for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < total; b0 += (long long)gridDim.x * blockDim.x) {
+    const long long i = b0 + threadIdx.x;
+    const bool act = i < total;
+    Track t;
+    t.item = 0;
+    t.leaf = 0;
+    int aux = 0;
+    if (act) {
+      const int64_t e = sg_entry(Q, kSgReloc, i);
+      sg_load(Q, e, t);
+      aux = __ldcs(Q.iw + 6 * Q.n + e);
+      if (want_slot) sg_restore_gidx(P, t);
+    }
+    const DGeom &G = P.geoms[P.items[act ? t.item : 0].geom];
+    // every lane searches (the step kernel already counted the zero step); aux = limiter << 1 | left the leaf
+    const int next = reloc_tail<MODE, false, true>(P, G, t, act, act, -1, (aux & 1) != 0, 0.0, aux >> 1, false, cnt,
+                                                   kEmpty);
+    const bool keep = act && next == kStep;
+    sg_push_block(Q, C, keep, keep ? sg_queue_of(P, t, ob) : 0, t);
+    sg_retire(C, act && next == kEmpty);
+  }
+  sg_flush(P, cnt);
+  if (sg_last_block(C, 3) && threadIdx.x == 0) {
+    ((volatile SgCtrl *)C)->cnt[kSgReloc] = 0;
     __threadfence();
   }
 }
@@ -484,7 +544,10 @@ int staged_run(g4n_ctx *ctx, const g4n_batch_desc *b, TParams &P, cudaStream_t s
 
   const size_t smem = mlp_smem_bytes(b->mode, 128);
   P.mlp_w = g4n_mlp_image(ctx);
-  const int g_step = sg_grid(ctx, b, k_staged_step<MODE>, smem);
+  const bool reloc_kernel = (b->staged_flags & G4N_STAGED_RELOCATION_KERNEL) != 0;
+  const int g_step = reloc_kernel ? sg_grid(ctx, b, k_staged_step<MODE, true>, smem)
+                                  : sg_grid(ctx, b, k_staged_step<MODE, false>, smem);
+  const int g_reloc = sg_grid(ctx, b, k_staged_reloc<MODE>, 0);
   const int g_fin = sg_grid(ctx, b, k_staged_finish<MODE>, 0);
   int per_sm_drain = 0;
   if (smem) cudaFuncSetAttribute(k_staged_drain<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -505,7 +568,13 @@ int staged_run(g4n_ctx *ctx, const g4n_batch_desc *b, TParams &P, cudaStream_t s
   for (long long chunk = 0;; ++chunk) {
     for (int j = 0; j < kSgChunk; ++j, ++it) {
       const int ib = (int)(it & 1);
-      k_staged_step<MODE><<<g_step, 128, smem, st>>>(P, Q, C, ib);
+      if (reloc_kernel) {
+        k_staged_step<MODE, true><<<g_step, 128, smem, st>>>(P, Q, C, ib);
+        k_staged_reloc<MODE><<<g_reloc, 128, 0, st>>>(P, Q, C, ib);
+        ++ctx->launches;
+      } else {
+        k_staged_step<MODE, false><<<g_step, 128, smem, st>>>(P, Q, C, ib);
+      }
       k_staged_finish<MODE><<<g_fin, 128, 0, st>>>(P, Q, C, ib, drain_tracks);
       ctx->launches += 2;
     }

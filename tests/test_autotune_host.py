@@ -35,8 +35,9 @@ def test_tuner_shapes_are_valid_batch_descriptions():
     for shape in [at.DEFAULT] + [dict(at.DEFAULT, schedule=b.G4N_SCHEDULE_STAGED, **s) for s in at.STAGED]:
         d = b._desc(items, 1, 0.01, 0, 100, 200, 0, shape["block_size"], shape["blocks_per_sm"], shape["refill_min"],
                     shape["interact_min"], False, shape["walk_budget"], shape["regroup_period"], shape["schedule"],
-                    shape["pool_tracks"], shape["drain_tracks"])
+                    shape["pool_tracks"], shape["drain_tracks"], shape["staged_flags"])
         assert d.schedule in (b.G4N_SCHEDULE_PERSISTENT, b.G4N_SCHEDULE_STAGED)
+        assert d.staged_flags in (0, b.G4N_STAGED_RELOCATION_KERNEL)
         assert d.pool_tracks >= 0 and d.drain_tracks >= -1 and 0 <= d.blocks_per_sm <= 16
         assert d.block_size % 32 == 0 and d.block_size <= 128
     assert {s["drain_tracks"] for s in at.STAGED} >= {0, -1}     # the default drain point and no drain are both tried

@@ -141,7 +141,7 @@ def test_queries_refused_on_host_only_context(g4):
 
 @pytest.mark.parametrize("field,value", [("walk_budget", -1), ("regroup_period", -2), ("refill_min", 33),
                                          ("interact_min", 40), ("block_size", 48), ("mode", 7), ("schedule", 2),
-                                         ("pool_tracks", -1)])
+                                         ("pool_tracks", -1), ("staged_flags", 2)])
 def test_transport_rejects_bad_launch_fields(g4, field, value):
     """Launch-shape fields are validated on the host before any device work (G4N_ERR_ARG); with valid fields the
     same call on a host-only context is refused as a device query (G4N_ERR_STATE).  The output pointers are host

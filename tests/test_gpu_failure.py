@@ -44,7 +44,7 @@ def _expect(env, code, text):
     assert e.value.code == code and text in str(e.value), str(e.value)
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2])   # 2: staged with the relocation kernel
 @pytest.mark.parametrize("mode", [0, 1])
 def test_walk_cap_reports_timeout_and_context_recovers(env, mode, schedule):
     """A voxel walk capped at one node gives up on every search that crosses a node boundary; the device
@@ -53,11 +53,12 @@ def test_walk_cap_reports_timeout_and_context_recovers(env, mode, schedule):
     g4, torch, ctx, sc, gid = env
     g4.g4n_set_loop_caps(ctx, 1, 0)
     try:
-        _run(env, mode=mode, schedule=schedule)
+        _run(env, mode=mode, schedule=min(schedule, 1), staged_flags=1 if schedule == 2 else 0)
         _expect(env, g4.G4N_ERR_TIMEOUT, "voxel walk")
     finally:
         g4.g4n_set_loop_caps(ctx, 0, 0)
-    edep, cnt, h = _run(env, n=3000, seed=12, mode=mode, schedule=schedule)
+    edep, cnt, h = _run(env, n=3000, seed=12, mode=mode, schedule=min(schedule, 1),
+                        staged_flags=1 if schedule == 2 else 0)
     g4.g4n_sync(ctx)
     ref = oracle.Geometry(sc).transport(synth.scenes.tiny_source(), 12, 3000)
     assert np.array_equal(h.cpu().numpy().view(np.uint64), ref["hashes"])

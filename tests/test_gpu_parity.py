@@ -283,7 +283,7 @@ def test_transport_parity(env, name, n, mode):
     _compare_transport(g4, r, edep, cnt, h, ln, sc.n_volumes)
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2])   # 2: staged with the relocation kernel
 @pytest.mark.parametrize("mode", MODES)
 def test_transport_calorimeter_full_size_sampled(env, mode, schedule):
     """The benchmark workload (10^6 tracks, default launch shape): sampled histories replayed one by one
@@ -293,7 +293,8 @@ def test_transport_calorimeter_full_size_sampled(env, mode, schedule):
     src = synth.scenes.calorimeter_source()
     seed = synth.scenes.CONFIG_SEEDS[1][1]
     n = 1_000_000
-    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, schedule=schedule)
+    edep, cnt, h, ln = _transport_gpu(env, gid, sc, src, seed, n, mode=mode, schedule=min(schedule, 1),
+                                      staged_flags=1 if schedule == 2 else 0)
     g4.g4n_sync(ctx)
     hashes = h.cpu().numpy().view(np.uint64)
     lens = ln.cpu().numpy()
@@ -474,7 +475,8 @@ def test_logical_volume_scene_parity(env, mode):
     assert g4.counters_dict(cnt)["geom_steps"] > 5 * n   # the tracks cross many cells
 
 
-def _full_size_sampled(env, entries_fn, seed, n_sample=300, modes=(0, 1, 2), schedules=(0, 1)):
+def _full_size_sampled(env, entries_fn, seed, n_sample=300, modes=(0, 1, 2), schedules=(0, 1, 2)):
+    # schedules: 0 the persistent kernel, 1 staged, 2 staged with the relocation kernel
     """Every mode and schedule over a full-size launch: identical histories across them, and a random
     sample of the histories replayed one by one by the oracle."""
     g4, torch, ctx = env
@@ -486,7 +488,8 @@ def _full_size_sampled(env, entries_fn, seed, n_sample=300, modes=(0, 1, 2), sch
             edep = torch.zeros((100, stride), dtype=torch.float64, device="cuda")
             cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
             h = torch.zeros(total, dtype=torch.int64, device="cuda")
-            g4.g4n_transport_batch(ctx, items, seed, edep, cnt, h, mode=mode, schedule=sched)
+            g4.g4n_transport_batch(ctx, items, seed, edep, cnt, h, mode=mode, schedule=min(sched, 1),
+                                   staged_flags=1 if sched == 2 else 0)
             g4.g4n_sync(ctx)
             hashes[mode, sched] = h.cpu().numpy().view(np.uint64)
             c = g4.counters_dict(cnt)

@@ -88,13 +88,15 @@ def _compare(g4, r, edep, cnt, h, ln, nv):
         assert abs(dg[:nv + 1].sum() - dg[nv + 1]) <= 1e-9 * dg[nv + 1]
 
 
+@pytest.mark.parametrize("flags", [0, 1])   # 1: G4N_STAGED_RELOCATION_KERNEL
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("name", list(SCENES))
-def test_staged_parity(env, name, mode):
-    """Default pool (the whole batch in flight) and default drain."""
+def test_staged_parity(env, name, mode, flags):
+    """Default pool (the whole batch in flight) and default drain, relocation searches in the step kernel or in
+    their own kernel."""
     g4, torch, ctx = env
     sc, src, n, og, gid, r = _scene(env, name)
-    out = _run(env, gid, sc, src, SEED, n, mode=mode)
+    out = _run(env, gid, sc, src, SEED, n, mode=mode, staged_flags=flags)
     g4.g4n_sync(ctx)
     _compare(g4, r, *out, sc.n_volumes)
 
@@ -109,8 +111,8 @@ def test_staged_pool_and_drain(env, name, pool, drain):
     if pool < 100:   # a tiny pool takes one iteration per step of every track: fewer tracks
         n = 500
         r = og.transport(src, SEED, n, threads=0)
-    for mode in (0, 1):
-        out = _run(env, gid, sc, src, SEED, n, mode=mode, pool_tracks=pool, drain_tracks=drain)
+    for mode, flags in ((0, 0), (1, 0), (0, 1)):
+        out = _run(env, gid, sc, src, SEED, n, mode=mode, pool_tracks=pool, drain_tracks=drain, staged_flags=flags)
         g4.g4n_sync(ctx)
         _compare(g4, r, *out, sc.n_volumes)
 
@@ -144,11 +146,18 @@ def test_staged_edge_cases(env):
         g4.g4n_sync(ctx)
     assert e.value.code == g4.G4N_ERR_STEP_LIMIT
     _compare(g4, r3, *out, sc.n_volumes)
-    # a pool of one track, a track id offset, the blocks per SM set
+    # a pool of one track, a track id offset, the blocks per SM set; the step cap with the relocation kernel
     r1 = og.transport(src, 8, 40, tid0=12345)
-    out = _run(env, gid, sc, src, 8, 40, tid0=12345, pool_tracks=1, drain_tracks=-1, blocks_per_sm=1)
-    g4.g4n_sync(ctx)
-    _compare(g4, r1, *out, sc.n_volumes)
+    for flags in (0, 1):
+        out = _run(env, gid, sc, src, 8, 40, tid0=12345, pool_tracks=1, drain_tracks=-1, blocks_per_sm=1,
+                   staged_flags=flags)
+        g4.g4n_sync(ctx)
+        _compare(g4, r1, *out, sc.n_volumes)
+    out = _run(env, gid, sc, src, 6, 500, max_steps=3, pool_tracks=64, drain_tracks=-1, staged_flags=1)
+    with pytest.raises(g4.G4NError) as e:
+        g4.g4n_sync(ctx)
+    assert e.value.code == g4.G4N_ERR_STEP_LIMIT
+    _compare(g4, r3, *out, sc.n_volumes)
 
 
 def test_staged_several_geometries(env):
@@ -164,11 +173,12 @@ def test_staged_several_geometries(env):
         tid += 700
     items = g4.make_items(entries)
     seed = 0x5A7E
-    for mode, pool in ((0, 0), (1, 2000), (2, 777)):
+    for mode, pool, flags in ((0, 0, 0), (1, 2000, 1), (2, 777, 0), (0, 999, 1)):
         edep = torch.zeros((100, off), dtype=torch.float64, device="cuda")
         cnt = torch.zeros(g4.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
         h = torch.zeros(tid, dtype=torch.int64, device="cuda")
-        g4.g4n_transport_batch(ctx, items, seed, edep, cnt, h, mode=mode, schedule=STAGED, pool_tracks=pool)
+        g4.g4n_transport_batch(ctx, items, seed, edep, cnt, h, mode=mode, schedule=STAGED, pool_tracks=pool,
+                               staged_flags=flags)
         g4.g4n_sync(ctx)
         hashes = h.cpu().numpy().view(np.uint64)
         for sc, og, o, t0 in geoms:
