@@ -7,7 +7,9 @@ block-wide regrouping, the staged schedule's drain point) or the precision mode,
 only speed does.  The tuner times trial launches of the caller's batch with CUDA
 events: a few staged shapes, then the persistent kernel's parameters one at a
 time from the defaults, keeping any value that is faster (coordinate descent),
-within a time budget.  It only calls the C ABI through the binding.
+within a time budget; a batch tuned on a proportional subset has its staged winner and that shape's
+twin with the other relocation-kernel setting timed once more on the whole batch.  It only calls the
+C ABI through the binding.
 """
 from __future__ import annotations
 
@@ -77,6 +79,7 @@ def autotune(ctx, items, stride, seed, modes=(b.G4N_MODE_FP64, b.G4N_MODE_FP32_R
     trials, so that the budget covers the whole search)."""
     import torch
     space = space or SPACE
+    full_items = items
     items = subset_items(items, max_tracks)
     edep = torch.zeros((n_batches, stride), dtype=torch.float64, device="cuda")
     cnt = torch.zeros(b.G4N_N_COUNTERS, dtype=torch.int64, device="cuda")
@@ -112,6 +115,17 @@ def autotune(ctx, items, stride, seed, modes=(b.G4N_MODE_FP64, b.G4N_MODE_FP32_R
                     pbest, pcfg = ms, trial
                 if ms < best:
                     best, cfg = ms, trial
+        if items is not full_items and cfg["schedule"] == b.G4N_SCHEDULE_STAGED:
+            # the staged kernels' balance shifts with the batch size: the winner and its relocation-kernel twin
+            # are timed once more on the whole batch
+            twin = dict(cfg, staged_flags=cfg["staged_flags"] ^ b.G4N_STAGED_RELOCATION_KERNEL)
+            time_launch(ctx, full_items, seed, edep, cnt, mode, cfg, 1, stream)   # warm-up (the queues grow)
+            full = {k: time_launch(ctx, full_items, seed, edep, cnt, mode, c, 1, stream)
+                    for k, c in (("best", cfg), ("twin", twin))}
+            trials.append((mode, dict(twin), full["twin"]))
+            if full["twin"] < full["best"]:
+                cfg = twin
+            best = min(full.values()) * best / max(full["best"], 1e-9)   # keep the subset's scale for the ranking
         per_mode[mode] = {"cfg": cfg, "ms": best}
     mode = min(per_mode, key=lambda m: per_mode[m]["ms"])
     return {"mode": mode, "cfg": per_mode[mode]["cfg"], "ms": per_mode[mode]["ms"], "per_mode": per_mode,
