@@ -58,21 +58,20 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 FP64 flop
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one transport batch, per workload, mode and schedule,
 # from single-pass ncu captures run without the L2 flush before the batch (--no-flush; the flush changes the figure by
-# < 1 %): the persistent kernel's one launch, or the sum over the staged schedule's kernels of a batch (launch list of
-# nine batches, divided by nine).  Summaries in profiles/.  Reported only while the CUDA sources hash to the value
-# they had when the captures were taken (else the kernels may have changed since).
-NCU_TRAFFIC = {"sources_sha256": "7442afa4330e317c30072e4a7cacb4ce8355323a69cb88fdfbe0647c62d1c6b7",
-               # staged: captured at commit 04de76f, whose CUDA sources differ from these only in comments and in the
-               # launch bounds of k_locate (a query kernel, not part of a transport batch); persistent kernel: captured at an earlier hash whose k_transport device code is the same (only
-               # host code and the staged kernels were added since); barrel: captured on the plain barrel workload (same
-               # scene and 10^7 tracks, another seed), which the learned workload's line times with the same kernels
-               "bytes_per_launch": {"barrel/fp64": 8518400 + 997785600, "barrel_learned/fp64": 8518400 + 997785600,
-                                    "calorimeter/fp64": 2280192 + 40204288,
-                                    "barrel/fp64/staged": 43353388459, "barrel_learned/fp64/staged": 43353388459,
-                                    "barrel/fp32_recheck/staged": 49741550791,
-                                    "barrel_learned/fp32_recheck/staged": 49741550791,
-                                    "barrel_nested/fp32_recheck/staged": 50813333873,
-                                    "calorimeter/fp64/staged": 4327307804}}
+# < 1 %): the sum over the staged schedule's kernels of a batch (launch list of nine batches, divided by nine).
+# Summaries in profiles/.  Reported only while the CUDA sources hash to the value they had when the captures were
+# taken (else the kernels may have changed since).
+NCU_TRAFFIC = {"sources_sha256": "2a515d3d1a2b363ad7e9903f0df9ca53372cbc4c2f82fbebbcc281eaf58812d7",
+               # barrel: captured on the plain barrel workload (same scene and 10^7 tracks, another seed), which the
+               # learned workload's line times with the same kernels; staged+reloc: the staged schedule with its
+               # relocation kernel.  (The persistent kernel's figures, 1.01 GB per barrel launch and 42.5 MB per
+               # calorimeter launch, were taken before its step code was shared with the staged kernels: see
+               # profiles/.)
+               "bytes_per_launch": {"barrel/fp64/staged+reloc": 62740151751,
+                                    "barrel_learned/fp64/staged+reloc": 62740151751,
+                                    "barrel/fp32_recheck/staged+reloc": 64838255189,
+                                    "barrel_learned/fp32_recheck/staged+reloc": 64838255189,
+                                    "calorimeter/fp64/staged": 4296949248}}
 
 
 def cuda_sources_sha256() -> str:
