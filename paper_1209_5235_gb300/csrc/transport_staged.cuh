@@ -18,13 +18,13 @@
 //
 // Each kernel is small enough for the instruction caches and its warps are full (the queues are
 // compact); the cost is one load and one store of a track's state (168 B) per step and per
-// interaction (and per deferred relocation), from HBM/L2 at full coalescing.  Every history is the same as in the persistent
-// kernel (the same device functions advance a track; the order of steps within a history is
-// fixed), so results do not depend on the schedule.
+// interaction (and per deferred relocation), from HBM/L2 at full coalescing.  Every history is the
+// same as in the persistent kernel (the same device functions advance a track; the order of steps
+// within a history is fixed), so results do not depend on the schedule.
 //
-// With G4N_STAGED_RELOCATION_KERNEL a third kernel runs between the two: the step kernel queues the steps
-// whose relocation needs a search (not answered by a face record), and the relocation kernel runs those
-// searches in full warps.
+// With G4N_STAGED_RELOCATION_KERNEL a third kernel runs between the two: the step kernel queues the
+// steps whose relocation needs a search (not answered by a face record), and the relocation kernel
+// runs those searches in full warps.
 //
 // The last tracks of a batch (fewer than drain_tracks in flight, no new ones left) are finished
 // by one persistent kernel that takes them from the queue: an iteration costs at least the

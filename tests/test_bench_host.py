@@ -41,6 +41,16 @@ def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
     assert bench.measured_traffic("barrel", "fp64") is None
 
 
+def test_source_hash_ignores_comments_only():
+    """The traffic figure's source check hashes what the compiler sees: comments and spacing do not count,
+    string literals and code do."""
+    a = 'int a = 1;  // one\n/* block */ const char *s = "x//y"; char q = \'"\';\n'
+    b = 'int a = 1;\nconst char *s = "x//y";   char q = \'"\'; // other comment\n'
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(a.replace("x//y", "x/y"))
+    assert bench.code_only(a) != bench.code_only(a.replace("a = 1", "a = 2"))
+
+
 def test_algorithmic_flops_weights_each_counted_event():
     counts = {k: 0 for k in bench.FLOPS}
     assert bench.algorithmic_flops(counts) == 0.0
