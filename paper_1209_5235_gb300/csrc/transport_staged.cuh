@@ -299,9 +299,11 @@ __global__ void __launch_bounds__(128, 4) k_staged_step(const TParams P, const S
 // search the step kernel deferred, in full warps of searching lanes (in the step kernel a warp's lanes limited
 // by physics or answered by a face record wait while the others search); then the push after ten zero
 // steps and the step record, as the step kernel would have done them, and the tracks go on to bank ob.  Its
-// last block empties the queue.
+// last block empties the queue.  8 blocks of 128 per SM (64 registers): the searches wait on chains of
+// dependent table loads, and more resident warps hide them (barrel 10^7: 2.4 % of the batch against 4 blocks
+// at 128 registers, 6 blocks in between).
 template <int MODE>
-__global__ void __launch_bounds__(128, 4) k_staged_reloc(const TParams P, const SgQueues Q, SgCtrl *C, int ib) {
+__global__ void __launch_bounds__(128, 8) k_staged_reloc(const TParams P, const SgQueues Q, SgCtrl *C, int ib) {
   const volatile SgCtrl *V0 = C;
   if (V0->drain_now || V0->done) return;
   Counters cnt;
