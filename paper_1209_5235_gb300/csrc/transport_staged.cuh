@@ -67,7 +67,7 @@ struct SgCtrl {
   unsigned int fin[4];                // blocks finished per kernel (step, finish, drain, relocation)
   int done;                           // every track has ended
   int drain_now, drain_bank;          // the drain kernel takes the tracks of this bank
-  long long iterations;               // iterations run (a runaway guard for the host)
+  long long iterations;               // iterations ended (a count for debugging; the host keeps its own)
   unsigned long long drain_head;      // drain kernel: next queue entry to take
   unsigned long long pad[4];
 };
