@@ -18,7 +18,8 @@
  *    DEVICE pointers (e.g. torch CUDA tensors), structure-of-arrays:
  *    a 3-vector array of n points is laid out as x[0..n), y[0..n), z[0..n).
  *    The `stream` argument is a cudaStream_t (NULL = legacy default stream).
- *    Calls are asynchronous on that stream; device-side errors (step caps,
+ *    Calls are asynchronous on that stream (a transport batch on the staged
+ *    schedule returns when the batch has ended); device-side errors (step caps,
  *    loop caps) are reported by the next g4n_sync() on the same stream.
  *  - The library owns the geometry tables and its workspace; g4n_destroy()
  *    frees them.  One context per host thread; one transport in flight per
